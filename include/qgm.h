@@ -1,0 +1,234 @@
+/*
+ * qgm.h -- C ABI of the GB300 amplitude engine.
+ *
+ * Computes output amplitudes <x|C|0^n> of low-depth random grid circuits as
+ * the partition function of a complex undirected graphical model, evaluated
+ * by variable elimination (Boixo, Isakov, Smelyanskiy, Neven,
+ * arXiv:1712.05384).  Host-side functions (circuit, model, plan) run on the
+ * CPU; the elimination itself runs in hand-written sm_103a CUDA kernels.
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status: QGM_OK (0) or a negative
+ *    QGM_ERR_* code.  No C++ exception crosses this boundary; the message of
+ *    the last error on the calling thread is returned by qgm_last_error().
+ *  - Handles (qgm_circuit, qgm_model, qgm_plan) are opaque, owned by the
+ *    library, and released with the matching qgm_*_free (NULL is accepted).
+ *  - Device buffers are owned by the caller: pointers are plain device
+ *    addresses (cudaMalloc or a torch tensor's data_ptr) and `stream` is a
+ *    cudaStream_t passed as void* (NULL = the legacy default stream).
+ *  - Bit j of an output bitstring (uint64) is the value of qubit j; qubit
+ *    q = r * cols + c on a rows x cols grid.
+ *  - Complex results are complex128, stored as interleaved (re, im) doubles.
+ */
+#ifndef QGM_H
+#define QGM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  QGM_OK = 0,
+  QGM_ERR_ARG = -1,       /* invalid argument, size or state */
+  QGM_ERR_OOM = -2,       /* plan exceeds the memory budget / workspace too small */
+  QGM_ERR_CUDA = -3,      /* a CUDA runtime call failed */
+  QGM_ERR_TIMEOUT = -4,   /* a bounded device wait gave up */
+  QGM_ERR_NONFINITE = -5, /* a tensor maximum became Inf/NaN */
+  QGM_ERR_NOGPU = -6      /* no CUDA device is visible */
+};
+
+/* Gate kinds (paper Sec. "Numerical results": H, X^1/2, Y^1/2, T, CZ) plus
+ * the parametrised one-qubit gate exp(-i theta (cos phi X + sin phi Y) / 2). */
+enum {
+  QGM_GATE_H = 0,
+  QGM_GATE_X12 = 1,
+  QGM_GATE_Y12 = 2,
+  QGM_GATE_T = 3,
+  QGM_GATE_CZ = 4,
+  QGM_GATE_RXY = 5
+};
+
+typedef struct {
+  int32_t kind;   /* QGM_GATE_* */
+  int32_t cycle;  /* clock cycle t of Eq. fpath (0 = the H layer) */
+  int32_t q0;     /* qubit */
+  int32_t q1;     /* second qubit of a CZ, else -1 */
+  double theta;   /* QGM_GATE_RXY only */
+  double phi;     /* QGM_GATE_RXY only */
+} qgm_gate;
+
+typedef struct qgm_circuit qgm_circuit;
+typedef struct qgm_model qgm_model;
+typedef struct qgm_plan qgm_plan;
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *qgm_last_error(void);
+
+/* ---------------------------------------------------------------- circuit */
+
+/* Random grid circuit, paper Sec. "Numerical results" (layout rules cited
+ * there, read as: H layer in cycle 0; CZ layer (t-1) mod 8 of the rotation
+ * [HZ0,HZ2,VT0,VT2,HZ1,HZ3,VT1,VT3] in cycle t; a qubit in a CZ at t-1 and
+ * none at t gets T the first time, then X^1/2 or Y^1/2 from SplitMix64(seed)).
+ * param_mode != 0 turns every X^1/2/Y^1/2 slot into RXY(theta, phi) with
+ * theta = pi u1, phi = 2 pi u2 from two draws.  depth counts all cycles.
+ * Errors: QGM_ERR_ARG for rows, cols, depth < 1 or rows*cols > 64. */
+int qgm_circuit_grid(int rows, int cols, int depth, uint64_t seed, int param_mode,
+                     qgm_circuit **out);
+
+/* Circuit from an explicit host gate list (copied).  Gates act in list
+ * order.  Errors: QGM_ERR_ARG for bad kinds or qubit indices. */
+int qgm_circuit_from_gates(int n_qubits, const qgm_gate *gates, int64_t n_gates,
+                           qgm_circuit **out);
+
+/* Copies up to `cap` gates into `gates` (host) and stores the count in *n. */
+int qgm_circuit_gates(const qgm_circuit *c, qgm_gate *gates, int64_t cap, int64_t *n);
+
+/* Indices (into the gate list) of the RXY gates, in list order: the
+ * parameter order of qgm_amplitude_grad (theta_p at 2p, phi_p at 2p+1). */
+int qgm_circuit_param_gates(const qgm_circuit *c, int32_t *idx, int64_t cap, int64_t *n);
+
+void qgm_circuit_free(qgm_circuit *c);
+
+/* ------------------------------------------------------------------ model */
+
+typedef struct {
+  int32_t n_qubits;
+  int32_t n_vars;      /* sum_j (d_j + 1): one variable b_j^k per qubit j and
+                          per non-diagonal gate k, plus b_j^0 (Sec. III.A) */
+  int32_t n_factors;   /* one factor per gate (Sec. III.B) */
+  int32_t n_nondiag;   /* L of App. F: number of non-diagonal gates */
+  int32_t n_params;    /* 2 * number of RXY gates */
+} qgm_model_info;
+
+/* Circuit -> graphical model (Sec. III.B, Eq. psi_x).  Diagonal gates (T, CZ)
+ * add factors but no variable; H, X^1/2, Y^1/2, RXY add one variable each.
+ * Variable ids: b_j^0 = j, then one id per non-diagonal gate in gate order. */
+int qgm_build_model(const qgm_circuit *c, qgm_model **out);
+int qgm_model_get_info(const qgm_model *m, qgm_model_info *info);
+
+/* Per variable: qubit j and worldline index k (arrays of n_vars, host). */
+int qgm_model_vars(const qgm_model *m, int32_t *qubit, int32_t *k);
+
+/* Per factor f: scope size in nvar[f] (1 or 2) and the variable ids in
+ * scope[2f], scope[2f+1] (-1 when unused). */
+int qgm_model_factors(const qgm_model *m, int32_t *nvar, int32_t *scope);
+
+void qgm_model_free(qgm_model *m);
+
+/* ------------------------------------------------------------------- plan */
+
+enum {
+  QGM_ORDER_AUTO = 0,       /* cheapest of the orders below by the cost model */
+  QGM_ORDER_MINFILL = 1,    /* min-fill; ties: fewest neighbours, smallest id */
+  QGM_ORDER_VERTICAL = 2,   /* Sec. IV.A: worldlines in lexicographic (j, k),
+                               j along the smaller lateral dimension first */
+  QGM_ORDER_VERTICAL_T = 3, /* the same with the other lateral dimension */
+  QGM_ORDER_GIVEN = 4       /* order passed in qgm_plan_opts.order */
+};
+
+enum {
+  QGM_OUT_BATCH = 0,  /* outputs fixed per bitstring of a batch (batch axis) */
+  QGM_OUT_OPEN = 1    /* all outputs left open: 2^n amplitudes (Eq. psi_x
+                         without output deltas) */
+};
+
+typedef struct {
+  int32_t order_kind;         /* QGM_ORDER_* */
+  int32_t output_mode;        /* QGM_OUT_* */
+  int64_t batch;              /* bitstrings per call (QGM_OUT_BATCH), >= 1 */
+  int64_t mem_budget_bytes;   /* cap on live intermediates; 0 = 64 GiB */
+  int32_t max_fuse;           /* max variables summed in one step (0 = 8) */
+  int32_t n_order;            /* QGM_ORDER_GIVEN: length of `order` */
+  const int32_t *order;       /* QGM_ORDER_GIVEN: elimination order (var ids) */
+} qgm_plan_opts;
+
+typedef struct {
+  int32_t order_kind;         /* the order actually used */
+  int32_t n_free;             /* variables eliminated */
+  int32_t max_clique;         /* induced width, size convention (Sec. IV.B) */
+  int32_t n_steps;            /* kernel steps per slice */
+  int32_t n_slice_vars;       /* variables sliced (conditioned on) */
+  int32_t batch_padded;       /* batch axis length in memory */
+  int64_t n_slices;           /* 2^n_slice_vars */
+  int64_t max_tensor_entries; /* largest intermediate, complex64 entries */
+  int64_t workspace_bytes;    /* device workspace qgm_plan_bind needs */
+  int64_t arena_bytes;        /* of which live intermediates */
+  double bytes_per_slice;     /* algorithmic bytes (inputs read + output written) */
+  double flops_per_slice;     /* algorithmic real flops of the products and sums */
+  double max_step_bytes;      /* algorithmic bytes of the largest step */
+} qgm_plan_info;
+
+/* Elimination order, slicing, step list and memory layout (Sec. IV, App. A).
+ * Host only; deterministic.  Errors: QGM_ERR_ARG for bad options,
+ * QGM_ERR_OOM when no slicing brings the live set under the budget. */
+int qgm_plan_order(const qgm_model *m, const qgm_plan_opts *opts, qgm_plan **out);
+int qgm_plan_get_info(const qgm_plan *p, qgm_plan_info *info);
+/* The elimination order (n_free var ids) and the sliced variables. */
+int qgm_plan_get_order(const qgm_plan *p, int32_t *order, int64_t cap, int64_t *n);
+int qgm_plan_get_slice_vars(const qgm_plan *p, int32_t *vars, int64_t cap, int64_t *n);
+/* Per-step record for tests and reports: for step s, out_rank[s] (binary
+ * variables of the output), k[s] (variables summed), n_in[s], batched[s]. */
+int qgm_plan_get_steps(const qgm_plan *p, int32_t *out_rank, int32_t *k, int32_t *n_in,
+                       int32_t *batched, int64_t cap);
+/* Algorithmic cost of step s: bytes[s] (inputs read once + output written,
+ * complex64) and flops[s] (real flops of the products and sums). */
+int qgm_plan_get_step_cost(const qgm_plan *p, double *bytes, double *flops, int64_t cap);
+void qgm_plan_free(qgm_plan *p);
+
+/* ------------------------------------------------------------- execution */
+
+/* Binds a caller-owned device workspace of at least info.workspace_bytes
+ * (256-byte aligned) to the plan and uploads the plan's constant tables into
+ * it on `stream`.  The caller keeps the workspace alive and untouched while
+ * it is bound; binding again (or to another buffer) replaces the binding.
+ * Errors: QGM_ERR_OOM if ws_bytes is too small, QGM_ERR_CUDA, QGM_ERR_NOGPU. */
+int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream);
+
+/* Amplitudes of B <= opts.batch bitstrings (Sec. III-IV; App. A):
+ * d_bitstrings: device uint64[B]; d_out: device double[2B] (re, im) written
+ * with <x_b|C|0^n> for b < B.  Runs every step of the plan, all slices, on
+ * `stream` (asynchronous; the first call with a given pointer set also
+ * builds a CUDA graph).  Requires QGM_OUT_BATCH and a bound workspace.
+ * Errors: QGM_ERR_ARG (mode, B, unbound), QGM_ERR_CUDA. */
+int qgm_amplitudes(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
+                   void *stream);
+
+/* The same with HOST bitstrings and a HOST result: copies in, runs, copies
+ * out and synchronises `stream`.  Uses the bound workspace for staging. */
+int qgm_amplitudes_host(qgm_plan *p, const uint64_t *h_bitstrings, int64_t B,
+                        double *h_out, void *stream);
+
+/* All 2^n amplitudes of a QGM_OUT_OPEN plan into device double[2 * 2^n]
+ * (entry x has bit j = qubit j): Eq. psi_x with the output deltas omitted. */
+int qgm_eliminate(qgm_plan *p, double *d_out, void *stream);
+
+/* Timing pass for reports: runs slice 0 of qgm_amplitudes kernel by kernel
+ * (no graph) with CUDA events around each launch on `stream` and stores the
+ * milliseconds in ms[0] (leaf build), ms[1 + s] (step s), ms[n_steps + 1]
+ * (accumulation); ms must hold n_steps + 2 floats (host).  Synchronises. */
+int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
+                     float *ms, void *stream);
+
+/* Reads and clears the device status word of the bound workspace
+ * (synchronises `stream`): QGM_OK, QGM_ERR_NONFINITE or QGM_ERR_TIMEOUT. */
+int qgm_status(qgm_plan *p, void *stream);
+
+/* Gradient (adjoint elimination) for a parametrised circuit: given
+ * g_b = dL/d(conj a_b) for the B bitstrings (device double[2B]), writes
+ * d_grad[i] = dL/dp_i = 2 Re sum_b conj(g_b) da_b/dp_i for the n_params
+ * parameters (theta, phi of each RXY gate, see qgm_circuit_param_gates) into
+ * device double[n_params], and the amplitudes into d_amp (device double[2B],
+ * may be NULL).  Requires QGM_OUT_BATCH.  Errors as qgm_amplitudes. */
+int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B,
+                       const double *d_dL_dconja, double *d_grad, double *d_amp,
+                       void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QGM_H */

@@ -1,0 +1,306 @@
+"""ctypes binding of libqgm.so (include/qgm.h): argument marshalling only.
+
+Every step of the amplitude path runs inside the library's CUDA kernels; this
+module only converts Python/numpy/torch arguments into the C ABI's plain
+pointers and sizes and turns negative status codes into exceptions.  There is
+no fallback: if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqgm.so")
+
+QGM_OK = 0
+ERRORS = {-1: "QGM_ERR_ARG", -2: "QGM_ERR_OOM", -3: "QGM_ERR_CUDA", -4: "QGM_ERR_TIMEOUT",
+          -5: "QGM_ERR_NONFINITE", -6: "QGM_ERR_NOGPU"}
+
+ORDER_AUTO, ORDER_MINFILL, ORDER_VERTICAL, ORDER_VERTICAL_T, ORDER_GIVEN = range(5)
+OUT_BATCH, OUT_OPEN = 0, 1
+
+
+class qgm_gate(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("cycle", C.c_int32), ("q0", C.c_int32), ("q1", C.c_int32),
+                ("theta", C.c_double), ("phi", C.c_double)]
+
+
+class qgm_model_info(C.Structure):
+    _fields_ = [("n_qubits", C.c_int32), ("n_vars", C.c_int32), ("n_factors", C.c_int32),
+                ("n_nondiag", C.c_int32), ("n_params", C.c_int32)]
+
+
+class qgm_plan_opts(C.Structure):
+    _fields_ = [("order_kind", C.c_int32), ("output_mode", C.c_int32), ("batch", C.c_int64),
+                ("mem_budget_bytes", C.c_int64), ("max_fuse", C.c_int32), ("n_order", C.c_int32),
+                ("order", C.POINTER(C.c_int32))]
+
+
+class qgm_plan_info(C.Structure):
+    _fields_ = [("order_kind", C.c_int32), ("n_free", C.c_int32), ("max_clique", C.c_int32),
+                ("n_steps", C.c_int32), ("n_slice_vars", C.c_int32), ("batch_padded", C.c_int32),
+                ("n_slices", C.c_int64), ("max_tensor_entries", C.c_int64),
+                ("workspace_bytes", C.c_int64), ("arena_bytes", C.c_int64),
+                ("bytes_per_slice", C.c_double), ("flops_per_slice", C.c_double),
+                ("max_step_bytes", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_P = C.c_void_p
+_I64P = C.POINTER(C.c_int64)
+_I32P = C.POINTER(C.c_int32)
+
+# name -> (argtypes); every function returns int status unless listed in _VOID
+_SIGS = {
+    "qgm_circuit_grid": [C.c_int, C.c_int, C.c_int, C.c_uint64, C.c_int, C.POINTER(_P)],
+    "qgm_circuit_from_gates": [C.c_int, C.POINTER(qgm_gate), C.c_int64, C.POINTER(_P)],
+    "qgm_circuit_gates": [_P, C.POINTER(qgm_gate), C.c_int64, _I64P],
+    "qgm_circuit_param_gates": [_P, _I32P, C.c_int64, _I64P],
+    "qgm_circuit_free": [_P],
+    "qgm_build_model": [_P, C.POINTER(_P)],
+    "qgm_model_get_info": [_P, C.POINTER(qgm_model_info)],
+    "qgm_model_vars": [_P, _I32P, _I32P],
+    "qgm_model_factors": [_P, _I32P, _I32P],
+    "qgm_model_free": [_P],
+    "qgm_plan_order": [_P, C.POINTER(qgm_plan_opts), C.POINTER(_P)],
+    "qgm_plan_get_info": [_P, C.POINTER(qgm_plan_info)],
+    "qgm_plan_get_order": [_P, _I32P, C.c_int64, _I64P],
+    "qgm_plan_get_slice_vars": [_P, _I32P, C.c_int64, _I64P],
+    "qgm_plan_get_steps": [_P, _I32P, _I32P, _I32P, _I32P, C.c_int64],
+    "qgm_plan_get_step_cost": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64],
+    "qgm_plan_profile": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), _P],
+    "qgm_plan_free": [_P],
+    "qgm_plan_bind": [_P, _P, C.c_size_t, _P],
+    "qgm_amplitudes": [_P, _P, C.c_int64, _P, _P],
+    "qgm_amplitudes_host": [_P, _P, C.c_int64, _P, _P],
+    "qgm_eliminate": [_P, _P, _P],
+    "qgm_status": [_P, _P],
+    "qgm_amplitude_grad": [_P, _P, C.c_int64, _P, _P, _P, _P],
+    "qgm_last_error": [],
+}
+_VOID = {"qgm_circuit_free", "qgm_model_free", "qgm_plan_free"}
+
+_lib = None
+
+
+def lib():
+    """Load libqgm.so (build it first with paper_1712_05384_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libqgm.so not built ({LIB_PATH}); run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = None if name in _VOID else (C.c_char_p if name == "qgm_last_error" else C.c_int)
+        _lib = L
+    return _lib
+
+
+class QgmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def check(rc):
+    if rc != QGM_OK:
+        raise QgmError(rc, lib().qgm_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+# ----------------------------------------------------------------- objects
+class Circuit:
+    def __init__(self, handle):
+        self._h = handle
+
+    @classmethod
+    def grid(cls, rows, cols, depth, seed=0, param=False):
+        h = _P()
+        check(lib().qgm_circuit_grid(rows, cols, depth, seed, int(param), C.byref(h)))
+        return cls(h)
+
+    @classmethod
+    def from_gates(cls, n, gates):
+        arr = (qgm_gate * max(len(gates), 1))()
+        for i, g in enumerate(gates):
+            arr[i] = qgm_gate(int(g.kind), int(g.cycle), int(g.q0), int(g.q1), float(g.theta),
+                              float(g.phi))
+        h = _P()
+        check(lib().qgm_circuit_from_gates(n, arr, len(gates), C.byref(h)))
+        return cls(h)
+
+    def gates(self):
+        n = C.c_int64()
+        check(lib().qgm_circuit_gates(self._h, None, 0, C.byref(n)))
+        arr = (qgm_gate * max(n.value, 1))()
+        check(lib().qgm_circuit_gates(self._h, arr, n.value, C.byref(n)))
+        return [(g.kind, g.cycle, g.q0, g.q1, g.theta, g.phi) for g in arr[: n.value]]
+
+    def param_gates(self):
+        n = C.c_int64()
+        check(lib().qgm_circuit_param_gates(self._h, None, 0, C.byref(n)))
+        a = np.zeros(max(n.value, 1), dtype=np.int32)
+        check(lib().qgm_circuit_param_gates(self._h, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
+        return a[: n.value]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qgm_circuit_free(self._h)
+            self._h = None
+
+
+class Model:
+    def __init__(self, circuit: Circuit):
+        self.circuit = circuit
+        self._h = _P()
+        check(lib().qgm_build_model(circuit._h, C.byref(self._h)))
+        self.info = qgm_model_info()
+        check(lib().qgm_model_get_info(self._h, C.byref(self.info)))
+
+    def vars(self):
+        nv = self.info.n_vars
+        q = np.zeros(nv, dtype=np.int32)
+        k = np.zeros(nv, dtype=np.int32)
+        check(lib().qgm_model_vars(self._h, q.ctypes.data_as(_I32P), k.ctypes.data_as(_I32P)))
+        return q, k
+
+    def factors(self):
+        nf = self.info.n_factors
+        nv = np.zeros(nf, dtype=np.int32)
+        sc = np.zeros(2 * nf, dtype=np.int32)
+        check(lib().qgm_model_factors(self._h, nv.ctypes.data_as(_I32P), sc.ctypes.data_as(_I32P)))
+        return [tuple(sc[2 * f: 2 * f + nv[f]]) for f in range(nf)]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qgm_model_free(self._h)
+            self._h = None
+
+
+class Plan:
+    def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
+                 mem_budget_bytes=0, max_fuse=0, order=None):
+        self.model = model
+        o = qgm_plan_opts()
+        o.order_kind = order_kind
+        o.output_mode = output_mode
+        o.batch = batch
+        o.mem_budget_bytes = mem_budget_bytes
+        o.max_fuse = max_fuse
+        self._order_buf = None
+        if order is not None:
+            self._order_buf = np.ascontiguousarray(order, dtype=np.int32)
+            o.order = self._order_buf.ctypes.data_as(_I32P)
+            o.n_order = len(self._order_buf)
+            o.order_kind = ORDER_GIVEN
+        self._h = _P()
+        check(lib().qgm_plan_order(model._h, C.byref(o), C.byref(self._h)))
+        self.info = qgm_plan_info()
+        check(lib().qgm_plan_get_info(self._h, C.byref(self.info)))
+        self.batch = batch
+        self.output_mode = output_mode
+        self._ws = None
+
+    def order(self):
+        n = C.c_int64()
+        check(lib().qgm_plan_get_order(self._h, None, 0, C.byref(n)))
+        a = np.zeros(max(n.value, 1), dtype=np.int32)
+        check(lib().qgm_plan_get_order(self._h, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
+        return a[: n.value]
+
+    def slice_vars(self):
+        n = C.c_int64()
+        check(lib().qgm_plan_get_slice_vars(self._h, None, 0, C.byref(n)))
+        a = np.zeros(max(n.value, 1), dtype=np.int32)
+        check(lib().qgm_plan_get_slice_vars(self._h, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
+        return a[: n.value]
+
+    def steps(self):
+        n = self.info.n_steps
+        arrs = [np.zeros(max(n, 1), dtype=np.int32) for _ in range(4)]
+        check(lib().qgm_plan_get_steps(self._h, *[a.ctypes.data_as(_I32P) for a in arrs], n))
+        return {k: a[:n] for k, a in zip(("out_rank", "k", "n_in", "batched"), arrs)}
+
+    def step_costs(self):
+        n = self.info.n_steps
+        b = np.zeros(max(n, 1))
+        f = np.zeros(max(n, 1))
+        check(lib().qgm_plan_get_step_cost(self._h, b.ctypes.data_as(C.POINTER(C.c_double)),
+                                           f.ctypes.data_as(C.POINTER(C.c_double)), n))
+        return b[:n], f[:n]
+
+    # ------------------------------------------------------------ device
+    def bind(self, workspace=None, stream=None):
+        """Bind a device workspace (a uint8 torch tensor); allocated here if None."""
+        import torch
+        if workspace is None:
+            workspace = torch.empty(self.info.workspace_bytes + 256, dtype=torch.uint8,
+                                    device="cuda")
+            off = (-workspace.data_ptr()) % 256
+            workspace = workspace[off:]
+        check(lib().qgm_plan_bind(self._h, workspace.data_ptr(), workspace.numel(), _stream(stream)))
+        self._ws = workspace
+        return self
+
+    def amplitudes(self, d_bits, d_out, B=None, stream=None):
+        B = d_bits.numel() if B is None else B
+        check(lib().qgm_amplitudes(self._h, _ptr(d_bits), B, _ptr(d_out), _stream(stream)))
+        return d_out
+
+    def amplitudes_host(self, bits: np.ndarray, stream=None) -> np.ndarray:
+        bits = np.ascontiguousarray(bits, dtype=np.uint64)
+        out = np.zeros(2 * len(bits), dtype=np.float64)
+        check(lib().qgm_amplitudes_host(self._h, bits.ctypes.data, len(bits), out.ctypes.data,
+                                        _stream(stream)))
+        return out[0::2] + 1j * out[1::2]
+
+    def eliminate(self, d_out, stream=None):
+        check(lib().qgm_eliminate(self._h, _ptr(d_out), _stream(stream)))
+        return d_out
+
+    def profile(self, d_bits, d_out, B=None, stream=None):
+        """Per-kernel milliseconds of one slice: [leaves, step 0..n-1, accumulate]."""
+        B = d_bits.numel() if B is None else B
+        ms = np.zeros(self.info.n_steps + 2, dtype=np.float32)
+        check(lib().qgm_plan_profile(self._h, _ptr(d_bits), B, _ptr(d_out),
+                                     ms.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
+        return ms
+
+    def status(self, stream=None):
+        return lib().qgm_status(self._h, _stream(stream))
+
+    def amplitude_grad(self, d_bits, d_dL_dconja, d_grad, d_amp=None, B=None, stream=None):
+        B = d_bits.numel() if B is None else B
+        check(lib().qgm_amplitude_grad(self._h, _ptr(d_bits), B, _ptr(d_dL_dconja), _ptr(d_grad),
+                                       _ptr(d_amp), _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qgm_plan_free(self._h)
+            self._h = None

@@ -1,0 +1,540 @@
+// Device execution of an elimination plan on sm_103a.
+//
+// Every tensor is a complex function of Boolean variables kept sorted by
+// elimination position, the earliest variable in the most significant index
+// bit (the paper's App. A invariant: indexes ordered low to high, sum over the
+// first axis).  A tensor that depends on the output bitstring carries a batch
+// axis beta as its innermost, contiguous dimension: row r holds the values of
+// all batch entries for variable assignment r.  One elimination step of
+// Eq. par_sum (a bucket of App. A, possibly several consecutive buckets fused)
+// is
+//
+//     out[j][beta] = sum_{e in {0,1}^k} prod_i F_i[pext(e.j, mask_i)][beta]
+//
+// where e.j is the union index (summed variables on top) and pext drops the
+// bits of variables F_i does not hold.  Because beta is innermost, every load
+// of a batched operand is a coalesced 128-bit load of two complex64 values,
+// whatever the variable order; gate factors without beta are tiny and hit L1.
+//
+// Amplitudes shrink like 2^{-n/2} and intermediate sums grow with the number
+// of paths, so each intermediate tensor carries a power-of-two exponent: the
+// producing kernel records max(|re|,|im|) over the tensor; the consuming
+// kernel scales that operand by 2^{-e} (exact) with e = floor(log2 max) + 1
+// and adds e to the exponent it passes on.  Partial amplitudes of the slices
+// are summed in FP64 with their exponents applied.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "host.h"
+
+using namespace qgm;
+
+namespace {
+
+struct Header {
+  int32_t status;    // QGM_OK or a QGM_ERR_* code raised on the device
+  int32_t slice_id;  // slice being computed
+  int32_t pad[62];
+};
+
+struct Meta {
+  uint32_t maxbits;  // float bits of max(|re|, |im|) over the tensor (>= 0)
+  int32_t exp;       // the tensor's values are multiplied by 2^exp
+};
+
+constexpr int STEP_THREADS = 128;
+
+__device__ __forceinline__ uint64_t pext_runs(uint64_t f, const InDesc &d) {
+  uint64_t r = 0;
+#pragma unroll 1
+  for (int q = 0; q < d.nruns; ++q)
+    r |= ((f >> d.src[q]) & ((1ull << d.len[q]) - 1ull)) << d.dst[q];
+  return r;
+}
+
+// Power-of-two rescale of an operand from its recorded maximum.  For a normal
+// maximum with biased exponent E, max in [2^(E-127), 2^(E-126)), so
+// e = E - 126 puts the scaled maximum in [0.5, 1).
+__device__ __forceinline__ void operand_scale(const Meta *meta, int slot, Header *hdr, float *scale,
+                                              int *e_out) {
+  if (slot < 0) {
+    *scale = 1.f;
+    *e_out = 0;
+    return;
+  }
+  uint32_t bits = meta[slot].maxbits;
+  int E = (int)((bits >> 23) & 0xff);
+  if (E == 0xff) {
+    if (hdr) atomicCAS(&hdr->status, 0, QGM_ERR_NONFINITE);
+    *scale = 1.f;
+    *e_out = 0;
+    return;
+  }
+  if (E == 0) {  // zero (or a subnormal maximum): leave as is
+    *scale = 1.f;
+    *e_out = 0;
+    return;
+  }
+  int e = E - 126;
+  if (e > 126) e = 126;
+  *scale = __int_as_float((127 - e) << 23);
+  *e_out = e;
+}
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+__device__ __forceinline__ float absmax2(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+
+// Block-wide max of non-negative floats, then one atomicMax on the slot
+// (non-negative IEEE floats order like their unsigned bit patterns).
+__device__ __forceinline__ void record_max(float v, Meta *meta, int slot) {
+  __shared__ float red[32];
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    v = lane < nw ? red[lane] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0 && v > 0.f) atomicMax(&meta[slot].maxbits, __float_as_uint(v));
+  }
+}
+
+// Leaf factors for the current slice and batch: base table entry chosen by
+// the leaf's internal row, the slice bits and the output bits of x_beta.
+// One block per leaf; block 0 also clears the intermediate metadata.
+__global__ void k_build_leaves(char *ws, const LeafDesc *leaves, int n_leaves, Meta *meta,
+                               int n_meta, const Header *hdr, const uint64_t *bits, int64_t B,
+                               int Bp) {
+  const int li = blockIdx.x;
+  if (li == 0)
+    for (int i = threadIdx.x; i < n_meta; i += blockDim.x) {
+      meta[i].maxbits = 0;
+      meta[i].exp = 0;
+    }
+  if (li >= n_leaves) return;
+  const LeafDesc d = leaves[li];
+  const int slice = hdr->slice_id;
+  int sbits = 0;
+  for (int a = 0; a < d.n_slice; ++a) sbits |= ((slice >> d.slice_bit[a]) & 1) << (d.n_slice - 1 - a);
+  const float2 *base = reinterpret_cast<const float2 *>(ws + d.base_off);
+  float2 *out = reinterpret_cast<float2 *>(ws + d.out_off);
+  const int rows = 1 << d.n_int;
+  const int width = d.batched ? Bp : 1;
+  for (int t = threadIdx.x; t < rows * width; t += blockDim.x) {
+    const int r = t / width, b = t - r * width;
+    int obits = 0;
+    if (d.n_out > 0) {
+      const uint64_t x = (b < B) ? bits[b] : 0ull;
+      for (int a = 0; a < d.n_out; ++a)
+        obits |= (int)((x >> d.out_qubit[a]) & 1ull) << (d.n_out - 1 - a);
+    }
+    const int idx = (((r << d.n_slice) | sbits) << d.n_out) | obits;
+    out[t] = base[idx];
+  }
+}
+
+// Product-sum step, batched output: thread = (row j, pair of batch entries).
+__global__ void __launch_bounds__(STEP_THREADS)
+    k_step_batched(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp) {
+  const int bp = (blockIdx.x * STEP_THREADS + threadIdx.x) * 2;
+  const bool active = bp < Bp;
+  float scale[MAXIN];
+  int esum = 0;
+#pragma unroll
+  for (int i = 0; i < MAXIN; ++i) {
+    if (i < d.m) {
+      int e;
+      operand_scale(meta, d.in[i].meta, hdr, &scale[i], &e);
+      esum += e + (d.in[i].meta >= 0 ? meta[d.in[i].meta].exp : 0);
+    }
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) meta[d.out_meta].exp = esum;
+  const uint64_t rows = 1ull << d.w_out;
+  const uint64_t terms = 1ull << d.k;
+  float lmax = 0.f;
+  float2 *out = reinterpret_cast<float2 *>(ws + d.out_off);
+  for (uint64_t j = blockIdx.y; j < rows; j += gridDim.y) {
+    if (!active) continue;
+    float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+    for (uint64_t e = 0; e < terms; ++e) {
+      const uint64_t f = (e << d.w_out) | j;
+      float2 p0 = make_float2(1.f, 0.f), p1 = p0;
+#pragma unroll
+      for (int i = 0; i < MAXIN; ++i) {
+        if (i < d.m) {
+          const InDesc &in = d.in[i];
+          const uint64_t idx = pext_runs(f, in);
+          if (in.batched) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(ws + in.off) +
+                                   ((idx * (uint64_t)Bp + bp) >> 1));
+            p0 = cmul(p0, make_float2(v.x * scale[i], v.y * scale[i]));
+            p1 = cmul(p1, make_float2(v.z * scale[i], v.w * scale[i]));
+          } else {
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(ws + in.off) + idx);
+            const float2 s = make_float2(v.x * scale[i], v.y * scale[i]);
+            p0 = cmul(p0, s);
+            p1 = cmul(p1, s);
+          }
+        }
+      }
+      a0.x += p0.x; a0.y += p0.y;
+      a1.x += p1.x; a1.y += p1.y;
+    }
+    reinterpret_cast<float4 *>(out)[(j * (uint64_t)Bp + bp) >> 1] = make_float4(a0.x, a0.y, a1.x, a1.y);
+    lmax = fmaxf(lmax, fmaxf(absmax2(a0), absmax2(a1)));
+  }
+  record_max(lmax, meta, d.out_meta);
+}
+
+// Product-sum step without a batch axis: thread = output entry j.
+__global__ void __launch_bounds__(256)
+    k_step_plain(char *ws, const StepDesc d, Meta *meta, Header *hdr) {
+  float scale[MAXIN];
+  int esum = 0;
+#pragma unroll
+  for (int i = 0; i < MAXIN; ++i) {
+    if (i < d.m) {
+      int e;
+      operand_scale(meta, d.in[i].meta, hdr, &scale[i], &e);
+      esum += e + (d.in[i].meta >= 0 ? meta[d.in[i].meta].exp : 0);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) meta[d.out_meta].exp = esum;
+  const uint64_t rows = 1ull << d.w_out;
+  const uint64_t terms = 1ull << d.k;
+  float lmax = 0.f;
+  float2 *out = reinterpret_cast<float2 *>(ws + d.out_off);
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < rows;
+       j += (uint64_t)gridDim.x * blockDim.x) {
+    float2 a = make_float2(0.f, 0.f);
+    for (uint64_t e = 0; e < terms; ++e) {
+      const uint64_t f = (e << d.w_out) | j;
+      float2 p = make_float2(1.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < MAXIN; ++i) {
+        if (i < d.m) {
+          const float2 v =
+              __ldg(reinterpret_cast<const float2 *>(ws + d.in[i].off) + pext_runs(f, d.in[i]));
+          p = cmul(p, make_float2(v.x * scale[i], v.y * scale[i]));
+        }
+      }
+      a.x += p.x;
+      a.y += p.y;
+    }
+    out[j] = a;
+    lmax = fmaxf(lmax, absmax2(a));
+  }
+  record_max(lmax, meta, d.out_meta);
+}
+
+// out[x] += F[x] * 2^exp * c in FP64 (one slice's partial amplitudes), then
+// advance the slice counter.
+__global__ void k_accumulate(const char *ws, int64_t final_off, int final_meta, int final_batched,
+                             int open_mode, int64_t n_out, double2 *out, const Meta *meta,
+                             Header *hdr, double c_re, double c_im) {
+  const float2 *F = reinterpret_cast<const float2 *>(ws + final_off);
+  const int e = final_meta >= 0 ? meta[final_meta].exp : 0;
+  const double s = ldexp(1.0, e);
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_out;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    // open outputs: x is the row of the final tensor; a batch: x is the
+    // batch entry of its single row (a final tensor without a batch axis is
+    // the same for every entry)
+    const int64_t src = open_mode ? x : (final_batched ? x : 0);
+    const float2 v = F[src];
+    const double re = (double)v.x * s, im = (double)v.y * s;
+    double2 o = out[x];
+    o.x += re * c_re - im * c_im;
+    o.y += re * c_im + im * c_re;
+    out[x] = o;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    __threadfence();
+    hdr->slice_id += 1;
+  }
+}
+
+// Zero the FP64 result and the status, restart at slice 0.
+__global__ void k_init(double2 *out, int64_t n_out, Header *hdr) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_out;
+       x += (int64_t)gridDim.x * blockDim.x)
+    out[x] = make_double2(0.0, 0.0);
+  if (blockIdx.x == 0 && threadIdx.x == 0) hdr->slice_id = 0;
+}
+
+}  // namespace
+
+struct qgm_exec_state {
+  int device = -1;
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaGraphExec_t graph = nullptr;
+  const void *g_bits = nullptr;
+  void *g_out = nullptr;
+  int64_t g_B = -1;
+  int sms = 148;
+};
+
+static int cuda_fail(cudaError_t e, const char *what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return QGM_ERR_CUDA;
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+extern "C" void qgm_exec_release(qgm_plan *p) {
+  if (!p || !p->exec) return;
+  if (p->exec->graph) cudaGraphExecDestroy(p->exec->graph);
+  delete p->exec;
+  p->exec = nullptr;
+}
+
+static void launch_leaves(qgm_plan *p, const uint64_t *d_bits, int64_t B, cudaStream_t st) {
+  char *ws = p->exec->ws;
+  const int nl = (int)p->leafdesc.size();
+  k_build_leaves<<<std::max(nl, 1), 256, 0, st>>>(
+      ws, reinterpret_cast<const LeafDesc *>(ws + p->off_leafdesc), nl,
+      reinterpret_cast<Meta *>(ws + p->off_meta), p->n_meta,
+      reinterpret_cast<Header *>(ws + p->off_header), d_bits, B, p->Bp);
+}
+
+static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st) {
+  qgm_exec_state *x = p->exec;
+  char *ws = x->ws;
+  Meta *meta = reinterpret_cast<Meta *>(ws + p->off_meta);
+  Header *hdr = reinterpret_cast<Header *>(ws + p->off_header);
+  const uint64_t rows = 1ull << d.w_out;
+  if (d.batched_out) {
+    const int bx = (p->Bp / 2 + STEP_THREADS - 1) / STEP_THREADS;
+    const uint64_t cap = (uint64_t)std::max(1, x->sms * 16 / bx);
+    dim3 grid(bx, (unsigned)std::min<uint64_t>(rows, std::min<uint64_t>(cap, 65535)));
+    k_step_batched<<<grid, STEP_THREADS, 0, st>>>(ws, d, meta, hdr, p->Bp);
+  } else {
+    const uint64_t blocks = (rows + 255) / 256;
+    k_step_plain<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)x->sms * 8), 256, 0, st>>>(ws, d, meta, hdr);
+  }
+}
+
+static void launch_accumulate(qgm_plan *p, double2 *d_out, int64_t n_out, cudaStream_t st) {
+  char *ws = p->exec->ws;
+  const int64_t blocks = std::min<int64_t>((n_out + 255) / 256, (int64_t)p->exec->sms * 8);
+  // the fixed-gate tables had 2^{-1/2} pulled out half_pow_total times
+  const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
+  k_accumulate<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(
+      ws, p->final_off, p->final_meta, p->final_batched, p->output_mode == QGM_OUT_OPEN ? 1 : 0,
+      n_out, d_out, reinterpret_cast<const Meta *>(ws + p->off_meta),
+      reinterpret_cast<Header *>(ws + p->off_header), c.real(), c.imag());
+}
+
+// Enqueue one slice: leaves, steps, accumulation.
+static int enqueue_slice(qgm_plan *p, const uint64_t *d_bits, int64_t B, double2 *d_out,
+                         int64_t n_out, cudaStream_t st) {
+  launch_leaves(p, d_bits, B, st);
+  for (const StepDesc &d : p->steps) launch_step(p, d, st);
+  launch_accumulate(p, d_out, n_out, st);
+  return QGM_OK;
+}
+
+static int run(qgm_plan *p, const uint64_t *d_bits, int64_t B, double2 *d_out, int64_t n_out,
+               cudaStream_t st) {
+  qgm_exec_state *x = p->exec;
+  Header *hdr = reinterpret_cast<Header *>(x->ws + p->off_header);
+  const int64_t nslices = (int64_t)1 << p->slice_vars.size();
+  if (!x->graph || x->g_bits != d_bits || x->g_out != d_out || x->g_B != B) {
+    if (x->graph) {
+      cudaGraphExecDestroy(x->graph);
+      x->graph = nullptr;
+    }
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      enqueue_slice(p, d_bits, B, d_out, n_out, cs);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+    e = cudaGraphInstantiate(&x->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    x->g_bits = d_bits;
+    x->g_out = d_out;
+    x->g_B = B;
+  }
+  const int64_t iblocks = std::min<int64_t>((n_out + 255) / 256, (int64_t)x->sms * 4);
+  k_init<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(d_out, n_out, hdr);
+  CK(cudaGetLastError());
+  for (int64_t s = 0; s < nslices; ++s) CK(cudaGraphLaunch(x->graph, st));
+  return QGM_OK;
+}
+
+static int check_bound(qgm_plan *p, const char *fn) {
+  if (!p) {
+    set_error("%s: null plan", fn);
+    return QGM_ERR_ARG;
+  }
+  if (!p->exec || !p->exec->ws) {
+    set_error("%s: no workspace bound (call qgm_plan_bind first)", fn);
+    return QGM_ERR_ARG;
+  }
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != p->exec->device) {
+    set_error("%s: current device %d differs from the bound device %d", fn, dev, p->exec->device);
+    return QGM_ERR_ARG;
+  }
+  return QGM_OK;
+}
+
+extern "C" {
+
+int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream) {
+  if (!p || !d_workspace) {
+    set_error("qgm_plan_bind: null argument");
+    return QGM_ERR_ARG;
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    set_error("qgm_plan_bind: no CUDA device");
+    return QGM_ERR_NOGPU;
+  }
+  if (((uintptr_t)d_workspace & 255) != 0) {
+    set_error("qgm_plan_bind: workspace must be 256-byte aligned");
+    return QGM_ERR_ARG;
+  }
+  if ((int64_t)ws_bytes < p->ws_bytes) {
+    set_error("qgm_plan_bind: workspace of %zu bytes, the plan needs %lld", ws_bytes,
+              (long long)p->ws_bytes);
+    return QGM_ERR_OOM;
+  }
+  qgm_exec_release(p);
+  p->exec = new qgm_exec_state;
+  qgm_exec_state *x = p->exec;
+  CK(cudaGetDevice(&x->device));
+  CK(cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, x->device));
+  x->ws = static_cast<char *>(d_workspace);
+  x->ws_bytes = ws_bytes;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaMemsetAsync(x->ws + p->off_header, 0, 256, st));
+  if (!p->base_tables.empty())
+    CK(cudaMemcpyAsync(x->ws + p->off_base, p->base_tables.data(), p->base_tables.size() * sizeof(float),
+                       cudaMemcpyHostToDevice, st));
+  if (!p->leafdesc.empty())
+    CK(cudaMemcpyAsync(x->ws + p->off_leafdesc, p->leafdesc.data(), p->leafdesc.size() * sizeof(LeafDesc),
+                       cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return QGM_OK;
+}
+
+int qgm_amplitudes(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out, void *stream) {
+  int rc = check_bound(p, "qgm_amplitudes");
+  if (rc) return rc;
+  if (p->output_mode != QGM_OUT_BATCH) {
+    set_error("qgm_amplitudes: plan has open outputs (use qgm_eliminate)");
+    return QGM_ERR_ARG;
+  }
+  if (B < 1 || B > p->batch || !d_bitstrings || !d_out) {
+    set_error("qgm_amplitudes: need 1 <= B <= %lld and non-null buffers", (long long)p->batch);
+    return QGM_ERR_ARG;
+  }
+  return run(p, d_bitstrings, B, reinterpret_cast<double2 *>(d_out), B, static_cast<cudaStream_t>(stream));
+}
+
+int qgm_amplitudes_host(qgm_plan *p, const uint64_t *h_bitstrings, int64_t B, double *h_out,
+                        void *stream) {
+  int rc = check_bound(p, "qgm_amplitudes_host");
+  if (rc) return rc;
+  if (p->output_mode != QGM_OUT_BATCH || B < 1 || B > p->batch || !h_bitstrings || !h_out) {
+    set_error("qgm_amplitudes_host: need a batch plan, 1 <= B <= %lld and non-null buffers",
+              (long long)p->batch);
+    return QGM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint64_t *d_bits = reinterpret_cast<uint64_t *>(p->exec->ws + p->off_bits);
+  double2 *d_out = reinterpret_cast<double2 *>(p->exec->ws + p->off_outstage);
+  CK(cudaMemcpyAsync(d_bits, h_bitstrings, B * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
+  rc = run(p, d_bits, B, d_out, B, st);
+  if (rc) return rc;
+  CK(cudaMemcpyAsync(h_out, d_out, B * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return QGM_OK;
+}
+
+int qgm_eliminate(qgm_plan *p, double *d_out, void *stream) {
+  int rc = check_bound(p, "qgm_eliminate");
+  if (rc) return rc;
+  if (p->output_mode != QGM_OUT_OPEN || !d_out) {
+    set_error("qgm_eliminate: needs a plan with open outputs and a non-null output");
+    return QGM_ERR_ARG;
+  }
+  uint64_t *d_bits = reinterpret_cast<uint64_t *>(p->exec->ws + p->off_bits);
+  return run(p, d_bits, 1, reinterpret_cast<double2 *>(d_out), p->final_entries,
+             static_cast<cudaStream_t>(stream));
+}
+
+int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out, float *ms,
+                     void *stream) {
+  int rc = check_bound(p, "qgm_plan_profile");
+  if (rc) return rc;
+  if (p->output_mode != QGM_OUT_BATCH || B < 1 || B > p->batch || !d_bitstrings || !d_out || !ms) {
+    set_error("qgm_plan_profile: need a batch plan, 1 <= B <= %lld and non-null buffers",
+              (long long)p->batch);
+    return QGM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int n = (int)p->steps.size() + 2;
+  std::vector<cudaEvent_t> ev(n + 1);
+  for (auto &e : ev) CK(cudaEventCreate(&e));
+  Header *hdr = reinterpret_cast<Header *>(p->exec->ws + p->off_header);
+  k_init<<<1, 256, 0, st>>>(reinterpret_cast<double2 *>(d_out), B, hdr);
+  CK(cudaEventRecord(ev[0], st));
+  launch_leaves(p, d_bitstrings, B, st);
+  CK(cudaEventRecord(ev[1], st));
+  for (size_t s = 0; s < p->steps.size(); ++s) {
+    launch_step(p, p->steps[s], st);
+    CK(cudaEventRecord(ev[2 + s], st));
+  }
+  launch_accumulate(p, reinterpret_cast<double2 *>(d_out), B, st);
+  CK(cudaEventRecord(ev[n], st));
+  CK(cudaGetLastError());
+  CK(cudaEventSynchronize(ev[n]));
+  for (int i = 0; i < n; ++i) CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
+  for (auto &e : ev) cudaEventDestroy(e);
+  return QGM_OK;
+}
+
+int qgm_status(qgm_plan *p, void *stream) {
+  int rc = check_bound(p, "qgm_status");
+  if (rc) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int32_t s = 0;
+  CK(cudaMemcpyAsync(&s, p->exec->ws + p->off_header, sizeof s, cudaMemcpyDeviceToHost, st));
+  CK(cudaMemsetAsync(p->exec->ws + p->off_header, 0, sizeof s, st));
+  CK(cudaStreamSynchronize(st));
+  return s;
+}
+
+int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, const double *d_dL_dconja,
+                       double *d_grad, double *d_amp, void *stream) {
+  (void)d_bitstrings; (void)B; (void)d_dL_dconja; (void)d_grad; (void)d_amp; (void)stream;
+  int rc = check_bound(p, "qgm_amplitude_grad");
+  if (rc) return rc;
+  set_error("qgm_amplitude_grad: not built yet");
+  return QGM_ERR_ARG;
+}
+
+}  // extern "C"

@@ -1,0 +1,1082 @@
+// Host side of the amplitude engine: random grid circuits, the complex
+// graphical model (paper Sec. III), elimination orders, slicing and the step
+// list of bucket elimination (Sec. IV, App. A), and the device layout the
+// kernels in exec.cu consume.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+
+#include "host.h"
+
+namespace qgm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char *fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+// ---------------------------------------------------------------- circuit
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): golden-ratio increment and
+// two xor-shift-multiply rounds.
+struct SplitMix64 {
+  uint64_t s;
+  explicit SplitMix64(uint64_t seed) : s(seed) {}
+  uint64_t next() {
+    s += 0x9E3779B97F4A7C15ULL;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+  double uniform() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); }
+};
+
+// The 8 CZ layers [HZ0, HZ2, VT0, VT2, HZ1, HZ3, VT1, VT3]: HZ_o pairs
+// (r,c)-(r,c+1) when c = o + 2(r mod 2) (mod 4); VT_o pairs (r,c)-(r+1,c)
+// when r = o + 2(c mod 2) (mod 4).
+static std::vector<std::vector<std::pair<int, int>>> cz_patterns(int rows, int cols) {
+  auto hz = [&](int o) {
+    std::vector<std::pair<int, int>> v;
+    for (int r = 0; r < rows; ++r)
+      for (int c = 0; c + 1 < cols; ++c)
+        if (c % 4 == (o + 2 * (r % 2)) % 4) v.push_back({r * cols + c, r * cols + c + 1});
+    return v;
+  };
+  auto vt = [&](int o) {
+    std::vector<std::pair<int, int>> v;
+    for (int r = 0; r + 1 < rows; ++r)
+      for (int c = 0; c < cols; ++c)
+        if (r % 4 == (o + 2 * (c % 2)) % 4) v.push_back({r * cols + c, (r + 1) * cols + c});
+    return v;
+  };
+  return {hz(0), hz(2), vt(0), vt(2), hz(1), hz(3), vt(1), vt(3)};
+}
+
+static Circuit grid_circuit(int rows, int cols, int depth, uint64_t seed, int param) {
+  Circuit c;
+  c.n = rows * cols;
+  c.rows = rows;
+  c.cols = cols;
+  c.depth = depth;
+  c.seed = seed;
+  c.param = param;
+  const int n = c.n;
+  auto pats = cz_patterns(rows, cols);
+  SplitMix64 rng(seed);
+  for (int q = 0; q < n; ++q) c.gates.push_back({QGM_GATE_H, 0, q, -1, 0.0, 0.0});
+  std::vector<char> prev(n, 0), had_t(n, 0);
+  for (int t = 1; t < depth; ++t) {
+    std::vector<char> in_cz(n, 0);
+    for (auto &pr : pats[(t - 1) % 8]) {
+      c.gates.push_back({QGM_GATE_CZ, t, pr.first, pr.second, 0.0, 0.0});
+      in_cz[pr.first] = in_cz[pr.second] = 1;
+    }
+    for (int q = 0; q < n; ++q) {
+      if (!(prev[q] && !in_cz[q])) continue;
+      if (!had_t[q]) {
+        had_t[q] = 1;
+        c.gates.push_back({QGM_GATE_T, t, q, -1, 0.0, 0.0});
+      } else if (param) {
+        double th = M_PI * rng.uniform();
+        double ph = 2.0 * M_PI * rng.uniform();
+        c.param_gates.push_back((int)c.gates.size());
+        c.gates.push_back({QGM_GATE_RXY, t, q, -1, th, ph});
+      } else {
+        uint64_t r = rng.next();
+        c.gates.push_back({(r >> 63) == 0 ? QGM_GATE_X12 : QGM_GATE_Y12, t, q, -1, 0.0, 0.0});
+      }
+    }
+    prev = in_cz;
+  }
+  return c;
+}
+
+// ------------------------------------------------------------------ model
+// psi_U(b', b) = <b'|U|b>; the non-diagonal fixed gates are stored with the
+// common 2^{-1/2} pulled out (entries in {+-1, +-i}), tracked by half_pow.
+static void gate_table(const qgm_gate &g, cd t[4], int *half_pow) {
+  const cd I(0.0, 1.0);
+  *half_pow = 0;
+  switch (g.kind) {
+    case QGM_GATE_H: t[0] = 1; t[1] = 1; t[2] = 1; t[3] = -1; *half_pow = 1; break;
+    case QGM_GATE_X12: t[0] = 1; t[1] = -I; t[2] = -I; t[3] = 1; *half_pow = 1; break;
+    case QGM_GATE_Y12: t[0] = 1; t[1] = -1; t[2] = 1; t[3] = 1; *half_pow = 1; break;
+    case QGM_GATE_RXY: {
+      double c = std::cos(g.theta / 2), s = std::sin(g.theta / 2);
+      t[0] = c;
+      t[1] = -I * std::exp(-I * g.phi) * s;
+      t[2] = -I * std::exp(I * g.phi) * s;
+      t[3] = c;
+      break;
+    }
+    case QGM_GATE_T: t[0] = 1; t[1] = std::exp(I * (M_PI / 4)); break;
+    case QGM_GATE_CZ: t[0] = 1; t[1] = 1; t[2] = 1; t[3] = -1; break;
+  }
+}
+
+static int build_model(const Circuit &c, Model &m) {
+  m = Model();
+  m.n = c.n;
+  m.rows = c.rows;
+  m.cols = c.cols;
+  m.gates = c.gates;
+  std::vector<int> cur(c.n);
+  for (int q = 0; q < c.n; ++q) {
+    cur[q] = q;
+    m.var_qubit.push_back(q);
+    m.var_k.push_back(0);
+    m.inputs.push_back(q);
+  }
+  int nv = c.n;
+  for (size_t gi = 0; gi < c.gates.size(); ++gi) {
+    const qgm_gate &g = c.gates[gi];
+    MFactor f;
+    f.gate = (int)gi;
+    gate_table(g, f.t, &f.half_pow);
+    if (g.kind == QGM_GATE_CZ) {
+      f.nv = 2;
+      f.v[0] = cur[g.q0];
+      f.v[1] = cur[g.q1];
+    } else if (g.kind == QGM_GATE_T) {
+      f.nv = 1;
+      f.v[0] = cur[g.q0];
+    } else {
+      int v = nv++;
+      m.var_qubit.push_back(g.q0);
+      m.var_k.push_back(m.var_k[cur[g.q0]] + 1);
+      f.nv = 2;
+      f.v[0] = v;  // b' (after the gate)
+      f.v[1] = cur[g.q0];
+      cur[g.q0] = v;
+      m.L++;
+      if (g.kind == QGM_GATE_RXY) m.param_factor.push_back((int)m.factors.size());
+    }
+    m.factors.push_back(f);
+  }
+  m.n_vars = nv;
+  m.outputs = cur;
+  return QGM_OK;
+}
+
+// ------------------------------------------------------------------- plan
+static std::vector<int> qubit_rank(int rows, int cols, bool transpose) {
+  bool colmajor = rows < cols;
+  if (transpose) colmajor = !colmajor;
+  std::vector<int> rank(rows * cols);
+  for (int q = 0; q < rows * cols; ++q) {
+    int r = q / cols, c = q % cols;
+    rank[q] = colmajor ? c * rows + r : q;
+  }
+  return rank;
+}
+
+// Table of a factor re-laid out over `scope` (C-order), given its current
+// scope and table.  `scope` must contain every variable of `from`.
+static std::vector<cd> expand_table(const std::vector<int> &from_scope, const std::vector<cd> &from,
+                                    const std::vector<int> &scope) {
+  const int r = (int)scope.size();
+  std::vector<int> where(from_scope.size());
+  for (size_t a = 0; a < from_scope.size(); ++a)
+    where[a] = (int)(std::find(scope.begin(), scope.end(), from_scope[a]) - scope.begin());
+  std::vector<cd> out((size_t)1 << r);
+  const int fr = (int)from_scope.size();
+  for (size_t i = 0; i < out.size(); ++i) {
+    size_t fi = 0;
+    for (int a = 0; a < fr; ++a) fi |= ((i >> (r - 1 - where[a])) & 1) << (fr - 1 - a);
+    out[i] = from[fi];
+  }
+  return out;
+}
+
+// Fix the input variables to 0, then merge factors with equal scopes and
+// absorb factors whose scope is a subset of another's (the product is the
+// same function; fewer, larger tables).
+static void reduce_factors(const Model &m, std::vector<LeafFactor> &leaves, cd &constant,
+                           int &half_pow_total) {
+  std::vector<char> is_in(m.n_vars, 0);
+  for (int v : m.inputs) is_in[v] = 1;
+  leaves.clear();
+  constant = 1.0;
+  half_pow_total = 0;
+  std::map<std::vector<int>, int> by_scope;
+  for (size_t fi = 0; fi < m.factors.size(); ++fi) {
+    const MFactor &f = m.factors[fi];
+    half_pow_total += f.half_pow;
+    std::vector<int> sc;
+    std::vector<cd> tab;
+    // substitute inputs = 0
+    std::vector<int> keep;
+    for (int a = 0; a < f.nv; ++a)
+      if (!is_in[f.v[a]]) keep.push_back(a);
+    for (int a : keep) sc.push_back(f.v[a]);
+    tab.assign((size_t)1 << keep.size(), 0.0);
+    for (size_t i = 0; i < tab.size(); ++i) {
+      int full = 0;
+      for (size_t b = 0; b < keep.size(); ++b)
+        if ((i >> (keep.size() - 1 - b)) & 1) full |= 1 << (f.nv - 1 - keep[b]);
+      tab[i] = f.t[full];
+    }
+    if (sc.empty()) {
+      constant *= tab[0];
+      continue;
+    }
+    // canonical: scope sorted by var id (merging two equal vars is impossible
+    // here: a two-variable factor always has two distinct variables)
+    std::vector<int> sorted = sc;
+    std::sort(sorted.begin(), sorted.end());
+    std::vector<cd> st = expand_table(sc, tab, sorted);
+    auto it = by_scope.find(sorted);
+    if (it != by_scope.end()) {
+      LeafFactor &L = leaves[it->second];
+      for (size_t i = 0; i < st.size(); ++i) L.table[i] *= st[i];
+      L.members.push_back((int)fi);
+    } else {
+      by_scope[sorted] = (int)leaves.size();
+      LeafFactor L;
+      L.scope = sorted;
+      L.table = st;
+      L.members.push_back((int)fi);
+      leaves.push_back(L);
+    }
+  }
+  // absorb proper subsets into the first superset
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (size_t a = 0; a < leaves.size() && !changed; ++a) {
+      for (size_t b = 0; b < leaves.size(); ++b) {
+        if (a == b || leaves[a].scope.size() >= leaves[b].scope.size()) continue;
+        if (!std::includes(leaves[b].scope.begin(), leaves[b].scope.end(), leaves[a].scope.begin(),
+                           leaves[a].scope.end()))
+          continue;
+        std::vector<cd> ex = expand_table(leaves[a].scope, leaves[a].table, leaves[b].scope);
+        for (size_t i = 0; i < ex.size(); ++i) leaves[b].table[i] *= ex[i];
+        leaves[b].members.insert(leaves[b].members.end(), leaves[a].members.begin(),
+                                 leaves[a].members.end());
+        leaves.erase(leaves.begin() + a);
+        changed = true;
+        break;
+      }
+    }
+  }
+}
+
+struct Graph {
+  int nv;
+  int words;
+  std::vector<uint64_t> bits;  // adjacency bitsets
+  std::vector<char> alive;
+  explicit Graph(int n) : nv(n), words((n + 63) / 64), bits((size_t)n * ((n + 63) / 64), 0), alive(n, 0) {}
+  uint64_t *row(int v) { return &bits[(size_t)v * words]; }
+  bool has(int a, int b) { return (row(a)[b >> 6] >> (b & 63)) & 1; }
+  void add(int a, int b) {
+    row(a)[b >> 6] |= 1ULL << (b & 63);
+    row(b)[a >> 6] |= 1ULL << (a & 63);
+  }
+  int degree(int v) {
+    int d = 0;
+    uint64_t *r = row(v);
+    for (int w = 0; w < words; ++w) d += __builtin_popcountll(r[w]);
+    return d;
+  }
+  std::vector<int> nbrs(int v) {
+    std::vector<int> out;
+    uint64_t *r = row(v);
+    for (int w = 0; w < words; ++w) {
+      uint64_t x = r[w];
+      while (x) {
+        int b = __builtin_ctzll(x);
+        out.push_back(w * 64 + b);
+        x &= x - 1;
+      }
+    }
+    return out;
+  }
+  // eliminate v: neighbours become a clique; returns the clique size (v + nbrs)
+  int eliminate(int v) {
+    std::vector<int> nb = nbrs(v);
+    for (size_t i = 0; i < nb.size(); ++i)
+      for (size_t j = i + 1; j < nb.size(); ++j) add(nb[i], nb[j]);
+    for (int a : nb) row(a)[v >> 6] &= ~(1ULL << (v & 63));
+    std::fill(row(v), row(v) + words, 0);
+    alive[v] = 0;
+    return 1 + (int)nb.size();
+  }
+  int fill(int v) {
+    std::vector<int> nb = nbrs(v);
+    int f = 0;
+    for (size_t i = 0; i < nb.size(); ++i)
+      for (size_t j = i + 1; j < nb.size(); ++j)
+        if (!has(nb[i], nb[j])) ++f;
+    return f;
+  }
+};
+
+// Interaction graph (Sec. III.B) on the variables in `in_graph`.
+static Graph make_graph(const qgm_plan *p, const std::vector<char> &in_graph) {
+  Graph g(p->model.n_vars);
+  for (int v = 0; v < p->model.n_vars; ++v) g.alive[v] = in_graph[v];
+  for (const LeafFactor &L : p->leaves)
+    for (size_t a = 0; a < L.scope.size(); ++a)
+      for (size_t b = a + 1; b < L.scope.size(); ++b)
+        if (in_graph[L.scope[a]] && in_graph[L.scope[b]]) g.add(L.scope[a], L.scope[b]);
+  return g;
+}
+
+// Min-fill: repeatedly eliminate the vertex adding the fewest fill edges;
+// ties by fewest neighbours, then smallest id.  Vertices in `keep` stay.
+static std::vector<int> order_minfill(Graph g, const std::vector<char> &keep) {
+  std::vector<int> order;
+  std::vector<int> fillc(g.nv, -1);
+  std::vector<char> dirty(g.nv, 1);
+  while (true) {
+    int best = -1, bf = 0, bd = 0;
+    for (int v = 0; v < g.nv; ++v) {
+      if (!g.alive[v] || keep[v]) continue;
+      if (dirty[v]) {
+        fillc[v] = g.fill(v);
+        dirty[v] = 0;
+      }
+      int f = fillc[v], d = g.degree(v);
+      if (best < 0 || f < bf || (f == bf && d < bd)) {
+        best = v;
+        bf = f;
+        bd = d;
+      }
+    }
+    if (best < 0) break;
+    // fill counts change for vertices within distance 2 of `best`
+    std::vector<int> nb = g.nbrs(best);
+    for (int a : nb) {
+      dirty[a] = 1;
+      for (int b : g.nbrs(a)) dirty[b] = 1;
+    }
+    g.eliminate(best);
+    for (int a : nb)
+      for (int b : g.nbrs(a)) dirty[b] = 1;
+    order.push_back(best);
+  }
+  return order;
+}
+
+static std::vector<int> order_vertical(const qgm_plan *p, const std::vector<char> &elim, bool transpose) {
+  const Model &m = p->model;
+  int rows = m.rows ? m.rows : 1, cols = m.rows ? m.cols : m.n;
+  std::vector<int> rank = qubit_rank(rows, cols, transpose);
+  std::vector<int> vs;
+  for (int v = 0; v < m.n_vars; ++v)
+    if (elim[v]) vs.push_back(v);
+  std::sort(vs.begin(), vs.end(), [&](int a, int b) {
+    int ra = rank[m.var_qubit[a]], rb = rank[m.var_qubit[b]];
+    if (ra != rb) return ra < rb;
+    if (m.var_k[a] != m.var_k[b]) return m.var_k[a] < m.var_k[b];
+    return a < b;
+  });
+  return vs;
+}
+
+// ---------------------------------------------------------- arena allocator
+struct Arena {
+  std::map<int64_t, int64_t> free_;  // off -> size
+  int64_t top = 0, peak = 0;
+  static int64_t align(int64_t x) { return (x + 255) & ~int64_t(255); }
+  int64_t alloc(int64_t bytes) {
+    bytes = align(std::max<int64_t>(bytes, 1));
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        int64_t off = it->first, sz = it->second;
+        free_.erase(it);
+        if (sz > bytes) free_[off + bytes] = sz - bytes;
+        return off;
+      }
+    }
+    int64_t off = top;
+    top += bytes;
+    peak = std::max(peak, top);
+    return off;
+  }
+  void release(int64_t off, int64_t bytes) {
+    bytes = align(std::max<int64_t>(bytes, 1));
+    auto it = free_.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+        it = pv;
+      }
+    }
+    if (it->first + it->second == top) {
+      top = it->first;
+      free_.erase(it);
+    }
+  }
+};
+
+// Symbolic bucket elimination (App. A) for `order` with `slice` variables
+// removed: the step list, its algorithmic bytes/flops and the arena peak.
+static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
+                          const std::vector<char> &sliced, int max_fuse, bool want_steps) {
+  const Model &m = p->model;
+  SimResult R;
+  std::vector<int> order;
+  for (int v : order_in)
+    if (!sliced[v]) order.push_back(v);
+  const int ne = (int)order.size();
+  std::vector<int> pos(m.n_vars, -1);
+  for (int i = 0; i < ne; ++i) pos[order[i]] = i;
+  // open variables after the eliminated ones, qubit n-1 first, so that the
+  // final tensor's index has qubit j at bit j
+  for (size_t i = 0; i < p->open_vars.size(); ++i) pos[p->open_vars[i]] = ne + (int)i;
+  const int64_t Bp = p->Bp;
+
+  auto entries = [&](const SymTensor &t) {
+    return ((int64_t)1 << t.vars.size()) * (t.batched ? Bp : 1);
+  };
+  std::vector<SymTensor> &T = R.tensors;
+  std::vector<std::vector<int>> bucket(ne);
+  std::vector<int> live(m.n_vars, 0);
+  std::vector<int> finals;
+  Arena arena;
+
+  auto place = [&](int id) {
+    const SymTensor &t = T[id];
+    if (t.vars.empty() || pos[t.vars[0]] >= ne)
+      finals.push_back(id);
+    else
+      bucket[pos[t.vars[0]]].push_back(id);
+    for (int v : t.vars) live[v]++;
+  };
+  for (size_t li = 0; li < p->leaves.size(); ++li) {
+    const LeafFactor &L = p->leaves[li];
+    SymTensor t;
+    t.leaf = (int)li;
+    for (int v : L.scope) {
+      int role = p->var_role[v];
+      if (role == 2) t.batched = true;
+      if (pos[v] >= 0) t.vars.push_back(v);
+    }
+    std::sort(t.vars.begin(), t.vars.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+    t.entries = entries(t);
+    T.push_back(t);
+    place((int)T.size() - 1);
+  }
+  int n_meta = 0;
+  auto emit = [&](std::vector<int> inputs, int k) -> int {
+    // union of the inputs' variables, sorted by position
+    std::vector<int> uni;
+    bool batched = false;
+    for (int id : inputs) {
+      for (int v : T[id].vars) uni.push_back(v);
+      batched |= T[id].batched;
+    }
+    std::sort(uni.begin(), uni.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+    uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+    SymTensor out;
+    out.vars.assign(uni.begin() + k, uni.end());
+    out.batched = batched;
+    out.entries = entries(out);
+    out.meta = n_meta++;
+    out.off = arena.alloc(out.entries * 8);
+    StepRec s;
+    s.inputs = inputs;
+    s.uni = uni;
+    s.k = k;
+    s.batched = batched;
+    double rb = 0;
+    for (int id : inputs) {
+      rb += (double)T[id].entries * 8;
+      for (int v : T[id].vars) live[v]--;
+      if (T[id].leaf < 0) arena.release(T[id].off, T[id].entries * 8);
+    }
+    s.bytes = rb + (double)out.entries * 8;
+    s.flops = (double)out.entries * (double)(1LL << k) * (6.0 * (inputs.size() - 1) + 2.0);
+    R.bytes += s.bytes;
+    R.flops += s.flops;
+    R.max_step_bytes = std::max(R.max_step_bytes, s.bytes);
+    R.max_entries = std::max(R.max_entries, out.entries);
+    R.max_clique = std::max(R.max_clique, (int)uni.size());
+    T.push_back(out);
+    int oid = (int)T.size() - 1;
+    s.out = oid;
+    if (want_steps) R.steps.push_back(s);
+    else R.steps.push_back(StepRec{{}, {}, k, oid, batched, s.bytes, s.flops});
+    return oid;
+  };
+  // more than MAXIN inputs: multiply the smallest ones together first
+  auto shrink = [&](std::vector<int> &inputs) {
+    while ((int)inputs.size() > MAXIN) {
+      std::stable_sort(inputs.begin(), inputs.end(),
+                       [&](int a, int b) { return T[a].entries < T[b].entries; });
+      std::vector<int> two = {inputs[0], inputs[1]};
+      inputs.erase(inputs.begin(), inputs.begin() + 2);
+      int id = emit(two, 0);
+      for (int v : T[id].vars) live[v]++;
+      inputs.push_back(id);
+    }
+  };
+  for (int pi = 0; pi < ne; ++pi) {
+    if (bucket[pi].empty()) continue;
+    std::vector<int> inputs = bucket[pi];
+    bucket[pi].clear();
+    std::vector<int> uni;
+    for (int id : inputs)
+      for (int v : T[id].vars) uni.push_back(v);
+    std::sort(uni.begin(), uni.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+    uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+    int k = 1;
+    // fuse the next variables of the union while every tensor holding them is
+    // already in the product and brings no new variable
+    while (k < max_fuse && k < (int)uni.size()) {
+      int u = uni[k];
+      int pu = pos[u];
+      if (pu >= ne) break;
+      int in_inputs = 0;
+      for (int id : inputs)
+        if (std::find(T[id].vars.begin(), T[id].vars.end(), u) != T[id].vars.end()) ++in_inputs;
+      if (live[u] != in_inputs + (int)bucket[pu].size()) break;
+      bool subset = true;
+      for (int id : bucket[pu])
+        for (int v : T[id].vars)
+          if (std::find(uni.begin(), uni.end(), v) == uni.end()) subset = false;
+      if (!subset) break;
+      for (int id : bucket[pu]) inputs.push_back(id);
+      bucket[pu].clear();
+      ++k;
+    }
+    shrink(inputs);
+    int oid = emit(inputs, k);
+    place(oid);
+  }
+  // final product over the remaining tensors (scalars per batch entry, or
+  // the tensor over the open outputs)
+  if (finals.empty()) {
+    set_error("internal: no final tensor");
+  }
+  std::vector<int> fin = finals;
+  if (fin.size() == 1 && T[fin[0]].leaf < 0) {
+    R.final_tensor = fin[0];
+  } else {
+    shrink(fin);
+    int oid = emit(fin, 0);
+    R.final_tensor = oid;
+  }
+  R.final_tensors = finals;
+  R.arena_peak = arena.peak;
+  return R;
+}
+
+static int64_t pow2(int r) { return (int64_t)1 << r; }
+
+int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
+  p->model = m;
+  p->opts = o;
+  p->opts.order = nullptr;
+  p->output_mode = o.output_mode;
+  if (o.output_mode != QGM_OUT_BATCH && o.output_mode != QGM_OUT_OPEN) {
+    set_error("qgm_plan_order: bad output_mode %d", o.output_mode);
+    return QGM_ERR_ARG;
+  }
+  if (o.output_mode == QGM_OUT_BATCH) {
+    if (o.batch < 1 || o.batch > (1 << 24)) {
+      set_error("qgm_plan_order: batch %lld out of [1, 2^24]", (long long)o.batch);
+      return QGM_ERR_ARG;
+    }
+    p->batch = o.batch;
+    p->Bp = (int32_t)((o.batch + 3) / 4 * 4);
+  } else {
+    if (m.n > 30) {
+      set_error("qgm_plan_order: open outputs need n <= 30 (got %d)", m.n);
+      return QGM_ERR_ARG;
+    }
+    p->batch = 1;
+    p->Bp = 1;
+  }
+  const int max_fuse = o.max_fuse > 0 ? std::min(o.max_fuse, 16) : 8;
+  const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)64 << 30;
+
+  reduce_factors(m, p->leaves, p->constant, p->half_pow_total);
+  p->var_role.assign(m.n_vars, 0);
+  for (int v : m.inputs) p->var_role[v] = 1;
+  p->open_vars.clear();
+  for (int q = m.n - 1; q >= 0; --q) {
+    int v = m.outputs[q];
+    if (p->var_role[v] == 1) continue;  // qubit without gates: output = input
+    if (o.output_mode == QGM_OUT_BATCH) p->var_role[v] = 2;
+    else {
+      p->var_role[v] = 3;
+      p->open_vars.push_back(v);
+    }
+  }
+  for (int q = 0; q < m.n; ++q)
+    if (p->var_role[m.outputs[q]] == 1) {
+      set_error("qgm_plan_order: qubit %d has no non-diagonal gate (every qubit needs one)", q);
+      return QGM_ERR_ARG;
+    }
+  std::vector<char> in_graph(m.n_vars, 0), elim(m.n_vars, 0), keep(m.n_vars, 0);
+  for (int v = 0; v < m.n_vars; ++v) {
+    in_graph[v] = p->var_role[v] == 0 || p->var_role[v] == 3;
+    elim[v] = p->var_role[v] == 0;
+    keep[v] = p->var_role[v] == 3;
+  }
+  Graph g = make_graph(p, in_graph);
+
+  std::vector<std::pair<int, std::vector<int>>> cands;
+  int kind = o.order_kind;
+  if (kind == QGM_ORDER_GIVEN) {
+    if (!o.order || o.n_order < 0) {
+      set_error("qgm_plan_order: QGM_ORDER_GIVEN without an order");
+      return QGM_ERR_ARG;
+    }
+    std::vector<int> given(o.order, o.order + o.n_order);
+    std::vector<char> seen(m.n_vars, 0);
+    for (int v : given) {
+      if (v < 0 || v >= m.n_vars || !elim[v] || seen[v]) {
+        set_error("qgm_plan_order: given order holds %d, not a free variable (or repeated)", v);
+        return QGM_ERR_ARG;
+      }
+      seen[v] = 1;
+    }
+    for (int v = 0; v < m.n_vars; ++v)
+      if (elim[v] && !seen[v]) {
+        set_error("qgm_plan_order: given order misses variable %d", v);
+        return QGM_ERR_ARG;
+      }
+    cands.push_back({QGM_ORDER_GIVEN, given});
+  } else {
+    if (kind < 0 || kind > QGM_ORDER_VERTICAL_T) {
+      set_error("qgm_plan_order: bad order_kind %d", kind);
+      return QGM_ERR_ARG;
+    }
+    if (kind == QGM_ORDER_AUTO || kind == QGM_ORDER_MINFILL)
+      cands.push_back({QGM_ORDER_MINFILL, order_minfill(g, keep)});
+    if (kind == QGM_ORDER_AUTO || kind == QGM_ORDER_VERTICAL)
+      cands.push_back({QGM_ORDER_VERTICAL, order_vertical(p, elim, false)});
+    if (kind == QGM_ORDER_AUTO || kind == QGM_ORDER_VERTICAL_T)
+      cands.push_back({QGM_ORDER_VERTICAL_T, order_vertical(p, elim, true)});
+  }
+  // slice each candidate until its live set fits, keep the cheapest
+  double best_cost = -1;
+  for (auto &c : cands) {
+    std::vector<char> sliced(m.n_vars, 0);
+    std::vector<int> svars;
+    SimResult r = simulate(p, c.second, sliced, max_fuse, false);
+    while (r.arena_peak > budget && svars.size() < 40) {
+      // the variable held by the most tensors of the largest size
+      std::vector<int> cnt(m.n_vars, 0);
+      for (const SymTensor &t : r.tensors)
+        if (t.leaf < 0 && t.entries == r.max_entries)
+          for (int v : t.vars)
+            if (p->var_role[v] == 0) cnt[v]++;
+      int bv = -1;
+      for (int v = 0; v < m.n_vars; ++v)
+        if (cnt[v] > 0 && (bv < 0 || cnt[v] > cnt[bv])) bv = v;
+      if (bv < 0) break;
+      sliced[bv] = 1;
+      svars.push_back(bv);
+      r = simulate(p, c.second, sliced, max_fuse, false);
+    }
+    if (r.arena_peak > budget) continue;
+    double cost = r.bytes * (double)pow2((int)svars.size());
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      p->order_kind = c.first;
+      p->order = c.second;
+      p->slice_vars = svars;
+    }
+  }
+  if (best_cost < 0) {
+    set_error("qgm_plan_order: no order fits the memory budget of %lld bytes even sliced",
+              (long long)budget);
+    return QGM_ERR_OOM;
+  }
+  std::vector<char> sliced(m.n_vars, 0);
+  for (int v : p->slice_vars) {
+    sliced[v] = 1;
+    p->var_role[v] = 4;
+  }
+  p->sim = simulate(p, p->order, sliced, max_fuse, true);
+  SimResult &S = p->sim;
+  // induced width along the order on the graph without the sliced variables
+  {
+    std::vector<char> ig = in_graph;
+    for (int v : p->slice_vars) ig[v] = 0;
+    Graph g2 = make_graph(p, ig);
+    int w = 0;
+    for (int v : p->order)
+      if (!sliced[v]) w = std::max(w, g2.eliminate(v));
+    S.max_clique = w;
+  }
+  p->pos.assign(m.n_vars, -1);
+  {
+    int i = 0;
+    for (int v : p->order)
+      if (!sliced[v]) p->pos[v] = i++;
+    for (size_t j = 0; j < p->open_vars.size(); ++j) p->pos[p->open_vars[j]] = i + (int)j;
+  }
+
+  // ---------------------------------------------------- device layout
+  const int64_t Bp = p->Bp;
+  int64_t off = 0;
+  auto take = [&](int64_t bytes) {
+    int64_t o2 = off;
+    off += (bytes + 255) & ~int64_t(255);
+    return o2;
+  };
+  int n_meta = 0;
+  for (const SymTensor &t : S.tensors)
+    if (t.leaf < 0) n_meta = std::max(n_meta, t.meta + 1);
+  p->n_meta = n_meta;
+  p->off_header = take(256);
+  p->off_meta = take((int64_t)std::max(n_meta, 1) * 8);
+  p->off_leafdesc = take((int64_t)std::max<size_t>(p->leaves.size(), 1) * sizeof(LeafDesc));
+  // base tables: (internal vars by position | slice vars | output vars by qubit)
+  p->base_tables.clear();
+  p->leafdesc.clear();
+  std::vector<int64_t> leaf_built_off(p->leaves.size(), -1);
+  int64_t base_floats = 0;
+  std::vector<int64_t> base_at(p->leaves.size());
+  for (size_t li = 0; li < p->leaves.size(); ++li) {
+    base_at[li] = base_floats;
+    base_floats += 2 * (int64_t)p->leaves[li].table.size();
+    base_floats = (base_floats + 3) & ~int64_t(3);
+  }
+  p->off_base = take(base_floats * 4);
+  p->base_tables.assign(base_floats, 0.f);
+  int64_t leaf_bytes = 0;
+  for (size_t li = 0; li < p->leaves.size(); ++li) {
+    const LeafFactor &L = p->leaves[li];
+    const SymTensor &t = S.tensors[li];
+    std::vector<int> intv = t.vars, slv, outv;
+    for (int v : L.scope) {
+      if (p->var_role[v] == 4) slv.push_back(v);
+      if (p->var_role[v] == 2) outv.push_back(v);
+    }
+    std::sort(slv.begin(), slv.end(), [&](int a, int b) {
+      return std::find(p->slice_vars.begin(), p->slice_vars.end(), a) <
+             std::find(p->slice_vars.begin(), p->slice_vars.end(), b);
+    });
+    std::sort(outv.begin(), outv.end(),
+              [&](int a, int b) { return m.var_qubit[a] < m.var_qubit[b]; });
+    std::vector<int> layout = intv;
+    layout.insert(layout.end(), slv.begin(), slv.end());
+    layout.insert(layout.end(), outv.begin(), outv.end());
+    if ((int)layout.size() > MAXLEAFV || layout.size() != L.scope.size()) {
+      set_error("internal: leaf %zu has %zu variables", li, layout.size());
+      return QGM_ERR_ARG;
+    }
+    std::vector<cd> tab = expand_table(L.scope, L.table, layout);
+    for (size_t i = 0; i < tab.size(); ++i) {
+      p->base_tables[base_at[li] + 2 * i] = (float)tab[i].real();
+      p->base_tables[base_at[li] + 2 * i + 1] = (float)tab[i].imag();
+    }
+    LeafDesc d{};
+    d.base_off = p->off_base + base_at[li] * 4;
+    d.n_int = (int)intv.size();
+    d.n_slice = (int)slv.size();
+    d.n_out = (int)outv.size();
+    d.batched = t.batched ? 1 : 0;
+    for (size_t a = 0; a < slv.size(); ++a)
+      d.slice_bit[a] = (int)(std::find(p->slice_vars.begin(), p->slice_vars.end(), slv[a]) -
+                             p->slice_vars.begin());
+    for (size_t a = 0; a < outv.size(); ++a) d.out_qubit[a] = m.var_qubit[outv[a]];
+    d.out_off = leaf_bytes;  // relative, fixed below
+    leaf_bytes += ((pow2(d.n_int) * (d.batched ? Bp : 1) * 8) + 255) & ~int64_t(255);
+    p->leafdesc.push_back(d);
+  }
+  p->off_leaf = take(leaf_bytes);
+  for (size_t li = 0; li < p->leafdesc.size(); ++li) {
+    p->leafdesc[li].out_off += p->off_leaf;
+    S.tensors[li].off = p->leafdesc[li].out_off;
+  }
+  p->off_bits = take(Bp * 8);
+  const SymTensor &F = S.tensors[S.final_tensor];
+  p->final_entries = pow2((int)F.vars.size());
+  p->final_batched = F.batched ? 1 : 0;
+  int64_t out_elems = o.output_mode == QGM_OUT_BATCH ? Bp : p->final_entries;
+  p->off_outstage = take(out_elems * 16);
+  p->off_acc = take(out_elems * 16);
+  p->off_arena = take(0);
+  for (SymTensor &t : S.tensors)
+    if (t.leaf < 0) t.off += p->off_arena;
+  p->ws_bytes = p->off_arena + ((S.arena_peak + 255) & ~int64_t(255)) + 256;
+  p->final_off = F.off;
+  p->final_meta = F.leaf < 0 ? F.meta : -1;
+
+  // step descriptors
+  p->steps.clear();
+  for (const StepRec &s : S.steps) {
+    StepDesc d{};
+    d.m = (int)s.inputs.size();
+    d.k = s.k;
+    const int U = (int)s.uni.size();
+    d.w_out = U - s.k;
+    const SymTensor &ot = S.tensors[s.out];
+    d.batched_out = ot.batched ? 1 : 0;
+    d.out_off = ot.off;
+    d.out_meta = ot.meta;
+    for (int i = 0; i < d.m; ++i) {
+      const SymTensor &it = S.tensors[s.inputs[i]];
+      InDesc &in = d.in[i];
+      in.off = it.off;
+      in.meta = it.leaf < 0 ? it.meta : -1;
+      in.batched = it.batched ? 1 : 0;
+      // union bit of var a is U-1-a; the input keeps its variables in order
+      int nr = 0, dst = 0;
+      int b = 0;
+      while (b < U) {
+        auto present = [&](int bit) {
+          int v = s.uni[U - 1 - bit];
+          return std::find(it.vars.begin(), it.vars.end(), v) != it.vars.end();
+        };
+        if (!present(b)) {
+          ++b;
+          continue;
+        }
+        int st = b;
+        while (b < U && present(b)) ++b;
+        if (nr >= MAXRUN) {
+          set_error("internal: index map with more than %d runs", MAXRUN);
+          return QGM_ERR_ARG;
+        }
+        in.src[nr] = (uint8_t)st;
+        in.len[nr] = (uint8_t)(b - st);
+        in.dst[nr] = (uint8_t)dst;
+        dst += b - st;
+        ++nr;
+      }
+      in.nruns = nr;
+    }
+    p->steps.push_back(d);
+  }
+  return QGM_OK;
+}
+
+}  // namespace qgm
+
+using namespace qgm;
+
+// ===================================================================== C ABI
+extern "C" {
+
+const char *qgm_last_error(void) { return g_last_error.c_str(); }
+
+int qgm_circuit_grid(int rows, int cols, int depth, uint64_t seed, int param_mode,
+                     qgm_circuit **out) {
+  if (!out || rows < 1 || cols < 1 || depth < 1 || rows * cols > 64) {
+    set_error("qgm_circuit_grid: need rows, cols, depth >= 1 and rows*cols <= 64");
+    return QGM_ERR_ARG;
+  }
+  *out = new qgm_circuit{grid_circuit(rows, cols, depth, seed, param_mode)};
+  return QGM_OK;
+}
+
+int qgm_circuit_from_gates(int n_qubits, const qgm_gate *gates, int64_t n_gates,
+                           qgm_circuit **out) {
+  if (!out || n_qubits < 1 || n_qubits > 64 || n_gates < 0 || (n_gates > 0 && !gates)) {
+    set_error("qgm_circuit_from_gates: bad arguments");
+    return QGM_ERR_ARG;
+  }
+  Circuit c;
+  c.n = n_qubits;
+  for (int64_t i = 0; i < n_gates; ++i) {
+    const qgm_gate &g = gates[i];
+    bool ok = g.kind >= QGM_GATE_H && g.kind <= QGM_GATE_RXY && g.q0 >= 0 && g.q0 < n_qubits;
+    if (g.kind == QGM_GATE_CZ) ok = ok && g.q1 >= 0 && g.q1 < n_qubits && g.q1 != g.q0;
+    if (!ok) {
+      set_error("qgm_circuit_from_gates: gate %lld is invalid", (long long)i);
+      return QGM_ERR_ARG;
+    }
+    if (g.kind == QGM_GATE_RXY) c.param_gates.push_back((int)i);
+    c.gates.push_back(g);
+    c.depth = std::max(c.depth, g.cycle + 1);
+  }
+  c.param = !c.param_gates.empty();
+  *out = new qgm_circuit{c};
+  return QGM_OK;
+}
+
+int qgm_circuit_gates(const qgm_circuit *c, qgm_gate *gates, int64_t cap, int64_t *n) {
+  if (!c || !n) {
+    set_error("qgm_circuit_gates: null argument");
+    return QGM_ERR_ARG;
+  }
+  *n = (int64_t)c->c.gates.size();
+  if (gates)
+    for (int64_t i = 0; i < std::min(cap, *n); ++i) gates[i] = c->c.gates[i];
+  return QGM_OK;
+}
+
+int qgm_circuit_param_gates(const qgm_circuit *c, int32_t *idx, int64_t cap, int64_t *n) {
+  if (!c || !n) {
+    set_error("qgm_circuit_param_gates: null argument");
+    return QGM_ERR_ARG;
+  }
+  *n = (int64_t)c->c.param_gates.size();
+  if (idx)
+    for (int64_t i = 0; i < std::min(cap, *n); ++i) idx[i] = c->c.param_gates[i];
+  return QGM_OK;
+}
+
+void qgm_circuit_free(qgm_circuit *c) { delete c; }
+
+int qgm_build_model(const qgm_circuit *c, qgm_model **out) {
+  if (!c || !out) {
+    set_error("qgm_build_model: null argument");
+    return QGM_ERR_ARG;
+  }
+  qgm_model *m = new qgm_model;
+  build_model(c->c, m->m);
+  *out = m;
+  return QGM_OK;
+}
+
+int qgm_model_get_info(const qgm_model *m, qgm_model_info *info) {
+  if (!m || !info) {
+    set_error("qgm_model_get_info: null argument");
+    return QGM_ERR_ARG;
+  }
+  info->n_qubits = m->m.n;
+  info->n_vars = m->m.n_vars;
+  info->n_factors = (int32_t)m->m.factors.size();
+  info->n_nondiag = m->m.L;
+  info->n_params = 2 * (int32_t)m->m.param_factor.size();
+  return QGM_OK;
+}
+
+int qgm_model_vars(const qgm_model *m, int32_t *qubit, int32_t *k) {
+  if (!m || !qubit || !k) {
+    set_error("qgm_model_vars: null argument");
+    return QGM_ERR_ARG;
+  }
+  for (int v = 0; v < m->m.n_vars; ++v) {
+    qubit[v] = m->m.var_qubit[v];
+    k[v] = m->m.var_k[v];
+  }
+  return QGM_OK;
+}
+
+int qgm_model_factors(const qgm_model *m, int32_t *nvar, int32_t *scope) {
+  if (!m || !nvar || !scope) {
+    set_error("qgm_model_factors: null argument");
+    return QGM_ERR_ARG;
+  }
+  for (size_t f = 0; f < m->m.factors.size(); ++f) {
+    nvar[f] = m->m.factors[f].nv;
+    scope[2 * f] = m->m.factors[f].v[0];
+    scope[2 * f + 1] = m->m.factors[f].nv > 1 ? m->m.factors[f].v[1] : -1;
+  }
+  return QGM_OK;
+}
+
+void qgm_model_free(qgm_model *m) { delete m; }
+
+void qgm_exec_release(qgm_plan *p);  // exec.cu
+
+int qgm_plan_order(const qgm_model *m, const qgm_plan_opts *opts, qgm_plan **out) {
+  if (!m || !opts || !out) {
+    set_error("qgm_plan_order: null argument");
+    return QGM_ERR_ARG;
+  }
+  qgm_plan *p = new qgm_plan;
+  int rc = build_plan(m->m, *opts, p);
+  if (rc != QGM_OK) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return QGM_OK;
+}
+
+int qgm_plan_get_info(const qgm_plan *p, qgm_plan_info *info) {
+  if (!p || !info) {
+    set_error("qgm_plan_get_info: null argument");
+    return QGM_ERR_ARG;
+  }
+  info->order_kind = p->order_kind;
+  info->n_free = (int32_t)p->order.size();
+  info->max_clique = p->sim.max_clique;
+  info->n_steps = (int32_t)p->steps.size();
+  info->n_slice_vars = (int32_t)p->slice_vars.size();
+  info->batch_padded = p->Bp;
+  info->n_slices = (int64_t)1 << p->slice_vars.size();
+  info->max_tensor_entries = p->sim.max_entries;
+  info->workspace_bytes = p->ws_bytes;
+  info->arena_bytes = p->sim.arena_peak;
+  info->bytes_per_slice = p->sim.bytes;
+  info->flops_per_slice = p->sim.flops;
+  info->max_step_bytes = p->sim.max_step_bytes;
+  return QGM_OK;
+}
+
+int qgm_plan_get_order(const qgm_plan *p, int32_t *order, int64_t cap, int64_t *n) {
+  if (!p || !n) {
+    set_error("qgm_plan_get_order: null argument");
+    return QGM_ERR_ARG;
+  }
+  *n = (int64_t)p->order.size();
+  if (order)
+    for (int64_t i = 0; i < std::min(cap, *n); ++i) order[i] = p->order[i];
+  return QGM_OK;
+}
+
+int qgm_plan_get_slice_vars(const qgm_plan *p, int32_t *vars, int64_t cap, int64_t *n) {
+  if (!p || !n) {
+    set_error("qgm_plan_get_slice_vars: null argument");
+    return QGM_ERR_ARG;
+  }
+  *n = (int64_t)p->slice_vars.size();
+  if (vars)
+    for (int64_t i = 0; i < std::min(cap, *n); ++i) vars[i] = p->slice_vars[i];
+  return QGM_OK;
+}
+
+int qgm_plan_get_steps(const qgm_plan *p, int32_t *out_rank, int32_t *k, int32_t *n_in,
+                       int32_t *batched, int64_t cap) {
+  if (!p) {
+    set_error("qgm_plan_get_steps: null argument");
+    return QGM_ERR_ARG;
+  }
+  for (int64_t s = 0; s < std::min<int64_t>(cap, (int64_t)p->steps.size()); ++s) {
+    if (out_rank) out_rank[s] = p->steps[s].w_out;
+    if (k) k[s] = p->steps[s].k;
+    if (n_in) n_in[s] = p->steps[s].m;
+    if (batched) batched[s] = p->steps[s].batched_out;
+  }
+  return QGM_OK;
+}
+
+int qgm_plan_get_step_cost(const qgm_plan *p, double *bytes, double *flops, int64_t cap) {
+  if (!p) {
+    set_error("qgm_plan_get_step_cost: null argument");
+    return QGM_ERR_ARG;
+  }
+  for (int64_t s = 0; s < std::min<int64_t>(cap, (int64_t)p->sim.steps.size()); ++s) {
+    if (bytes) bytes[s] = p->sim.steps[s].bytes;
+    if (flops) flops[s] = p->sim.steps[s].flops;
+  }
+  return QGM_OK;
+}
+
+void qgm_plan_free(qgm_plan *p) {
+  if (!p) return;
+  qgm_exec_release(p);
+  delete p;
+}
+
+}  // extern "C"

@@ -1,0 +1,163 @@
+// Internal host-side structures shared by host.cpp (circuit, model, plan)
+// and exec.cu (device execution).  Not part of the C ABI.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qgm.h"
+
+namespace qgm {
+
+using cd = std::complex<double>;
+
+void set_error(const char *fmt, ...);
+
+// ---------------------------------------------------------------- circuit
+struct Circuit {
+  int n = 0, rows = 0, cols = 0, depth = 0;
+  uint64_t seed = 0;
+  int param = 0;
+  std::vector<qgm_gate> gates;
+  std::vector<int> param_gates;
+};
+
+// ------------------------------------------------------------------ model
+// One factor per gate (Sec. III.B).  Table index = (bit(v[0]) << (nv-1)) | bit(v[1]).
+struct MFactor {
+  int nv = 0;
+  int v[2] = {-1, -1};
+  cd t[4];
+  int gate = -1;
+  int half_pow = 0;  // number of 2^{-1/2} factors pulled out of the table
+};
+
+struct Model {
+  int n = 0, rows = 0, cols = 0;
+  int n_vars = 0;
+  std::vector<int> var_qubit, var_k, inputs, outputs;
+  std::vector<MFactor> factors;
+  int L = 0;                       // non-diagonal gates
+  std::vector<int> param_factor;   // factor index of each RXY gate
+  std::vector<qgm_gate> gates;     // copy of the circuit's gates
+};
+
+// ------------------------------------------------------------------- plan
+constexpr int MAXIN = 8;    // tensors multiplied in one step
+constexpr int MAXRUN = 12;  // contiguous bit runs of an index map
+constexpr int MAXLEAFV = 4; // variables of a leaf factor (internal+slice+output)
+
+// Index map of one step input: the input's index is the union index with
+// the bits of absent variables squeezed out (a "pext" by contiguous runs).
+struct InDesc {
+  int64_t off;       // byte offset of the tensor in the workspace
+  int32_t meta;      // tensor metadata slot (intermediates), -1 for leaves
+  int32_t batched;   // 1: rows of batch_padded complex values
+  int32_t nruns;
+  uint8_t src[MAXRUN], len[MAXRUN], dst[MAXRUN];
+};
+
+struct StepDesc {
+  int32_t m;            // inputs
+  int32_t k;            // variables summed (top k bits of the union index)
+  int32_t w_out;        // output rank (binary variables)
+  int32_t batched_out;
+  int64_t out_off;
+  int32_t out_meta;
+  int32_t pad_;
+  InDesc in[MAXIN];
+};
+
+// Leaf factor built on the device per slice: base table over
+// (internal vars | slice vars | output vars), MSB first.
+struct LeafDesc {
+  int64_t base_off;  // complex64 base table (bytes into the workspace)
+  int64_t out_off;   // built table
+  int32_t n_int, n_slice, n_out, batched;
+  int32_t slice_bit[MAXLEAFV];  // bit of the slice id for each slice var
+  int32_t out_qubit[MAXLEAFV];  // qubit of each output var
+};
+
+struct SymTensor {
+  std::vector<int> vars;  // sorted by elimination position
+  bool batched = false;
+  int leaf = -1;          // leaf index or -1
+  int meta = -1;          // metadata slot for intermediates
+  int64_t off = -1;       // byte offset in the workspace
+  int64_t entries = 0;
+};
+
+struct StepRec {
+  std::vector<int> inputs;  // SymTensor ids
+  std::vector<int> uni;     // union vars (sorted)
+  int k = 0;
+  int out = -1;
+  bool batched = false;
+  double bytes = 0, flops = 0;
+};
+
+struct LeafFactor {          // merged factor after fixing the inputs
+  std::vector<int> scope;    // var ids (table is C-order over scope)
+  std::vector<cd> table;
+  int half_pow = 0;
+  std::vector<int> members; // model factor ids merged into it
+};
+
+struct SimResult {
+  double bytes = 0, flops = 0, max_step_bytes = 0;
+  int64_t max_entries = 0;
+  int64_t arena_peak = 0;
+  int max_clique = 0;
+  std::vector<SymTensor> tensors;
+  std::vector<StepRec> steps;
+  std::vector<int> final_tensors;
+  int final_tensor = -1;
+};
+
+}  // namespace qgm
+
+struct qgm_circuit {
+  qgm::Circuit c;
+};
+struct qgm_model {
+  qgm::Model m;
+};
+
+struct qgm_exec_state;  // device-side state (exec.cu)
+
+struct qgm_plan {
+  const qgm::Model *model_copy_owner = nullptr;
+  qgm::Model model;
+  qgm_plan_opts opts{};
+  int order_kind = 0;
+  int output_mode = 0;
+  int64_t batch = 1;
+  int32_t Bp = 1;
+  std::vector<int> order;        // eliminated vars
+  std::vector<int> open_vars;    // never eliminated (open outputs)
+  std::vector<int> slice_vars;
+  std::vector<int> pos;          // elimination position per var (-1: not in graph)
+  std::vector<int> var_role;     // 0 free, 1 input, 2 output(batched), 3 open, 4 slice
+  std::vector<qgm::LeafFactor> leaves;
+  qgm::cd constant = 1.0;        // product of scope-free factors and 2^{-L/2}
+  int half_pow_total = 0;
+  qgm::SimResult sim;
+  // device layout
+  std::vector<qgm::StepDesc> steps;
+  std::vector<qgm::LeafDesc> leafdesc;
+  std::vector<float> base_tables;  // interleaved complex64
+  int n_meta = 0;
+  int64_t off_header = 0, off_meta = 0, off_leafdesc = 0, off_base = 0, off_leaf = 0, off_bits = 0,
+          off_outstage = 0, off_acc = 0, off_arena = 0, ws_bytes = 0;
+  int64_t final_entries = 0;     // rows of the final tensor (2^n_open or 1)
+  int final_batched = 0;
+  int64_t final_off = 0;
+  int final_meta = -1;
+  qgm_exec_state *exec = nullptr;
+};
+
+namespace qgm {
+int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p);
+}

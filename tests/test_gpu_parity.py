@@ -1,0 +1,184 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GB300).
+
+Tolerance (complex64 path): the paper reports relative error below 1e-5 per
+probability in single precision.  Relative error is undefined at exact zeros,
+so it is measured over amplitudes with |a_ref| >= 1e-3 * 2^{-n/2}; the
+absolute error scaled by 2^{n/2} is bounded as well.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import qgm_inputs as qi
+from oracle import statevector as sv
+from oracle import ve
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-5
+ABS_TOL = 1e-5   # on |a - a_ref| * 2^{n/2}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1712_05384_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def Q():
+    import paper_1712_05384_gb300 as q
+    return q
+
+
+def errors(a, ref, n):
+    a = np.asarray(a)
+    ref = np.asarray(ref)
+    big = np.abs(ref) >= 1e-3 * 2.0 ** (-n / 2)
+    rel = np.max(np.abs(a - ref)[big] / np.abs(ref[big])) if big.any() else 0.0
+    return rel, np.max(np.abs(a - ref)) * 2.0 ** (n / 2)
+
+
+def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0):
+    q = Q()
+    if circuit_py.rows:
+        c = q.Circuit.grid(circuit_py.rows, circuit_py.cols, circuit_py.depth, circuit_py.seed,
+                           circuit_py.param)
+    else:
+        c = q.Circuit.from_gates(circuit_py.n, circuit_py.gates)
+    p = q.Plan(q.Model(c), order_kind=order_kind, batch=B, mem_budget_bytes=budget,
+               max_fuse=max_fuse).bind()
+    if bits is None:
+        bits = qi.bitstrings(circuit_py.n, B, circuit_py.seed)
+    d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
+    d_out = torch.empty(2 * len(bits), dtype=torch.float64, device="cuda")
+    p.amplitudes(d_bits, d_out, B=len(bits))
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    o = d_out.cpu().numpy()
+    return o[0::2] + 1j * o[1::2], bits, p
+
+
+def test_app_d_example(app_d):
+    a, bits, _ = run_batch(app_d, 4, bits=np.arange(4, dtype=np.uint64))
+    ref = sv.state(app_d)
+    assert abs(a[0] - 0.5) < 1e-7          # App. D: <00|C|00> = 1/2
+    assert np.allclose(a, ref, atol=1e-7)
+
+
+@pytest.mark.parametrize("rows,cols,depth,B", [(3, 3, 8, 37), (4, 4, 12, 64), (2, 5, 16, 5),
+                                               (3, 4, 20, 130)])
+def test_small_grids_vs_state_vector(rows, cols, depth, B):
+    c = qi.grid_circuit(rows, cols, depth, seed=2)
+    a, bits, _ = run_batch(c, B)
+    ref = sv.amplitudes(c, bits)
+    rel, ab = errors(a, ref, c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3])
+def test_every_order_kind(kind):
+    c = qi.grid_circuit(4, 4, 14, seed=5)
+    a, bits, p = run_batch(c, 48, order_kind=kind)
+    assert p.info.order_kind == kind
+    rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+def test_sliced_equals_unsliced():
+    c = qi.grid_circuit(4, 5, 16, seed=1)
+    a0, bits, p0 = run_batch(c, 40, order_kind=1)
+    a1, _, p1 = run_batch(c, 40, order_kind=1, budget=p0.info.arena_bytes // 5)
+    assert p1.info.n_slices > 1
+    rel, ab = errors(a1, sv.amplitudes(c, bits), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+    assert np.max(np.abs(a1 - a0)) * 2 ** (c.n / 2) < 1e-5
+
+
+def test_fusion_limits_agree():
+    c = qi.grid_circuit(4, 4, 16, seed=9)
+    a1, bits, _ = run_batch(c, 24, max_fuse=1)
+    a8, _, _ = run_batch(c, 24, max_fuse=8)
+    ref = sv.amplitudes(c, bits)
+    for a in (a1, a8):
+        rel, ab = errors(a, ref, c.n)
+        assert rel < REL_TOL and ab < ABS_TOL
+
+
+def test_parametrised_circuit():
+    c = qi.grid_circuit(3, 4, 14, seed=4, param=True)
+    a, bits, _ = run_batch(c, 33)
+    rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+def test_depth_one_is_uniform():
+    # only the H layer: every amplitude is 2^{-n/2}
+    c = qi.grid_circuit(3, 3, 1, seed=0)
+    a, _, _ = run_batch(c, 12)
+    assert np.allclose(a, 2 ** -4.5, rtol=1e-7, atol=0)
+
+
+def test_open_outputs_4x4_d10_all_amplitudes():
+    # 4x4 grid, depth 10: all 2^16 amplitudes at once (output deltas omitted)
+    q = Q()
+    c = qi.grid_circuit(4, 4, 10, 0)
+    p = q.Plan(q.Model(q.Circuit.grid(4, 4, 10, 0)), output_mode=q.OUT_OPEN).bind()
+    d_out = torch.empty(2 << 16, dtype=torch.float64, device="cuda")
+    p.eliminate(d_out)
+    torch.cuda.synchronize()
+    o = d_out.cpu().numpy()
+    a = o[0::2] + 1j * o[1::2]
+    ref = sv.state(c)
+    rel, ab = errors(a, ref, c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+    assert abs(np.vdot(a, a).real - 1) < 1e-5
+    assert np.allclose(a, ve.open_amplitudes(c), atol=1e-6 * 2 ** -8)
+
+
+def test_grid5x5_d20_b1024_sampled():
+    # full-size workload, the launch configuration the benchmark times;
+    # 64 sampled outputs against the oracle's own elimination
+    c = qi.grid_circuit(5, 5, 20, 0)
+    a, bits, p = run_batch(c, 1024)
+    idx = np.linspace(0, 1023, 64).astype(int)
+    ref = ve.amplitudes(c, bits[idx])
+    rel, ab = errors(a[idx], ref, c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+    # Porter-Thomas: N p has mean 1 and second moment 2 (4-sigma bands)
+    Np = (2 ** c.n) * np.abs(a) ** 2
+    assert abs(Np.mean() - 1) < 4 * 1 / math.sqrt(1024)
+    assert abs((Np ** 2).mean() - 2) < 4 * math.sqrt(20 / 1024)
+
+
+def test_host_api_matches_device_api():
+    q = Q()
+    c = qi.grid_circuit(4, 4, 12, 3)
+    bits = qi.bitstrings(16, 50, 3)
+    a_dev, _, p = run_batch(c, 50, bits=bits)
+    a_host = p.amplitudes_host(bits)
+    assert np.array_equal(a_dev, a_host)
+    # a second call with fewer bitstrings reuses the plan
+    a_part = p.amplitudes_host(bits[:7])
+    assert np.array_equal(a_part, a_dev[:7])
+
+
+def test_errors_are_reported():
+    q = Q()
+    m = q.Model(q.Circuit.grid(3, 3, 8, 0))
+    p = q.Plan(m, batch=8)
+    d_bits = torch.zeros(8, dtype=torch.int64, device="cuda")
+    d_out = torch.zeros(16, dtype=torch.float64, device="cuda")
+    with pytest.raises(q.QgmError):
+        p.amplitudes(d_bits, d_out)               # not bound
+    small = torch.empty(256, dtype=torch.uint8, device="cuda")
+    with pytest.raises(q.QgmError):
+        p.bind(small)                             # workspace too small
+    p.bind()
+    with pytest.raises(q.QgmError):
+        p.amplitudes(d_bits, d_out, B=9)          # more than the plan's batch
+    with pytest.raises(q.QgmError):
+        p.eliminate(d_out)                        # not an open-output plan

