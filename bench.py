@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid5x5_d20_b1024", choices=sorted(qi.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--executor", type=int, default=0, help="0 auto, 1 stepwise, 2 resident")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -202,7 +203,8 @@ def main():
     # weak scaling: each rank takes its own batch of B bitstrings
     all_bits = qi.bitstrings(c_py.n, B * world, 0)
     bits = all_bits[rank * B:(rank + 1) * B]
-    plan = q.Plan(q.Model(q.Circuit.grid(rows, cols, depth, 0, param)), batch=B).bind()
+    plan = q.Plan(q.Model(q.Circuit.grid(rows, cols, depth, 0, param)), batch=B,
+                  executor=args.executor).bind()
     info = plan.info
     stream = torch.cuda.current_stream(dev)
     d_bits = torch.from_numpy(bits.astype(np.int64)).to(dev)
@@ -261,19 +263,42 @@ def main():
         e2e_s = float(t.item())
     e2e = world * B * args.steps / e2e_s
 
-    # roofline of the dominant kernel class (the product-sum step kernel),
-    # per-launch times from a kernel-by-kernel pass with events on the stream
+    # roofline of the dominant kernel, per-launch times from a pass with CUDA
+    # events on the launching stream
     step_bytes, step_flops = plan.step_costs()
+    ex_kind, ex_chunk, ex_smem = plan.executor()
     reps = 5
     ms = np.zeros(info.n_steps + 2)
     for _ in range(reps):
         flush.fill_(1.0)
         ms += plan.profile(d_bits, d_out, B=B, stream=stream)
     ms /= reps
-    k_ms = float(ms[1:-1].sum())
-    achieved = float(step_bytes.sum()) / (k_ms / 1e3) / 1e9
-    peak, peak_kind = peaks()
     traffic = NCU_TRAFFIC.get(kernel_hash())
+    if ex_kind == q.EXEC_RESIDENT:
+        # all intermediates live in shared memory: bound by the SM's FP32/ALU
+        # issue, peak = 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
+        k_ms = float(ms[0])
+        peak = 152 * 128 * 2 * 2.070e9 / 1e12
+        achieved = float(step_flops.sum()) / (k_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": f"k_resident (whole pass, {ex_chunk} bitstring(s) per CTA, "
+                          f"{ex_smem} B shared memory)",
+                "algorithmic_flops_per_pass": float(step_flops.sum()),
+                "algorithmic_bytes_per_pass": float(step_bytes.sum()),
+                "kernel_ms_per_pass": k_ms,
+                "peak_source": "derived: FP32 lanes x SMs x max SM clock"}
+        launches = args.steps
+    else:
+        k_ms = float(ms[1:-1].sum())
+        achieved = float(step_bytes.sum()) / (k_ms / 1e3) / 1e9
+        peak, peak_kind = peaks()
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_step_batched (all elimination steps)",
+                "algorithmic_bytes_per_pass": float(step_bytes.sum()),
+                "kernel_ms_per_pass": k_ms, "peak_source": peak_kind}
+        launches = args.steps * int(info.n_slices * (info.n_steps + 2) + 1)
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -284,15 +309,12 @@ def main():
                    "batch_per_gpu": B, "seed": 0, "order": info.order_kind,
                    "max_clique": info.max_clique, "steps_per_pass": info.n_steps,
                    "slices": info.n_slices, "parallelism": f"replicas{world}",
+                   "executor": {1: "stepwise", 2: "resident"}.get(ex_kind), "chunk": ex_chunk,
                    "l2": "flushed between timed steps (264 MB write, untimed)"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * B,
                 "d2h_bytes_per_step": 16 * B},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": traffic,
-                     "kernel": "k_step_batched (all elimination steps)",
-                     "algorithmic_bytes_per_pass": float(step_bytes.sum()),
-                     "kernel_ms_per_pass": k_ms, "peak_source": peak_kind},
-        "gpu_launches": args.steps * int(info.n_slices * (info.n_steps + 2) + 1),
+        "roofline": roof,
+        "gpu_launches": launches,
         "clocks": clk.summary(),
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -144,7 +144,18 @@ typedef struct {
   int32_t max_fuse;           /* max variables summed in one step (0 = 8) */
   int32_t n_order;            /* QGM_ORDER_GIVEN: length of `order` */
   const int32_t *order;       /* QGM_ORDER_GIVEN: elimination order (var ids) */
+  int32_t executor;           /* QGM_EXEC_* */
+  int32_t resident_chunk;     /* bitstrings per CTA of the resident executor:
+                                 1, 2, 4 or 8; 0 = chosen at bind (fewest
+                                 waves x chunk on the bound device) */
 } qgm_plan_opts;
+
+enum {
+  QGM_EXEC_AUTO = 0,      /* resident when a chunk's live set fits in shared memory */
+  QGM_EXEC_STEPWISE = 1,  /* one kernel per step over the whole batch (CUDA graph) */
+  QGM_EXEC_RESIDENT = 2   /* one persistent launch: each CTA runs all steps for a
+                             chunk of bitstrings out of shared memory */
+};
 
 typedef struct {
   int32_t order_kind;         /* the order actually used */
@@ -212,6 +223,10 @@ int qgm_eliminate(qgm_plan *p, double *d_out, void *stream);
  * (accumulation); ms must hold n_steps + 2 floats (host).  Synchronises. */
 int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
                      float *ms, void *stream);
+
+/* Executor chosen at bind time: *kind (QGM_EXEC_STEPWISE or _RESIDENT), the
+ * bitstrings per CTA *chunk and the dynamic shared memory per CTA (resident). */
+int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int64_t *smem_bytes);
 
 /* Reads and clears the device status word of the bound workspace
  * (synchronises `stream`): QGM_OK, QGM_ERR_NONFINITE or QGM_ERR_TIMEOUT. */

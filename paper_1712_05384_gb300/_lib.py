@@ -21,6 +21,7 @@ ERRORS = {-1: "QGM_ERR_ARG", -2: "QGM_ERR_OOM", -3: "QGM_ERR_CUDA", -4: "QGM_ERR
 
 ORDER_AUTO, ORDER_MINFILL, ORDER_VERTICAL, ORDER_VERTICAL_T, ORDER_GIVEN = range(5)
 OUT_BATCH, OUT_OPEN = 0, 1
+EXEC_AUTO, EXEC_STEPWISE, EXEC_RESIDENT = 0, 1, 2
 
 
 class qgm_gate(C.Structure):
@@ -36,7 +37,8 @@ class qgm_model_info(C.Structure):
 class qgm_plan_opts(C.Structure):
     _fields_ = [("order_kind", C.c_int32), ("output_mode", C.c_int32), ("batch", C.c_int64),
                 ("mem_budget_bytes", C.c_int64), ("max_fuse", C.c_int32), ("n_order", C.c_int32),
-                ("order", C.POINTER(C.c_int32))]
+                ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
+                ("resident_chunk", C.c_int32)]
 
 
 class qgm_plan_info(C.Structure):
@@ -80,6 +82,7 @@ _SIGS = {
     "qgm_amplitudes_host": [_P, _P, C.c_int64, _P, _P],
     "qgm_eliminate": [_P, _P, _P],
     "qgm_status": [_P, _P],
+    "qgm_plan_get_executor": [_P, _I32P, _I32P, _I64P],
     "qgm_amplitude_grad": [_P, _P, C.c_int64, _P, _P, _P, _P],
     "qgm_last_error": [],
 }
@@ -205,7 +208,8 @@ class Model:
 
 class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
-                 mem_budget_bytes=0, max_fuse=0, order=None):
+                 mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
+                 resident_chunk=0):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -213,6 +217,8 @@ class Plan:
         o.batch = batch
         o.mem_budget_bytes = mem_budget_bytes
         o.max_fuse = max_fuse
+        o.executor = executor
+        o.resident_chunk = resident_chunk
         self._order_buf = None
         if order is not None:
             self._order_buf = np.ascontiguousarray(order, dtype=np.int32)
@@ -291,6 +297,12 @@ class Plan:
         check(lib().qgm_plan_profile(self._h, _ptr(d_bits), B, _ptr(d_out),
                                      ms.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
         return ms
+
+    def executor(self):
+        """(kind, chunk, smem_bytes) of the bound executor."""
+        k, c, m = C.c_int32(), C.c_int32(), C.c_int64()
+        check(lib().qgm_plan_get_executor(self._h, C.byref(k), C.byref(c), C.byref(m)))
+        return k.value, c.value, m.value
 
     def status(self, stream=None):
         return lib().qgm_status(self._h, _stream(stream))

@@ -271,6 +271,122 @@ __global__ void k_init(double2 *out, int64_t n_out, Header *hdr) {
   if (blockIdx.x == 0 && threadIdx.x == 0) hdr->slice_id = 0;
 }
 
+// ------------------------------------------------------------------------
+// Resident executor: one CTA per chunk of Bc bitstrings runs every step of
+// the plan with all of its tensors in shared memory; the only global reads
+// are the bitstrings and the unbatched gate tables (L1-resident), the only
+// global write is the chunk's FP64 amplitudes.  Steps are separated by
+// __syncthreads only: no grid-wide barrier, no launch per step.
+constexpr int RES_THREADS = 256;
+
+__device__ __forceinline__ void res_scale(const Meta *meta, int slot, Header *hdr, float *scale,
+                                          int *e_out) {
+  operand_scale(meta, slot, hdr, scale, e_out);
+}
+
+__global__ void __launch_bounds__(RES_THREADS)
+    k_resident(const char *ws, const RStep *steps, int n_steps, const RLeaf *rleaves, int n_rleaves,
+               const LeafDesc *leaves, const uint64_t *bits, int64_t B, int logBc, int n_meta,
+               int final_soff, int final_meta, int final_batched, double c_re, double c_im,
+               double2 *out, Header *hdr) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ RStep sd;
+  __shared__ float red[RES_THREADS / 32];
+  const int Bc = 1 << logBc;
+  const int tid = threadIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.x * Bc;
+  Meta *meta = reinterpret_cast<Meta *>(sm);
+  for (int i = tid; i < n_meta; i += RES_THREADS) {
+    meta[i].maxbits = 0;
+    meta[i].exp = 0;
+  }
+  // batched leaves of this chunk: entry (row r, beta) of the base table with
+  // the output bits of x_beta
+  for (int l = 0; l < n_rleaves; ++l) {
+    const RLeaf rl = rleaves[l];
+    const LeafDesc &d = leaves[rl.leaf];
+    const float2 *base = reinterpret_cast<const float2 *>(ws + d.base_off);
+    float2 *dst = reinterpret_cast<float2 *>(sm + rl.soff);
+    const int n = (1 << d.n_int) << logBc;
+    for (int t = tid; t < n; t += RES_THREADS) {
+      const int r = t >> logBc, b = t & (Bc - 1);
+      const uint64_t x = (b0 + b < B) ? bits[b0 + b] : 0ull;
+      int ob = 0;
+      for (int a = 0; a < d.n_out; ++a) ob |= (int)((x >> d.out_qubit[a]) & 1ull) << (d.n_out - 1 - a);
+      dst[t] = base[(r << d.n_out) | ob];
+    }
+  }
+  for (int s = 0; s < n_steps; ++s) {
+    __syncthreads();
+    {
+      const int *src = reinterpret_cast<const int *>(steps + s);
+      int *dstw = reinterpret_cast<int *>(&sd);
+      for (int w = tid; w < (int)(sizeof(RStep) / 4); w += RES_THREADS) dstw[w] = src[w];
+    }
+    __syncthreads();
+    float scale[MAXIN];
+    int esum = 0;
+#pragma unroll
+    for (int i = 0; i < MAXIN; ++i) {
+      if (i < sd.m) {
+        int e;
+        res_scale(meta, sd.in[i].meta, hdr, &scale[i], &e);
+        esum += e + (sd.in[i].meta >= 0 ? meta[sd.in[i].meta].exp : 0);
+      }
+    }
+    const int lb = sd.batched_out ? logBc : 0;
+    const int items = (1 << sd.w_out) << lb;
+    const int terms = 1 << sd.k;
+    float lmax = 0.f;
+    float2 *o = reinterpret_cast<float2 *>(sm + sd.out_soff);
+    for (int it = tid; it < items; it += RES_THREADS) {
+      const uint32_t row = (uint32_t)it >> lb;
+      const int beta = it & ((1 << lb) - 1);
+      float2 acc = make_float2(0.f, 0.f);
+      for (int e = 0; e < terms; ++e) {
+        const uint64_t f = ((uint64_t)e << sd.w_out) | row;
+        float2 pr = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < MAXIN; ++i) {
+          if (i < sd.m) {
+            const RIn &in = sd.in[i];
+            uint32_t idx = 0;
+            for (int q = 0; q < in.nruns; ++q)
+              idx |= (uint32_t)((f >> in.src[q]) & ((1u << in.len[q]) - 1u)) << in.dst[q];
+            float2 v;
+            if (in.soff < 0)
+              v = __ldg(reinterpret_cast<const float2 *>(ws + in.goff) + idx);
+            else
+              v = reinterpret_cast<const float2 *>(sm + in.soff)[in.batched ? ((idx << logBc) | beta) : idx];
+            pr = cmul(pr, make_float2(v.x * scale[i], v.y * scale[i]));
+          }
+        }
+        acc.x += pr.x;
+        acc.y += pr.y;
+      }
+      o[it] = acc;
+      lmax = fmaxf(lmax, absmax2(acc));
+    }
+    // block max -> the output's metadata (one writer, no atomics)
+    for (int q = 16; q > 0; q >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
+    if ((tid & 31) == 0) red[tid >> 5] = lmax;
+    __syncthreads();
+    if (tid == 0) {
+      float m = 0.f;
+      for (int w = 0; w < RES_THREADS / 32; ++w) m = fmaxf(m, red[w]);
+      meta[sd.out_meta].maxbits = __float_as_uint(m);
+      meta[sd.out_meta].exp = esum;
+    }
+  }
+  __syncthreads();
+  if (tid < Bc && b0 + tid < B) {
+    const float2 v = reinterpret_cast<const float2 *>(sm + final_soff)[final_batched ? tid : 0];
+    const double sc = ldexp(1.0, meta[final_meta].exp);
+    const double re = (double)v.x * sc, im = (double)v.y * sc;
+    out[b0 + tid] = make_double2(re * c_re - im * c_im, re * c_im + im * c_re);
+  }
+}
+
 }  // namespace
 
 struct qgm_exec_state {
@@ -282,6 +398,8 @@ struct qgm_exec_state {
   void *g_out = nullptr;
   int64_t g_B = -1;
   int sms = 148;
+  int kind = QGM_EXEC_STEPWISE;
+  int layout = -1;  // index into qgm_plan::resident
 };
 
 static int cuda_fail(cudaError_t e, const char *what) {
@@ -348,9 +466,30 @@ static int enqueue_slice(qgm_plan *p, const uint64_t *d_bits, int64_t B, double2
   return QGM_OK;
 }
 
+static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, double2 *d_out,
+                            cudaStream_t st) {
+  qgm_exec_state *x = p->exec;
+  const ResidentLayout &L = p->resident[x->layout];
+  const int logBc = __builtin_ctz(L.chunk);
+  const int64_t G = (B + L.chunk - 1) / L.chunk;
+  const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
+  const char *ws = x->ws;
+  k_resident<<<(unsigned)G, RES_THREADS, (size_t)L.smem_bytes, st>>>(
+      ws, reinterpret_cast<const RStep *>(ws + p->off_rsteps), (int)L.steps.size(),
+      reinterpret_cast<const RLeaf *>(ws + p->off_rsteps + L.steps.size() * sizeof(RStep)),
+      (int)L.leaves.size(), reinterpret_cast<const LeafDesc *>(ws + p->off_leafdesc), d_bits, B, logBc,
+      p->n_meta, L.final_soff, L.final_meta, p->final_batched, c.real(), c.imag(), d_out,
+      reinterpret_cast<Header *>(x->ws + p->off_header));
+}
+
 static int run(qgm_plan *p, const uint64_t *d_bits, int64_t B, double2 *d_out, int64_t n_out,
                cudaStream_t st) {
   qgm_exec_state *x = p->exec;
+  if (x->kind == QGM_EXEC_RESIDENT) {
+    launch_resident(p, d_bits, B, d_out, st);
+    CK(cudaGetLastError());
+    return QGM_OK;
+  }
   Header *hdr = reinterpret_cast<Header *>(x->ws + p->off_header);
   const int64_t nslices = (int64_t)1 << p->slice_vars.size();
   if (!x->graph || x->g_bits != d_bits || x->g_out != d_out || x->g_B != B) {
@@ -436,7 +575,56 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
   if (!p->leafdesc.empty())
     CK(cudaMemcpyAsync(x->ws + p->off_leafdesc, p->leafdesc.data(), p->leafdesc.size() * sizeof(LeafDesc),
                        cudaMemcpyHostToDevice, st));
-  CK(cudaStreamSynchronize(st));
+  // executor: resident when a layout fits; chunk size by fewest waves x chunk
+  x->kind = QGM_EXEC_STEPWISE;
+  x->layout = -1;
+  if (p->executor_pref != QGM_EXEC_STEPWISE && !p->resident.empty()) {
+    int optin = 0;
+    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, x->device));
+    double best = -1;
+    for (size_t li = 0; li < p->resident.size(); ++li) {
+      const ResidentLayout &L = p->resident[li];
+      if (p->opts.resident_chunk > 0 && L.chunk != p->opts.resident_chunk) continue;
+      if (L.smem_bytes + (int64_t)sizeof(RStep) + 64 > optin) continue;
+      CK(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+      int cps = 0;
+      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_resident, RES_THREADS, (size_t)L.smem_bytes));
+      if (cps < 1) continue;
+      const int64_t G = (p->batch + L.chunk - 1) / L.chunk;
+      const int64_t waves = (G + (int64_t)x->sms * cps - 1) / ((int64_t)x->sms * cps);
+      const double cost = (double)waves * L.chunk;
+      if (best < 0 || cost < best) {
+        best = cost;
+        x->layout = (int)li;
+      }
+    }
+    if (x->layout >= 0) {
+      const ResidentLayout &L = p->resident[x->layout];
+      CK(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+      CK(cudaMemcpyAsync(x->ws + p->off_rsteps, L.steps.data(), L.steps.size() * sizeof(RStep),
+                         cudaMemcpyHostToDevice, st));
+      if (!L.leaves.empty())
+        CK(cudaMemcpyAsync(x->ws + p->off_rsteps + L.steps.size() * sizeof(RStep), L.leaves.data(),
+                           L.leaves.size() * sizeof(RLeaf), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+      x->kind = QGM_EXEC_RESIDENT;
+    } else if (p->executor_pref == QGM_EXEC_RESIDENT) {
+      set_error("qgm_plan_bind: no resident layout fits this device's shared memory");
+      return QGM_ERR_ARG;
+    }
+  }
+  return QGM_OK;
+}
+
+int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int64_t *smem_bytes) {
+  if (!p || !p->exec) {
+    set_error("qgm_plan_get_executor: plan not bound");
+    return QGM_ERR_ARG;
+  }
+  const qgm_exec_state *x = p->exec;
+  if (kind) *kind = x->kind;
+  if (chunk) *chunk = x->kind == QGM_EXEC_RESIDENT ? p->resident[x->layout].chunk : (int32_t)p->Bp;
+  if (smem_bytes) *smem_bytes = x->kind == QGM_EXEC_RESIDENT ? p->resident[x->layout].smem_bytes : 0;
   return QGM_OK;
 }
 
@@ -497,6 +685,21 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int n = (int)p->steps.size() + 2;
+  if (p->exec->kind == QGM_EXEC_RESIDENT) {
+    cudaEvent_t a, b;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    CK(cudaEventRecord(a, st));
+    launch_resident(p, d_bitstrings, B, reinterpret_cast<double2 *>(d_out), st);
+    CK(cudaEventRecord(b, st));
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(b));
+    for (int i = 0; i < n; ++i) ms[i] = 0.f;
+    CK(cudaEventElapsedTime(&ms[0], a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return QGM_OK;
+  }
   std::vector<cudaEvent_t> ev(n + 1);
   for (auto &e : ev) CK(cudaEventCreate(&e));
   Header *hdr = reinterpret_cast<Header *>(p->exec->ws + p->off_header);

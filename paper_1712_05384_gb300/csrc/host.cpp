@@ -389,7 +389,8 @@ static std::vector<int> order_vertical(const qgm_plan *p, const std::vector<char
 struct Arena {
   std::map<int64_t, int64_t> free_;  // off -> size
   int64_t top = 0, peak = 0;
-  static int64_t align(int64_t x) { return (x + 255) & ~int64_t(255); }
+  int64_t al = 256;
+  int64_t align(int64_t x) const { return (x + al - 1) & ~(al - 1); }
   int64_t alloc(int64_t bytes) {
     bytes = align(std::max<int64_t>(bytes, 1));
     for (auto it = free_.begin(); it != free_.end(); ++it) {
@@ -582,6 +583,72 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
 }
 
 static int64_t pow2(int r) { return (int64_t)1 << r; }
+
+// Shared-memory layouts of the resident executor for chunks of Bc batch
+// entries: metadata slots first, then an arena holding the batched leaves
+// and every intermediate of the chunk with the stepwise plan's liveness.
+static void build_resident(qgm_plan *p) {
+  p->resident.clear();
+  if (p->output_mode != QGM_OUT_BATCH || !p->slice_vars.empty()) return;
+  const SimResult &S = p->sim;
+  const int nl = (int)p->leaves.size();
+  const int64_t meta_bytes = ((int64_t)p->n_meta * 8 + 15) & ~int64_t(15);
+  for (int Bc : {1, 2, 4, 8}) {
+    ResidentLayout L;
+    L.chunk = Bc;
+    Arena arena;
+    arena.al = 16;
+    std::vector<int64_t> soff(S.tensors.size(), -1);
+    auto bytes_of = [&](const SymTensor &t) {
+      return pow2((int)t.vars.size()) * (t.batched ? Bc : 1) * 8;
+    };
+    for (int li = 0; li < nl; ++li)
+      if (S.tensors[li].batched) {
+        soff[li] = arena.alloc(bytes_of(S.tensors[li]));
+        L.leaves.push_back({li, (int32_t)(meta_bytes + soff[li])});
+      }
+    for (size_t si = 0; si < S.steps.size(); ++si) {
+      const StepRec &st = S.steps[si];
+      const SymTensor &ot = S.tensors[st.out];
+      soff[st.out] = arena.alloc(bytes_of(ot));
+      for (int id : st.inputs)
+        if (soff[id] >= 0) arena.release(soff[id], bytes_of(S.tensors[id]));
+      const StepDesc &d = p->steps[si];
+      RStep r{};
+      r.m = d.m;
+      r.k = d.k;
+      r.w_out = d.w_out;
+      r.batched_out = d.batched_out;
+      r.out_soff = (int32_t)(meta_bytes + soff[st.out]);
+      r.out_meta = ot.meta;
+      for (int i = 0; i < d.m; ++i) {
+        const SymTensor &it = S.tensors[st.inputs[i]];
+        RIn &in = r.in[i];
+        in.batched = it.batched ? 1 : 0;
+        in.meta = it.leaf < 0 ? it.meta : -1;
+        if (it.leaf >= 0 && !it.batched) {
+          in.soff = -1;
+          in.goff = p->leafdesc[it.leaf].base_off;  // no slices: base table = leaf table
+        } else {
+          in.soff = (int32_t)(meta_bytes + soff[st.inputs[i]]);
+          in.goff = 0;
+        }
+        in.nruns = (uint8_t)d.in[i].nruns;
+        for (int q = 0; q < d.in[i].nruns; ++q) {
+          in.src[q] = d.in[i].src[q];
+          in.len[q] = d.in[i].len[q];
+          in.dst[q] = d.in[i].dst[q];
+        }
+      }
+      L.steps.push_back(r);
+    }
+    L.final_soff = (int)(meta_bytes + soff[S.final_tensor]);
+    L.final_meta = S.tensors[S.final_tensor].meta;
+    L.smem_bytes = meta_bytes + arena.peak;
+    if (L.smem_bytes > 200 * 1024) break;  // larger chunks only grow
+    p->resident.push_back(L);
+  }
+}
 
 int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   p->model = m;
@@ -811,6 +878,8 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   int64_t out_elems = o.output_mode == QGM_OUT_BATCH ? Bp : p->final_entries;
   p->off_outstage = take(out_elems * 16);
   p->off_acc = take(out_elems * 16);
+  p->off_rsteps = take((int64_t)(S.steps.size() + 1) * sizeof(RStep) +
+                       (int64_t)(p->leaves.size() + 1) * sizeof(RLeaf));
   p->off_arena = take(0);
   for (SymTensor &t : S.tensors)
     if (t.leaf < 0) t.off += p->off_arena;
@@ -820,6 +889,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
 
   // step descriptors
   p->steps.clear();
+  p->executor_pref = o.executor;
   for (const StepRec &s : S.steps) {
     StepDesc d{};
     d.m = (int)s.inputs.size();
@@ -863,6 +933,21 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
       in.nruns = nr;
     }
     p->steps.push_back(d);
+  }
+  build_resident(p);
+  if (o.executor < 0 || o.executor > 2) {
+    set_error("qgm_plan_order: bad executor %d", o.executor);
+    return QGM_ERR_ARG;
+  }
+  if (o.resident_chunk != 0 && o.resident_chunk != 1 && o.resident_chunk != 2 &&
+      o.resident_chunk != 4 && o.resident_chunk != 8) {
+    set_error("qgm_plan_order: resident_chunk must be 0, 1, 2, 4 or 8");
+    return QGM_ERR_ARG;
+  }
+  if (o.executor == QGM_EXEC_RESIDENT && p->resident.empty()) {
+    set_error("qgm_plan_order: the resident executor needs a batch plan without slices whose "
+              "per-bitstring live set fits in shared memory");
+    return QGM_ERR_ARG;
   }
   return QGM_OK;
 }

@@ -80,6 +80,37 @@ struct LeafDesc {
   int32_t out_qubit[MAXLEAFV];  // qubit of each output var
 };
 
+// Resident executor: one CTA per chunk of Bc batch entries runs every step
+// with its tensors in shared memory.  Offsets are bytes into dynamic smem.
+struct RIn {
+  int32_t soff;      // smem offset, or -1: unbatched leaf read from global
+  int32_t meta;      // smem metadata slot (intermediates), -1 for leaves
+  int64_t goff;      // global offset of an unbatched leaf
+  uint8_t batched;
+  uint8_t nruns;
+  uint8_t pad_[2];
+  uint8_t src[MAXRUN], len[MAXRUN], dst[MAXRUN];
+};
+
+struct RStep {
+  int32_t m, k, w_out, batched_out;
+  int32_t out_soff, out_meta;
+  RIn in[MAXIN];
+};
+
+struct RLeaf {        // batched leaf materialised in smem per chunk
+  int32_t leaf;       // index into the LeafDesc table
+  int32_t soff;
+};
+
+struct ResidentLayout {
+  int chunk = 0;            // Bc
+  int64_t smem_bytes = 0;   // dynamic shared memory per CTA
+  std::vector<RStep> steps;
+  std::vector<RLeaf> leaves;
+  int final_soff = -1, final_meta = -1;
+};
+
 struct SymTensor {
   std::vector<int> vars;  // sorted by elimination position
   bool batched = false;
@@ -155,6 +186,10 @@ struct qgm_plan {
   int final_batched = 0;
   int64_t final_off = 0;
   int final_meta = -1;
+  // resident executor layouts for Bc = 1, 2, 4, 8 (empty when infeasible)
+  std::vector<qgm::ResidentLayout> resident;
+  int64_t off_rsteps = 0;   // workspace region for the chosen layout's steps
+  int executor_pref = 0;    // qgm_plan_opts.executor
   qgm_exec_state *exec = nullptr;
 };
 

@@ -20,6 +20,7 @@ from oracle import ve
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+EXECS = [1, 2]   # stepwise, resident
 REL_TOL = 1e-5
 ABS_TOL = 1e-5   # on |a - a_ref| * 2^{n/2}
 
@@ -45,7 +46,7 @@ def errors(a, ref, n):
     return rel, np.max(np.abs(a - ref)) * 2.0 ** (n / 2)
 
 
-def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0):
+def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0, executor=0):
     q = Q()
     if circuit_py.rows:
         c = q.Circuit.grid(circuit_py.rows, circuit_py.cols, circuit_py.depth, circuit_py.seed,
@@ -53,7 +54,9 @@ def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0):
     else:
         c = q.Circuit.from_gates(circuit_py.n, circuit_py.gates)
     p = q.Plan(q.Model(c), order_kind=order_kind, batch=B, mem_budget_bytes=budget,
-               max_fuse=max_fuse).bind()
+               max_fuse=max_fuse, executor=executor).bind()
+    if executor:
+        assert p.executor()[0] == executor
     if bits is None:
         bits = qi.bitstrings(circuit_py.n, B, circuit_py.seed)
     d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
@@ -65,27 +68,30 @@ def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0):
     return o[0::2] + 1j * o[1::2], bits, p
 
 
-def test_app_d_example(app_d):
-    a, bits, _ = run_batch(app_d, 4, bits=np.arange(4, dtype=np.uint64))
+@pytest.mark.parametrize("executor", EXECS)
+def test_app_d_example(app_d, executor):
+    a, bits, _ = run_batch(app_d, 4, bits=np.arange(4, dtype=np.uint64), executor=executor)
     ref = sv.state(app_d)
     assert abs(a[0] - 0.5) < 1e-7          # App. D: <00|C|00> = 1/2
     assert np.allclose(a, ref, atol=1e-7)
 
 
+@pytest.mark.parametrize("executor", EXECS)
 @pytest.mark.parametrize("rows,cols,depth,B", [(3, 3, 8, 37), (4, 4, 12, 64), (2, 5, 16, 5),
                                                (3, 4, 20, 130)])
-def test_small_grids_vs_state_vector(rows, cols, depth, B):
+def test_small_grids_vs_state_vector(rows, cols, depth, B, executor):
     c = qi.grid_circuit(rows, cols, depth, seed=2)
-    a, bits, _ = run_batch(c, B)
+    a, bits, _ = run_batch(c, B, executor=executor)
     ref = sv.amplitudes(c, bits)
     rel, ab = errors(a, ref, c.n)
     assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
 
 
+@pytest.mark.parametrize("executor", EXECS)
 @pytest.mark.parametrize("kind", [1, 2, 3])
-def test_every_order_kind(kind):
+def test_every_order_kind(kind, executor):
     c = qi.grid_circuit(4, 4, 14, seed=5)
-    a, bits, p = run_batch(c, 48, order_kind=kind)
+    a, bits, p = run_batch(c, 48, order_kind=kind, executor=executor)
     assert p.info.order_kind == kind
     rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
     assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
@@ -101,27 +107,30 @@ def test_sliced_equals_unsliced():
     assert np.max(np.abs(a1 - a0)) * 2 ** (c.n / 2) < 1e-5
 
 
-def test_fusion_limits_agree():
+@pytest.mark.parametrize("executor", EXECS)
+def test_fusion_limits_agree(executor):
     c = qi.grid_circuit(4, 4, 16, seed=9)
-    a1, bits, _ = run_batch(c, 24, max_fuse=1)
-    a8, _, _ = run_batch(c, 24, max_fuse=8)
+    a1, bits, _ = run_batch(c, 24, max_fuse=1, executor=executor)
+    a8, _, _ = run_batch(c, 24, max_fuse=8, executor=executor)
     ref = sv.amplitudes(c, bits)
     for a in (a1, a8):
         rel, ab = errors(a, ref, c.n)
         assert rel < REL_TOL and ab < ABS_TOL
 
 
-def test_parametrised_circuit():
+@pytest.mark.parametrize("executor", EXECS)
+def test_parametrised_circuit(executor):
     c = qi.grid_circuit(3, 4, 14, seed=4, param=True)
-    a, bits, _ = run_batch(c, 33)
+    a, bits, _ = run_batch(c, 33, executor=executor)
     rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
     assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
 
 
-def test_depth_one_is_uniform():
+@pytest.mark.parametrize("executor", EXECS)
+def test_depth_one_is_uniform(executor):
     # only the H layer: every amplitude is 2^{-n/2}
     c = qi.grid_circuit(3, 3, 1, seed=0)
-    a, _, _ = run_batch(c, 12)
+    a, _, _ = run_batch(c, 12, executor=executor)
     assert np.allclose(a, 2 ** -4.5, rtol=1e-7, atol=0)
 
 
@@ -142,11 +151,14 @@ def test_open_outputs_4x4_d10_all_amplitudes():
     assert np.allclose(a, ve.open_amplitudes(c), atol=1e-6 * 2 ** -8)
 
 
-def test_grid5x5_d20_b1024_sampled():
-    # full-size workload, the launch configuration the benchmark times;
-    # 64 sampled outputs against the oracle's own elimination
+@pytest.mark.parametrize("executor", [0, 1])
+def test_grid5x5_d20_b1024_sampled(executor):
+    # full-size workload; executor 0 (auto) is the launch configuration the
+    # benchmark times; 64 sampled outputs against the oracle's own elimination
     c = qi.grid_circuit(5, 5, 20, 0)
-    a, bits, p = run_batch(c, 1024)
+    a, bits, p = run_batch(c, 1024, executor=executor)
+    if executor == 0:
+        assert p.executor()[0] == 2
     idx = np.linspace(0, 1023, 64).astype(int)
     ref = ve.amplitudes(c, bits[idx])
     rel, ab = errors(a[idx], ref, c.n)
@@ -157,11 +169,12 @@ def test_grid5x5_d20_b1024_sampled():
     assert abs((Np ** 2).mean() - 2) < 4 * math.sqrt(20 / 1024)
 
 
-def test_host_api_matches_device_api():
+@pytest.mark.parametrize("executor", EXECS)
+def test_host_api_matches_device_api(executor):
     q = Q()
     c = qi.grid_circuit(4, 4, 12, 3)
     bits = qi.bitstrings(16, 50, 3)
-    a_dev, _, p = run_batch(c, 50, bits=bits)
+    a_dev, _, p = run_batch(c, 50, bits=bits, executor=executor)
     a_host = p.amplitudes_host(bits)
     assert np.array_equal(a_dev, a_host)
     # a second call with fewer bitstrings reuses the plan
@@ -185,3 +198,24 @@ def test_errors_are_reported():
         p.amplitudes(d_bits, d_out, B=9)          # more than the plan's batch
     with pytest.raises(q.QgmError):
         p.eliminate(d_out)                        # not an open-output plan
+    sliced = q.Plan(q.Model(q.Circuit.grid(4, 5, 16, 1)), order_kind=1, batch=8,
+                    mem_budget_bytes=4096)
+    assert sliced.info.n_slices > 1
+    with pytest.raises(q.QgmError):               # resident needs one slice
+        q.Plan(q.Model(q.Circuit.grid(4, 5, 16, 1)), order_kind=1, batch=8,
+               mem_budget_bytes=4096, executor=2)
+
+
+@pytest.mark.parametrize("chunk", [1, 2, 4, 8])
+def test_resident_chunks_agree(chunk):
+    # bitstrings per CTA 1..8, batch 77 leaves a ragged last chunk
+    q = Q()
+    c = qi.grid_circuit(4, 4, 16, 6)
+    bits = qi.bitstrings(16, 77, 6)
+    ref = sv.amplitudes(c, bits)
+    p = q.Plan(q.Model(q.Circuit.grid(4, 4, 16, 6)), batch=77, executor=2,
+               resident_chunk=chunk).bind()
+    assert p.executor()[:2] == (2, chunk)
+    a = p.amplitudes_host(bits)
+    rel, ab = errors(a, ref, c.n)
+    assert rel < REL_TOL and ab < ABS_TOL
