@@ -96,11 +96,12 @@ __device__ __forceinline__ float absmax2(float2 a) { return fmaxf(fabsf(a.x), fa
 __device__ __forceinline__ void record_max(float v, Meta *meta, int slot) {
   __shared__ float red[32];
   for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = t & 31, wid = t >> 5;
   if (lane == 0) red[wid] = v;
   __syncthreads();
   if (wid == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
+    const int nw = (blockDim.x * blockDim.y + 31) >> 5;
     v = lane < nw ? red[lane] : 0.f;
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (lane == 0 && v > 0.f) atomicMax(&meta[slot].maxbits, __float_as_uint(v));
@@ -141,10 +142,13 @@ __global__ void k_build_leaves(char *ws, const LeafDesc *leaves, int n_leaves, M
   }
 }
 
-// Product-sum step, batched output: thread = (row j, pair of batch entries).
-__global__ void __launch_bounds__(STEP_THREADS)
+// Product-sum step, batched output: thread (x, y) = (pair of batch entries,
+// term group); threadIdx.y splits the 2^k summed terms when rows are few.
+__global__ void __launch_bounds__(1024)
     k_step_batched(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp) {
-  const int bp = (blockIdx.x * STEP_THREADS + threadIdx.x) * 2;
+  __shared__ float4 part[1024];
+  const int tx = threadIdx.x, ty = threadIdx.y, T = blockDim.y;
+  const int bp = (blockIdx.x * STEP_THREADS + tx) * 2;
   const bool active = bp < Bp;
   float scale[MAXIN];
   int esum = 0;
@@ -156,40 +160,54 @@ __global__ void __launch_bounds__(STEP_THREADS)
       esum += e + (d.in[i].meta >= 0 ? meta[d.in[i].meta].exp : 0);
     }
   }
-  if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) meta[d.out_meta].exp = esum;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && tx == 0 && ty == 0) meta[d.out_meta].exp = esum;
   const uint64_t rows = 1ull << d.w_out;
   const uint64_t terms = 1ull << d.k;
   float lmax = 0.f;
   float2 *out = reinterpret_cast<float2 *>(ws + d.out_off);
   for (uint64_t j = blockIdx.y; j < rows; j += gridDim.y) {
-    if (!active) continue;
     float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-    for (uint64_t e = 0; e < terms; ++e) {
-      const uint64_t f = (e << d.w_out) | j;
-      float2 p0 = make_float2(1.f, 0.f), p1 = p0;
+    if (active) {
+      for (uint64_t e = ty; e < terms; e += T) {
+        const uint64_t f = (e << d.w_out) | j;
+        float2 p0 = make_float2(1.f, 0.f), p1 = p0;
 #pragma unroll
-      for (int i = 0; i < MAXIN; ++i) {
-        if (i < d.m) {
-          const InDesc &in = d.in[i];
-          const uint64_t idx = pext_runs(f, in);
-          if (in.batched) {
-            const float4 v = __ldg(reinterpret_cast<const float4 *>(ws + in.off) +
-                                   ((idx * (uint64_t)Bp + bp) >> 1));
-            p0 = cmul(p0, make_float2(v.x * scale[i], v.y * scale[i]));
-            p1 = cmul(p1, make_float2(v.z * scale[i], v.w * scale[i]));
-          } else {
-            const float2 v = __ldg(reinterpret_cast<const float2 *>(ws + in.off) + idx);
-            const float2 s = make_float2(v.x * scale[i], v.y * scale[i]);
-            p0 = cmul(p0, s);
-            p1 = cmul(p1, s);
+        for (int i = 0; i < MAXIN; ++i) {
+          if (i < d.m) {
+            const InDesc &in = d.in[i];
+            const uint64_t idx = pext_runs(f, in);
+            if (in.batched) {
+              const float4 v = __ldg(reinterpret_cast<const float4 *>(ws + in.off) +
+                                     ((idx * (uint64_t)Bp + bp) >> 1));
+              p0 = cmul(p0, make_float2(v.x * scale[i], v.y * scale[i]));
+              p1 = cmul(p1, make_float2(v.z * scale[i], v.w * scale[i]));
+            } else {
+              const float2 v = __ldg(reinterpret_cast<const float2 *>(ws + in.off) + idx);
+              const float2 sv = make_float2(v.x * scale[i], v.y * scale[i]);
+              p0 = cmul(p0, sv);
+              p1 = cmul(p1, sv);
+            }
           }
         }
+        a0.x += p0.x; a0.y += p0.y;
+        a1.x += p1.x; a1.y += p1.y;
       }
-      a0.x += p0.x; a0.y += p0.y;
-      a1.x += p1.x; a1.y += p1.y;
     }
-    reinterpret_cast<float4 *>(out)[(j * (uint64_t)Bp + bp) >> 1] = make_float4(a0.x, a0.y, a1.x, a1.y);
-    lmax = fmaxf(lmax, fmaxf(absmax2(a0), absmax2(a1)));
+    if (T > 1) {
+      part[ty * STEP_THREADS + tx] = make_float4(a0.x, a0.y, a1.x, a1.y);
+      __syncthreads();
+      if (ty == 0) {
+        for (int y = 1; y < T; ++y) {
+          const float4 q = part[y * STEP_THREADS + tx];
+          a0.x += q.x; a0.y += q.y; a1.x += q.z; a1.y += q.w;
+        }
+      }
+      __syncthreads();
+    }
+    if (active && ty == 0) {
+      reinterpret_cast<float4 *>(out)[(j * (uint64_t)Bp + bp) >> 1] = make_float4(a0.x, a0.y, a1.x, a1.y);
+      lmax = fmaxf(lmax, fmaxf(absmax2(a0), absmax2(a1)));
+    }
   }
   record_max(lmax, meta, d.out_meta);
 }
@@ -278,19 +296,102 @@ __global__ void k_init(double2 *out, int64_t n_out, Header *hdr) {
 // global write is the chunk's FP64 amplitudes.  Steps are separated by
 // __syncthreads only: no grid-wide barrier, no launch per step.
 constexpr int RES_THREADS = 256;
+constexpr int RSTEP_WORDS = (int)(sizeof(RStep) / 4);
+static_assert(RSTEP_WORDS <= RES_THREADS, "one descriptor word per thread");
 
-__device__ __forceinline__ void res_scale(const Meta *meta, int slot, Header *hdr, float *scale,
-                                          int *e_out) {
-  operand_scale(meta, slot, hdr, scale, e_out);
+// pext of the summed-variable index e by a k-bit mask (bits kept in order)
+__device__ __forceinline__ uint32_t pext_small(uint32_t e, uint32_t mask) {
+  uint32_t r = 0;
+  int o = 0;
+  while (mask) {
+    const int b = __ffs(mask) - 1;
+    r |= ((e >> b) & 1u) << o++;
+    mask &= mask - 1;
+  }
+  return r;
 }
 
-__global__ void __launch_bounds__(RES_THREADS)
+// One elimination step of the chunk with M inputs (M known at compile time so
+// the per-input state lives in registers for the whole term loop).
+template <int M>
+__device__ __forceinline__ float res_step(const RStep &S, char *sm, const float *scale, int logBc,
+                                          int tid) {
+  int soff[M], bsh[M], rb[M], nr[M];
+  uint32_t est[M], em[M];
+  bool egen[M];
+  const int k = S.k;
+  const uint32_t kfull = (1u << k) - 1u;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    soff[i] = S.in[i].soff;
+    bsh[i] = S.in[i].batched ? logBc : 0;
+    rb[i] = S.in[i].rowbits;
+    nr[i] = S.in[i].nruns;
+    em[i] = S.in[i].emask;
+    est[i] = em[i] == kfull ? (1u << rb[i]) : 0u;
+    egen[i] = em[i] != kfull && em[i] != 0u;
+  }
+  const int lb = S.batched_out ? logBc : 0;
+  const int items = (1 << S.w_out) << lb;
+  const int terms = 1 << k;
+  // lanes per item: split the summed terms when there are few items
+  int lg = 0;
+  while (lg < 5 && lg < k && (items << (lg + 1)) <= RES_THREADS) ++lg;
+  const int tpi = 1 << lg;
+  const int g = tid & (tpi - 1);
+  float lmax = 0.f;
+  float2 *o = reinterpret_cast<float2 *>(sm + S.out_soff);
+  for (int it0 = 0; it0 < items * tpi; it0 += RES_THREADS) {
+    const int it = (it0 + tid) >> lg;
+    const bool live = it < items;
+    float2 acc = make_float2(0.f, 0.f);
+    if (live) {
+      const uint32_t row = (uint32_t)it >> lb;
+      const uint32_t beta = (uint32_t)it & ((1u << lb) - 1u);
+      uint32_t ridx[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        uint32_t r = 0;
+        for (int q = 0; q < nr[i]; ++q) {
+          const uint32_t pr = S.in[i].prun[q];
+          r |= ((row >> (pr & 0xffu)) & (pr >> 16)) << ((pr >> 8) & 0xffu);
+        }
+        // fold the batch entry in now: element = (idx << bsh) | beta
+        ridx[i] = r;
+      }
+      for (int e = g; e < terms; e += tpi) {
+        float2 p = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          const uint32_t idx =
+              egen[i] ? (ridx[i] | (pext_small((uint32_t)e, em[i]) << rb[i])) : ridx[i] + (uint32_t)e * est[i];
+          const float2 v = reinterpret_cast<const float2 *>(sm + soff[i])[(idx << bsh[i]) | (bsh[i] ? beta : 0u)];
+          p = cmul(p, make_float2(v.x * scale[i], v.y * scale[i]));
+        }
+        acc.x += p.x;
+        acc.y += p.y;
+      }
+    }
+    // reduce the tpi partial sums of an item (aligned lane groups)
+    for (int q = 1; q < tpi; q <<= 1) {
+      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, q);
+      acc.y += __shfl_xor_sync(0xffffffffu, acc.y, q);
+    }
+    if (live && g == 0) {
+      o[it] = acc;
+      lmax = fmaxf(lmax, absmax2(acc));
+    }
+  }
+  return lmax;
+}
+
+__global__ void __launch_bounds__(RES_THREADS, 5)
     k_resident(const char *ws, const RStep *steps, int n_steps, const RLeaf *rleaves, int n_rleaves,
                const LeafDesc *leaves, const uint64_t *bits, int64_t B, int logBc, int n_meta,
                int final_soff, int final_meta, int final_batched, double c_re, double c_im,
                double2 *out, Header *hdr) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ RStep sd;
+  __shared__ RStep sd[2];
   __shared__ float red[RES_THREADS / 32];
   const int Bc = 1 << logBc;
   const int tid = threadIdx.x;
@@ -300,85 +401,70 @@ __global__ void __launch_bounds__(RES_THREADS)
     meta[i].maxbits = 0;
     meta[i].exp = 0;
   }
-  // batched leaves of this chunk: entry (row r, beta) of the base table with
-  // the output bits of x_beta
+  if (tid < RSTEP_WORDS && n_steps > 0)
+    reinterpret_cast<int *>(&sd[0])[tid] = __ldg(reinterpret_cast<const int *>(steps) + tid);
+  // leaves of this chunk: batched ones take entry (row r, beta) of the base
+  // table with the output bits of x_beta; unbatched ones are the table itself
   for (int l = 0; l < n_rleaves; ++l) {
     const RLeaf rl = rleaves[l];
     const LeafDesc &d = leaves[rl.leaf];
     const float2 *base = reinterpret_cast<const float2 *>(ws + d.base_off);
     float2 *dst = reinterpret_cast<float2 *>(sm + rl.soff);
+    if (!rl.batched) {
+      for (int t = tid; t < (1 << d.n_int); t += RES_THREADS) dst[t] = __ldg(base + t);
+      continue;
+    }
     const int n = (1 << d.n_int) << logBc;
     for (int t = tid; t < n; t += RES_THREADS) {
       const int r = t >> logBc, b = t & (Bc - 1);
       const uint64_t x = (b0 + b < B) ? bits[b0 + b] : 0ull;
       int ob = 0;
       for (int a = 0; a < d.n_out; ++a) ob |= (int)((x >> d.out_qubit[a]) & 1ull) << (d.n_out - 1 - a);
-      dst[t] = base[(r << d.n_out) | ob];
+      dst[t] = __ldg(base + ((r << d.n_out) | ob));
     }
   }
+  __syncthreads();
   for (int s = 0; s < n_steps; ++s) {
-    __syncthreads();
-    {
-      const int *src = reinterpret_cast<const int *>(steps + s);
-      int *dstw = reinterpret_cast<int *>(&sd);
-      for (int w = tid; w < (int)(sizeof(RStep) / 4); w += RES_THREADS) dstw[w] = src[w];
-    }
-    __syncthreads();
+    const RStep &S = sd[s & 1];
+    // prefetch the next descriptor into registers; stored after the compute
+    int nextw = 0;
+    if (s + 1 < n_steps && tid < RSTEP_WORDS)
+      nextw = __ldg(reinterpret_cast<const int *>(steps + s + 1) + tid);
     float scale[MAXIN];
     int esum = 0;
 #pragma unroll
     for (int i = 0; i < MAXIN; ++i) {
-      if (i < sd.m) {
+      scale[i] = 1.f;
+      if (i < S.m) {
         int e;
-        res_scale(meta, sd.in[i].meta, hdr, &scale[i], &e);
-        esum += e + (sd.in[i].meta >= 0 ? meta[sd.in[i].meta].exp : 0);
+        operand_scale(meta, S.in[i].meta, hdr, &scale[i], &e);
+        esum += e + (S.in[i].meta >= 0 ? meta[S.in[i].meta].exp : 0);
       }
     }
-    const int lb = sd.batched_out ? logBc : 0;
-    const int items = (1 << sd.w_out) << lb;
-    const int terms = 1 << sd.k;
-    float lmax = 0.f;
-    float2 *o = reinterpret_cast<float2 *>(sm + sd.out_soff);
-    for (int it = tid; it < items; it += RES_THREADS) {
-      const uint32_t row = (uint32_t)it >> lb;
-      const int beta = it & ((1 << lb) - 1);
-      float2 acc = make_float2(0.f, 0.f);
-      for (int e = 0; e < terms; ++e) {
-        const uint64_t f = ((uint64_t)e << sd.w_out) | row;
-        float2 pr = make_float2(1.f, 0.f);
-#pragma unroll
-        for (int i = 0; i < MAXIN; ++i) {
-          if (i < sd.m) {
-            const RIn &in = sd.in[i];
-            uint32_t idx = 0;
-            for (int q = 0; q < in.nruns; ++q)
-              idx |= (uint32_t)((f >> in.src[q]) & ((1u << in.len[q]) - 1u)) << in.dst[q];
-            float2 v;
-            if (in.soff < 0)
-              v = __ldg(reinterpret_cast<const float2 *>(ws + in.goff) + idx);
-            else
-              v = reinterpret_cast<const float2 *>(sm + in.soff)[in.batched ? ((idx << logBc) | beta) : idx];
-            pr = cmul(pr, make_float2(v.x * scale[i], v.y * scale[i]));
-          }
-        }
-        acc.x += pr.x;
-        acc.y += pr.y;
-      }
-      o[it] = acc;
-      lmax = fmaxf(lmax, absmax2(acc));
+    float lmax;
+    switch (S.m) {
+      case 1: lmax = res_step<1>(S, sm, scale, logBc, tid); break;
+      case 2: lmax = res_step<2>(S, sm, scale, logBc, tid); break;
+      case 3: lmax = res_step<3>(S, sm, scale, logBc, tid); break;
+      case 4: lmax = res_step<4>(S, sm, scale, logBc, tid); break;
+      case 5: lmax = res_step<5>(S, sm, scale, logBc, tid); break;
+      case 6: lmax = res_step<6>(S, sm, scale, logBc, tid); break;
+      case 7: lmax = res_step<7>(S, sm, scale, logBc, tid); break;
+      default: lmax = res_step<8>(S, sm, scale, logBc, tid); break;
     }
-    // block max -> the output's metadata (one writer, no atomics)
+    // block max -> the output's metadata; next descriptor -> the other buffer
     for (int q = 16; q > 0; q >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
     if ((tid & 31) == 0) red[tid >> 5] = lmax;
+    if (s + 1 < n_steps && tid < RSTEP_WORDS) reinterpret_cast<int *>(&sd[(s + 1) & 1])[tid] = nextw;
     __syncthreads();
     if (tid == 0) {
       float m = 0.f;
       for (int w = 0; w < RES_THREADS / 32; ++w) m = fmaxf(m, red[w]);
-      meta[sd.out_meta].maxbits = __float_as_uint(m);
-      meta[sd.out_meta].exp = esum;
+      meta[S.out_meta].maxbits = __float_as_uint(m);
+      meta[S.out_meta].exp = esum;
     }
+    __syncthreads();
   }
-  __syncthreads();
   if (tid < Bc && b0 + tid < B) {
     const float2 v = reinterpret_cast<const float2 *>(sm + final_soff)[final_batched ? tid : 0];
     const double sc = ldexp(1.0, meta[final_meta].exp);
@@ -438,8 +524,13 @@ static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st) {
   if (d.batched_out) {
     const int bx = (p->Bp / 2 + STEP_THREADS - 1) / STEP_THREADS;
     const uint64_t cap = (uint64_t)std::max(1, x->sms * 16 / bx);
+    // split the summed terms over threadIdx.y while the grid is small
+    int T = 1;
+    while (T < 8 && (T * 2) <= (1 << std::min(d.k, 4)) &&
+           rows * (uint64_t)bx * STEP_THREADS * T < (uint64_t)x->sms * 1024)
+      T *= 2;
     dim3 grid(bx, (unsigned)std::min<uint64_t>(rows, std::min<uint64_t>(cap, 65535)));
-    k_step_batched<<<grid, STEP_THREADS, 0, st>>>(ws, d, meta, hdr, p->Bp);
+    k_step_batched<<<grid, dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, p->Bp);
   } else {
     const uint64_t blocks = (rows + 255) / 256;
     k_step_plain<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)x->sms * 8), 256, 0, st>>>(ws, d, meta, hdr);

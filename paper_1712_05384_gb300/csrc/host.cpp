@@ -602,11 +602,11 @@ static void build_resident(qgm_plan *p) {
     auto bytes_of = [&](const SymTensor &t) {
       return pow2((int)t.vars.size()) * (t.batched ? Bc : 1) * 8;
     };
-    for (int li = 0; li < nl; ++li)
-      if (S.tensors[li].batched) {
-        soff[li] = arena.alloc(bytes_of(S.tensors[li]));
-        L.leaves.push_back({li, (int32_t)(meta_bytes + soff[li])});
-      }
+    bool ok = true;
+    for (int li = 0; li < nl; ++li) {
+      soff[li] = arena.alloc(bytes_of(S.tensors[li]));
+      L.leaves.push_back({li, (int32_t)(meta_bytes + soff[li]), S.tensors[li].batched ? 1 : 0, 0});
+    }
     for (size_t si = 0; si < S.steps.size(); ++si) {
       const StepRec &st = S.steps[si];
       const SymTensor &ot = S.tensors[st.out];
@@ -626,22 +626,31 @@ static void build_resident(qgm_plan *p) {
         RIn &in = r.in[i];
         in.batched = it.batched ? 1 : 0;
         in.meta = it.leaf < 0 ? it.meta : -1;
-        if (it.leaf >= 0 && !it.batched) {
-          in.soff = -1;
-          in.goff = p->leafdesc[it.leaf].base_off;  // no slices: base table = leaf table
-        } else {
-          in.soff = (int32_t)(meta_bytes + soff[st.inputs[i]]);
-          in.goff = 0;
-        }
-        in.nruns = (uint8_t)d.in[i].nruns;
+        in.soff = (int32_t)(meta_bytes + soff[st.inputs[i]]);
+        // split the union runs at the row/summed boundary (bit w_out)
+        int nr = 0, rowbits = 0;
+        uint32_t emask = 0;
         for (int q = 0; q < d.in[i].nruns; ++q) {
-          in.src[q] = d.in[i].src[q];
-          in.len[q] = d.in[i].len[q];
-          in.dst[q] = d.in[i].dst[q];
+          int a = d.in[i].src[q], b = a + d.in[i].len[q];
+          if (a < d.w_out) {
+            int hi = std::min(b, d.w_out);
+            if (nr >= RMAXRUN || hi - a > 16) {
+              ok = false;
+              break;
+            }
+            in.prun[nr] = (uint32_t)a | ((uint32_t)rowbits << 8) | (((1u << (hi - a)) - 1u) << 16);
+            rowbits += hi - a;
+            ++nr;
+          }
+          for (int bit = std::max(a, d.w_out); bit < b; ++bit) emask |= 1u << (bit - d.w_out);
         }
+        in.nruns = (uint8_t)nr;
+        in.rowbits = (uint8_t)rowbits;
+        in.emask = (uint16_t)emask;
       }
       L.steps.push_back(r);
     }
+    if (!ok) break;  // an index map too fragmented for the resident kernel
     L.final_soff = (int)(meta_bytes + soff[S.final_tensor]);
     L.final_meta = S.tensors[S.final_tensor].meta;
     L.smem_bytes = meta_bytes + arena.peak;

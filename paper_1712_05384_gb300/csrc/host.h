@@ -82,14 +82,22 @@ struct LeafDesc {
 
 // Resident executor: one CTA per chunk of Bc batch entries runs every step
 // with its tensors in shared memory.  Offsets are bytes into dynamic smem.
+// Input index = pext(row, runs) | (pext(e, emask) << rowbits): the summed
+// variables are the top bits of the union index and, the input's variables
+// being sorted the same way, the top bits of the input index too.
+constexpr int RMAXRUN = 6;  // row runs of one resident input
 struct RIn {
-  int32_t soff;      // smem offset, or -1: unbatched leaf read from global
+  int32_t soff;      // smem byte offset of the tensor
   int32_t meta;      // smem metadata slot (intermediates), -1 for leaves
-  int64_t goff;      // global offset of an unbatched leaf
   uint8_t batched;
-  uint8_t nruns;
-  uint8_t pad_[2];
-  uint8_t src[MAXRUN], len[MAXRUN], dst[MAXRUN];
+  uint8_t nruns;     // runs over the row (output) bits only
+  uint8_t rowbits;   // input bits that come from the row
+  uint8_t pad_;
+  uint16_t emask;    // which of the k summed variables the input holds
+  uint16_t pad2_;
+  // run q: bits [src, src + len) of the row go to bits [dst, dst + len) of
+  // the index; packed as src | dst << 8 | ((1 << len) - 1) << 16
+  uint32_t prun[RMAXRUN];
 };
 
 struct RStep {
@@ -98,9 +106,11 @@ struct RStep {
   RIn in[MAXIN];
 };
 
-struct RLeaf {        // batched leaf materialised in smem per chunk
+struct RLeaf {        // leaf materialised in smem per chunk
   int32_t leaf;       // index into the LeafDesc table
   int32_t soff;
+  int32_t batched;    // 1: rows x Bc entries from the bitstrings; 0: the table
+  int32_t pad_;
 };
 
 struct ResidentLayout {
