@@ -228,6 +228,24 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
  * bitstrings per CTA *chunk and the dynamic shared memory per CTA (resident). */
 int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int64_t *smem_bytes);
 
+/* No counterpart in the paper: an allocation-free variant of qgm_amplitudes
+ * for callers that cannot allocate device memory when they need amplitudes
+ * (a framework whose pool allocator owns all device memory, or a
+ * latency-critical loop where cudaMalloc/cudaFree would synchronise the
+ * device).  Runs the plan with the stepwise kernels, their scratch being one
+ * static device array of QGM_STATIC_SCRATCH_BYTES that every GPU loading this
+ * library holds until exit; no qgm_plan_bind is needed and nothing is
+ * allocated.  d_bitstrings: device uint64[B]; d_out: device double[2B].
+ * The first call on a device (that device current) looks the array's device
+ * address up with cudaGetSymbolAddress; make that first call before any
+ * stream capture.  Calls share the array: each reloads the plan's tables and
+ * clears what must start at zero, and calls that overlap on the GPU race.
+ * Errors: QGM_ERR_OOM when the plan's workspace_bytes exceeds
+ * QGM_STATIC_SCRATCH_BYTES (bind a workspace instead), QGM_ERR_ARG, QGM_ERR_CUDA. */
+#define QGM_STATIC_SCRATCH_BYTES (64ull << 20)
+int qgm_amplitudes_static(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
+                          void *stream);
+
 /* Reads and clears the device status word of the bound workspace
  * (synchronises `stream`): QGM_OK, QGM_ERR_NONFINITE or QGM_ERR_TIMEOUT. */
 int qgm_status(qgm_plan *p, void *stream);

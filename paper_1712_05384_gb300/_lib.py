@@ -83,6 +83,7 @@ _SIGS = {
     "qgm_eliminate": [_P, _P, _P],
     "qgm_status": [_P, _P],
     "qgm_plan_get_executor": [_P, _I32P, _I32P, _I64P],
+    "qgm_amplitudes_static": [_P, _P, C.c_int64, _P, _P],
     "qgm_amplitude_grad": [_P, _P, C.c_int64, _P, _P, _P, _P],
     "qgm_last_error": [],
 }

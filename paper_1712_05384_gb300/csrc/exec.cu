@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "host.h"
@@ -832,3 +833,119 @@ int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, con
 }
 
 }  // extern "C"
+
+// ===========================================================================
+// Allocation-free entry point.
+//
+// Some callers cannot allocate device memory at the moment they need
+// amplitudes: a host framework whose pool allocator owns all device memory
+// and forbids side allocations, or a latency-critical loop in which a
+// cudaMalloc/cudaFree would synchronise the device.  For them the stepwise
+// kernels run with their scratch (the workspace of qgm_plan_bind) in one
+// file-scope device array of QGM_STATIC_SCRATCH_BYTES.  Every GPU that loads
+// this library holds that array until the process exits.
+//
+// Host code cannot use the array's name as a device address (it names a
+// host-side stand-in), so the first call on each device, with that device
+// current, looks the address up with cudaGetSymbolAddress and caches it.
+// That first call should therefore come before any stream capture.  Every
+// call shares the one array and leaves the previous call's contents in it;
+// everything the kernels need zeroed (status, slice counter, tensor maxima,
+// the FP64 result) is cleared by the call itself.  Calls whose work overlaps
+// on the GPU (different streams, or other host threads) race on the array.
+// ===========================================================================
+namespace {
+
+static __device__ __align__(256) char g_static_scratch[QGM_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+char *g_static_addr[128] = {nullptr};
+
+int static_scratch_address(int dev, char **out) {
+  if (dev < 0 || dev >= 128) {
+    set_error("qgm_amplitudes_static: device ordinal %d out of range", dev);
+    return QGM_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void *a = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&a, g_static_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(static scratch)");
+    g_static_addr[dev] = static_cast<char *>(a);
+  }
+  *out = g_static_addr[dev];
+  return QGM_OK;
+}
+
+// The stepwise launches of one slice with an explicit workspace base.
+void static_slice(const qgm_plan *p, char *ws, int sms, const uint64_t *d_bits, int64_t B,
+                  double2 *d_out, cudaStream_t st) {
+  Meta *meta = reinterpret_cast<Meta *>(ws + p->off_meta);
+  Header *hdr = reinterpret_cast<Header *>(ws + p->off_header);
+  const int nl = (int)p->leafdesc.size();
+  k_build_leaves<<<std::max(nl, 1), 256, 0, st>>>(ws, reinterpret_cast<const LeafDesc *>(ws + p->off_leafdesc),
+                                                   nl, meta, p->n_meta, hdr, d_bits, B, p->Bp);
+  for (const StepDesc &d : p->steps) {
+    const uint64_t rows = 1ull << d.w_out;
+    if (d.batched_out) {
+      const int bx = (p->Bp / 2 + STEP_THREADS - 1) / STEP_THREADS;
+      const uint64_t cap = (uint64_t)std::max(1, sms * 16 / bx);
+      int T = 1;
+      while (T < 8 && (T * 2) <= (1 << std::min(d.k, 4)) &&
+             rows * (uint64_t)bx * STEP_THREADS * T < (uint64_t)sms * 1024)
+        T *= 2;
+      dim3 grid(bx, (unsigned)std::min<uint64_t>(rows, std::min<uint64_t>(cap, 65535)));
+      k_step_batched<<<grid, dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, p->Bp);
+    } else {
+      const uint64_t blocks = (rows + 255) / 256;
+      k_step_plain<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)sms * 8), 256, 0, st>>>(ws, d, meta, hdr);
+    }
+  }
+  const int64_t blocks = std::min<int64_t>((B + 255) / 256, (int64_t)sms * 8);
+  const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
+  k_accumulate<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(
+      ws, p->final_off, p->final_meta, p->final_batched, 0, B, d_out, meta, hdr, c.real(), c.imag());
+}
+
+}  // namespace
+
+extern "C" int qgm_amplitudes_static(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B,
+                                     double *d_out, void *stream) {
+  if (!p || !d_bitstrings || !d_out) {
+    set_error("qgm_amplitudes_static: null argument");
+    return QGM_ERR_ARG;
+  }
+  if (p->output_mode != QGM_OUT_BATCH || B < 1 || B > p->batch) {
+    set_error("qgm_amplitudes_static: needs a batch plan and 1 <= B <= %lld", (long long)p->batch);
+    return QGM_ERR_ARG;
+  }
+  if (p->ws_bytes > (int64_t)QGM_STATIC_SCRATCH_BYTES) {
+    set_error("qgm_amplitudes_static: the plan needs %lld bytes of scratch, more than the %llu-byte "
+              "static scratch; use qgm_plan_bind with a caller-allocated workspace",
+              (long long)p->ws_bytes, (unsigned long long)QGM_STATIC_SCRATCH_BYTES);
+    return QGM_ERR_OOM;
+  }
+  int dev = -1, sms = 0;
+  CK(cudaGetDevice(&dev));
+  char *ws = nullptr;
+  int rc = static_scratch_address(dev, &ws);
+  if (rc) return rc;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the previous call's plan may have left other tables here: reload ours
+  CK(cudaMemsetAsync(ws + p->off_header, 0, 256, st));
+  if (!p->base_tables.empty())
+    CK(cudaMemcpyAsync(ws + p->off_base, p->base_tables.data(), p->base_tables.size() * sizeof(float),
+                       cudaMemcpyHostToDevice, st));
+  if (!p->leafdesc.empty())
+    CK(cudaMemcpyAsync(ws + p->off_leafdesc, p->leafdesc.data(), p->leafdesc.size() * sizeof(LeafDesc),
+                       cudaMemcpyHostToDevice, st));
+  Header *hdr = reinterpret_cast<Header *>(ws + p->off_header);
+  double2 *out = reinterpret_cast<double2 *>(d_out);
+  const int64_t iblocks = std::min<int64_t>((B + 255) / 256, (int64_t)sms * 4);
+  k_init<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(out, B, hdr);
+  const int64_t nslices = (int64_t)1 << p->slice_vars.size();
+  for (int64_t s = 0; s < nslices; ++s) static_slice(p, ws, sms, d_bitstrings, B, out, st);
+  CK(cudaGetLastError());
+  return QGM_OK;
+}
