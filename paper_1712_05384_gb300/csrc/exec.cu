@@ -313,31 +313,34 @@ __device__ __forceinline__ uint32_t pext_small(uint32_t e, uint32_t mask) {
 }
 
 // One elimination step of the chunk with M inputs (M known at compile time so
-// the per-input state lives in registers for the whole term loop).
+// the per-input state lives in registers for the whole term loop).  Only the
+// warps the step needs call this; the rest go straight to the barrier.
 template <int M>
-__device__ __forceinline__ float res_step(const RStep &S, char *sm, const float *scale, int logBc,
-                                          int tid) {
+__device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *meta, Header *hdr,
+                                          int logBc, int lb, int lg, int items, int tid, int *esum_out) {
   int soff[M], bsh[M], rb[M], nr[M];
   uint32_t est[M], em[M];
   bool egen[M];
+  float scale[M];
+  int esum = 0;
   const int k = S.k;
   const uint32_t kfull = (1u << k) - 1u;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    soff[i] = S.in[i].soff;
-    bsh[i] = S.in[i].batched ? logBc : 0;
-    rb[i] = S.in[i].rowbits;
-    nr[i] = S.in[i].nruns;
-    em[i] = S.in[i].emask;
+    const RIn &in = S.in[i];
+    soff[i] = in.soff;
+    bsh[i] = in.batched ? logBc : 0;
+    rb[i] = in.rowbits;
+    nr[i] = in.nruns;
+    em[i] = in.emask;
     est[i] = em[i] == kfull ? (1u << rb[i]) : 0u;
     egen[i] = em[i] != kfull && em[i] != 0u;
+    int e;
+    operand_scale(meta, in.meta, hdr, &scale[i], &e);
+    esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
   }
-  const int lb = S.batched_out ? logBc : 0;
-  const int items = (1 << S.w_out) << lb;
+  *esum_out = esum;
   const int terms = 1 << k;
-  // lanes per item: split the summed terms when there are few items
-  int lg = 0;
-  while (lg < 5 && lg < k && (items << (lg + 1)) <= RES_THREADS) ++lg;
   const int tpi = 1 << lg;
   const int g = tid & (tpi - 1);
   float lmax = 0.f;
@@ -357,7 +360,6 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const float 
           const uint32_t pr = S.in[i].prun[q];
           r |= ((row >> (pr & 0xffu)) & (pr >> 16)) << ((pr >> 8) & 0xffu);
         }
-        // fold the batch entry in now: element = (idx << bsh) | beta
         ridx[i] = r;
       }
       for (int e = g; e < terms; e += tpi) {
@@ -387,15 +389,14 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const float 
 }
 
 __global__ void __launch_bounds__(RES_THREADS, 5)
-    k_resident(const char *ws, const RStep *steps, int n_steps, const RLeaf *rleaves, int n_rleaves,
-               const LeafDesc *leaves, const uint64_t *bits, int64_t B, int logBc, int n_meta,
-               int final_soff, int final_meta, int final_batched, double c_re, double c_im,
-               double2 *out, Header *hdr) {
+    k_resident(const char *ws, const RStep *steps, int n_steps, const RJob *jobs, int n_jobs,
+               const uint64_t *bits, int64_t B, int logBc, int n_meta, int final_soff, int final_meta,
+               int final_batched, double c_re, double c_im, double2 *out, Header *hdr) {
   extern __shared__ __align__(16) char sm[];
   __shared__ RStep sd[2];
   __shared__ float red[RES_THREADS / 32];
   const int Bc = 1 << logBc;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, wid = tid >> 5;
   const int64_t b0 = (int64_t)blockIdx.x * Bc;
   Meta *meta = reinterpret_cast<Meta *>(sm);
   for (int i = tid; i < n_meta; i += RES_THREADS) {
@@ -404,25 +405,20 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
   }
   if (tid < RSTEP_WORDS && n_steps > 0)
     reinterpret_cast<int *>(&sd[0])[tid] = __ldg(reinterpret_cast<const int *>(steps) + tid);
-  // leaves of this chunk: batched ones take entry (row r, beta) of the base
-  // table with the output bits of x_beta; unbatched ones are the table itself
-  for (int l = 0; l < n_rleaves; ++l) {
-    const RLeaf rl = rleaves[l];
-    const LeafDesc &d = leaves[rl.leaf];
-    const float2 *base = reinterpret_cast<const float2 *>(ws + d.base_off);
-    float2 *dst = reinterpret_cast<float2 *>(sm + rl.soff);
-    if (!rl.batched) {
-      for (int t = tid; t < (1 << d.n_int); t += RES_THREADS) dst[t] = __ldg(base + t);
-      continue;
-    }
-    const int n = (1 << d.n_int) << logBc;
-    for (int t = tid; t < n; t += RES_THREADS) {
-      const int r = t >> logBc, b = t & (Bc - 1);
+  // leaves of this chunk, one job per leaf row: batched rows take the base
+  // entry selected by the output bits of x_beta, unbatched rows the entry
+  const float2 *wsf = reinterpret_cast<const float2 *>(ws);
+  for (int t = tid; t < (n_jobs << logBc); t += RES_THREADS) {
+    const int b = t & (Bc - 1);
+    const RJob j = jobs[t >> logBc];
+    if (!j.batched && b) continue;
+    int ob = 0;
+    if (j.n_out) {
       const uint64_t x = (b0 + b < B) ? bits[b0 + b] : 0ull;
-      int ob = 0;
-      for (int a = 0; a < d.n_out; ++a) ob |= (int)((x >> d.out_qubit[a]) & 1ull) << (d.n_out - 1 - a);
-      dst[t] = __ldg(base + ((r << d.n_out) | ob));
+      ob = j.n_out == 1 ? (int)((x >> j.q0) & 1ull)
+                        : (int)((((x >> j.q0) & 1ull) << 1) | ((x >> j.q1) & 1ull));
     }
+    reinterpret_cast<float2 *>(sm + j.dst)[j.batched ? b : 0] = __ldg(wsf + j.src + ob);
   }
   __syncthreads();
   for (int s = 0; s < n_steps; ++s) {
@@ -431,36 +427,33 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
     int nextw = 0;
     if (s + 1 < n_steps && tid < RSTEP_WORDS)
       nextw = __ldg(reinterpret_cast<const int *>(steps + s + 1) + tid);
-    float scale[MAXIN];
+    const int lb = S.batched_out ? logBc : 0;
+    const int items = (1 << S.w_out) << lb;
+    // lanes per item: split the summed terms when there are few items
+    int lg = 0;
+    while (lg < 5 && lg < S.k && (items << (lg + 1)) <= RES_THREADS) ++lg;
+    const int need = min(RES_THREADS / 32, ((items << lg) + 31) >> 5);
+    float lmax = 0.f;
     int esum = 0;
-#pragma unroll
-    for (int i = 0; i < MAXIN; ++i) {
-      scale[i] = 1.f;
-      if (i < S.m) {
-        int e;
-        operand_scale(meta, S.in[i].meta, hdr, &scale[i], &e);
-        esum += e + (S.in[i].meta >= 0 ? meta[S.in[i].meta].exp : 0);
+    if (wid < need) {
+      switch (S.m) {
+        case 1: lmax = res_step<1>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
+        case 2: lmax = res_step<2>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
+        case 3: lmax = res_step<3>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
+        case 4: lmax = res_step<4>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
+        case 5: lmax = res_step<5>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
+        case 6: lmax = res_step<6>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
+        case 7: lmax = res_step<7>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
+        default: lmax = res_step<8>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
       }
+      for (int q = 16; q > 0; q >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
+      if ((tid & 31) == 0) red[wid] = lmax;
     }
-    float lmax;
-    switch (S.m) {
-      case 1: lmax = res_step<1>(S, sm, scale, logBc, tid); break;
-      case 2: lmax = res_step<2>(S, sm, scale, logBc, tid); break;
-      case 3: lmax = res_step<3>(S, sm, scale, logBc, tid); break;
-      case 4: lmax = res_step<4>(S, sm, scale, logBc, tid); break;
-      case 5: lmax = res_step<5>(S, sm, scale, logBc, tid); break;
-      case 6: lmax = res_step<6>(S, sm, scale, logBc, tid); break;
-      case 7: lmax = res_step<7>(S, sm, scale, logBc, tid); break;
-      default: lmax = res_step<8>(S, sm, scale, logBc, tid); break;
-    }
-    // block max -> the output's metadata; next descriptor -> the other buffer
-    for (int q = 16; q > 0; q >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
-    if ((tid & 31) == 0) red[tid >> 5] = lmax;
     if (s + 1 < n_steps && tid < RSTEP_WORDS) reinterpret_cast<int *>(&sd[(s + 1) & 1])[tid] = nextw;
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0) {  // warp 0 always takes part, so esum is thread 0's
       float m = 0.f;
-      for (int w = 0; w < RES_THREADS / 32; ++w) m = fmaxf(m, red[w]);
+      for (int w = 0; w < need; ++w) m = fmaxf(m, red[w]);
       meta[S.out_meta].maxbits = __float_as_uint(m);
       meta[S.out_meta].exp = esum;
     }
@@ -568,10 +561,9 @@ static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, doub
   const char *ws = x->ws;
   k_resident<<<(unsigned)G, RES_THREADS, (size_t)L.smem_bytes, st>>>(
       ws, reinterpret_cast<const RStep *>(ws + p->off_rsteps), (int)L.steps.size(),
-      reinterpret_cast<const RLeaf *>(ws + p->off_rsteps + L.steps.size() * sizeof(RStep)),
-      (int)L.leaves.size(), reinterpret_cast<const LeafDesc *>(ws + p->off_leafdesc), d_bits, B, logBc,
-      p->n_meta, L.final_soff, L.final_meta, p->final_batched, c.real(), c.imag(), d_out,
-      reinterpret_cast<Header *>(x->ws + p->off_header));
+      reinterpret_cast<const RJob *>(ws + p->off_rsteps + L.steps.size() * sizeof(RStep)),
+      (int)L.jobs.size(), d_bits, B, logBc, p->n_meta, L.final_soff, L.final_meta, p->final_batched,
+      c.real(), c.imag(), d_out, reinterpret_cast<Header *>(x->ws + p->off_header));
 }
 
 static int run(qgm_plan *p, const uint64_t *d_bits, int64_t B, double2 *d_out, int64_t n_out,
@@ -695,9 +687,9 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
       CK(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
       CK(cudaMemcpyAsync(x->ws + p->off_rsteps, L.steps.data(), L.steps.size() * sizeof(RStep),
                          cudaMemcpyHostToDevice, st));
-      if (!L.leaves.empty())
-        CK(cudaMemcpyAsync(x->ws + p->off_rsteps + L.steps.size() * sizeof(RStep), L.leaves.data(),
-                           L.leaves.size() * sizeof(RLeaf), cudaMemcpyHostToDevice, st));
+      if (!L.jobs.empty())
+        CK(cudaMemcpyAsync(x->ws + p->off_rsteps + L.steps.size() * sizeof(RStep), L.jobs.data(),
+                           L.jobs.size() * sizeof(RJob), cudaMemcpyHostToDevice, st));
       CK(cudaStreamSynchronize(st));
       x->kind = QGM_EXEC_RESIDENT;
     } else if (p->executor_pref == QGM_EXEC_RESIDENT) {

@@ -605,7 +605,20 @@ static void build_resident(qgm_plan *p) {
     bool ok = true;
     for (int li = 0; li < nl; ++li) {
       soff[li] = arena.alloc(bytes_of(S.tensors[li]));
-      L.leaves.push_back({li, (int32_t)(meta_bytes + soff[li]), S.tensors[li].batched ? 1 : 0, 0});
+      const bool bt = S.tensors[li].batched;
+      L.leaves.push_back({li, (int32_t)(meta_bytes + soff[li]), bt ? 1 : 0, 0});
+      const LeafDesc &d = p->leafdesc[li];
+      if (d.n_out > 2 || d.n_slice > 0) ok = false;
+      for (int r = 0; r < (1 << d.n_int); ++r) {
+        RJob j{};
+        j.src = (int32_t)((d.base_off / 8) + ((int64_t)r << d.n_out));
+        j.dst = (int32_t)(meta_bytes + soff[li] + (int64_t)r * (bt ? Bc : 1) * 8);
+        j.n_out = (uint8_t)d.n_out;
+        j.q0 = (uint8_t)(d.n_out > 0 ? d.out_qubit[0] : 0);
+        j.q1 = (uint8_t)(d.n_out > 1 ? d.out_qubit[1] : 0);
+        j.batched = bt ? 1 : 0;
+        L.jobs.push_back(j);
+      }
     }
     for (size_t si = 0; si < S.steps.size(); ++si) {
       const StepRec &st = S.steps[si];
@@ -887,8 +900,13 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   int64_t out_elems = o.output_mode == QGM_OUT_BATCH ? Bp : p->final_entries;
   p->off_outstage = take(out_elems * 16);
   p->off_acc = take(out_elems * 16);
-  p->off_rsteps = take((int64_t)(S.steps.size() + 1) * sizeof(RStep) +
-                       (int64_t)(p->leaves.size() + 1) * sizeof(RLeaf));
+  {
+    int64_t njobs = 0;
+    for (size_t li = 0; li < p->leaves.size(); ++li)
+      njobs += (int64_t)1 << (S.tensors[li].vars.size());
+    p->off_rsteps = take((int64_t)(S.steps.size() + 1) * sizeof(RStep) +
+                         (int64_t)(p->leaves.size() + 1) * sizeof(RLeaf) + (njobs + 1) * sizeof(RJob));
+  }
   p->off_arena = take(0);
   for (SymTensor &t : S.tensors)
     if (t.leaf < 0) t.off += p->off_arena;

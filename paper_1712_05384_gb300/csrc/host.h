@@ -113,11 +113,23 @@ struct RLeaf {        // leaf materialised in smem per chunk
   int32_t pad_;
 };
 
+// One row of a leaf staged into shared memory: entry (row, beta) is base
+// entry src + (output bits of x_beta) stored at smem byte dst + 8 * beta
+// (batched) or dst (unbatched).
+struct RJob {
+  int32_t src;      // float2 index into the workspace base tables
+  int32_t dst;      // smem byte offset of (row, beta = 0)
+  uint8_t n_out;    // output qubits of the leaf (0..2)
+  uint8_t q0, q1;   // their qubits, most significant first
+  uint8_t batched;
+};
+
 struct ResidentLayout {
   int chunk = 0;            // Bc
   int64_t smem_bytes = 0;   // dynamic shared memory per CTA
   std::vector<RStep> steps;
   std::vector<RLeaf> leaves;
+  std::vector<RJob> jobs;
   int final_soff = -1, final_meta = -1;
 };
 
