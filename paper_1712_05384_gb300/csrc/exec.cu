@@ -312,12 +312,50 @@ __device__ __forceinline__ uint32_t pext_small(uint32_t e, uint32_t mask) {
   return r;
 }
 
-// One elimination step of the chunk with M inputs (M known at compile time so
-// the per-input state lives in registers for the whole term loop).  Only the
-// warps the step needs call this; the rest go straight to the barrier.
+// Per-tensor metadata of the resident executor: the maximum of each warp
+// that produced part of the tensor (zero for the others) and the exponent.
+struct RMeta {
+  float wmax[RES_WARPS];
+  int32_t exp;
+  int32_t pad_;
+};
+
+__device__ __forceinline__ void res_scale(const RMeta *meta, int slot, Header *hdr, float *scale,
+                                          int *e_out) {
+  if (slot < 0) {
+    *scale = 1.f;
+    *e_out = 0;
+    return;
+  }
+  float m = 0.f;
+#pragma unroll
+  for (int w = 0; w < RES_WARPS; ++w) m = fmaxf(m, meta[slot].wmax[w]);
+  const uint32_t bits = __float_as_uint(m);
+  const int E = (int)((bits >> 23) & 0xff);
+  if (E == 0xff) {
+    atomicCAS(&hdr->status, 0, QGM_ERR_NONFINITE);
+    *scale = 1.f;
+    *e_out = 0;
+    return;
+  }
+  if (E == 0) {
+    *scale = 1.f;
+    *e_out = 0;
+    return;
+  }
+  int e = E - 126;
+  if (e > 126) e = 126;
+  *scale = __int_as_float((127 - e) << 23);
+  *e_out = e;
+}
+
+// One elimination step run by a group of G threads (gt = thread index in the
+// group); M inputs known at compile time so the per-input state lives in
+// registers for the whole term loop.
 template <int M>
-__device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *meta, Header *hdr,
-                                          int logBc, int lb, int lg, int items, int tid, int *esum_out) {
+__device__ __forceinline__ float res_step(const RStep &S, char *sm, const RMeta *meta, Header *hdr,
+                                          int logBc, int lb, int lg, int items, int gt, int G,
+                                          int *esum_out) {
   int soff[M], bsh[M], rb[M], nr[M];
   uint32_t est[M], em[M];
   bool egen[M];
@@ -336,17 +374,17 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
     est[i] = em[i] == kfull ? (1u << rb[i]) : 0u;
     egen[i] = em[i] != kfull && em[i] != 0u;
     int e;
-    operand_scale(meta, in.meta, hdr, &scale[i], &e);
+    res_scale(meta, in.meta, hdr, &scale[i], &e);
     esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
   }
   *esum_out = esum;
   const int terms = 1 << k;
   const int tpi = 1 << lg;
-  const int g = tid & (tpi - 1);
+  const int g = gt & (tpi - 1);
   float lmax = 0.f;
   float2 *o = reinterpret_cast<float2 *>(sm + S.out_soff);
-  for (int it0 = 0; it0 < items * tpi; it0 += RES_THREADS) {
-    const int it = (it0 + tid) >> lg;
+  for (int it0 = 0; it0 < items * tpi; it0 += G) {
+    const int it = (it0 + gt) >> lg;
     const bool live = it < items;
     float2 acc = make_float2(0.f, 0.f);
     if (live) {
@@ -388,23 +426,21 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
   return lmax;
 }
 
+// The whole pass for one chunk of Bc bitstrings.  Steps come in dependency
+// levels; within a level each step runs on its own warp group with no block
+// barrier, and one __syncthreads closes the level.
 __global__ void __launch_bounds__(RES_THREADS, 5)
     k_resident(const char *ws, const RStep *steps, int n_steps, const RJob *jobs, int n_jobs,
                const uint64_t *bits, int64_t B, int logBc, int n_meta, int final_soff, int final_meta,
                int final_batched, double c_re, double c_im, double2 *out, Header *hdr) {
   extern __shared__ __align__(16) char sm[];
-  __shared__ RStep sd[2];
-  __shared__ float red[RES_THREADS / 32];
+  __shared__ RStep wsd[RES_WARPS];
   const int Bc = 1 << logBc;
-  const int tid = threadIdx.x, wid = tid >> 5;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int64_t b0 = (int64_t)blockIdx.x * Bc;
-  Meta *meta = reinterpret_cast<Meta *>(sm);
-  for (int i = tid; i < n_meta; i += RES_THREADS) {
-    meta[i].maxbits = 0;
-    meta[i].exp = 0;
-  }
-  if (tid < RSTEP_WORDS && n_steps > 0)
-    reinterpret_cast<int *>(&sd[0])[tid] = __ldg(reinterpret_cast<const int *>(steps) + tid);
+  RMeta *meta = reinterpret_cast<RMeta *>(sm);
+  for (int i = tid; i < n_meta * (int)(sizeof(RMeta) / 4); i += RES_THREADS)
+    reinterpret_cast<int *>(sm)[i] = 0;
   // leaves of this chunk, one job per leaf row: batched rows take the base
   // entry selected by the output bits of x_beta, unbatched rows the entry
   const float2 *wsf = reinterpret_cast<const float2 *>(ws);
@@ -421,43 +457,39 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
     reinterpret_cast<float2 *>(sm + j.dst)[j.batched ? b : 0] = __ldg(wsf + j.src + ob);
   }
   __syncthreads();
+  RStep &S = wsd[wid];
   for (int s = 0; s < n_steps; ++s) {
-    const RStep &S = sd[s & 1];
-    // prefetch the next descriptor into registers; stored after the compute
-    int nextw = 0;
-    if (s + 1 < n_steps && tid < RSTEP_WORDS)
-      nextw = __ldg(reinterpret_cast<const int *>(steps + s + 1) + tid);
-    const int lb = S.batched_out ? logBc : 0;
-    const int items = (1 << S.w_out) << lb;
-    // lanes per item: split the summed terms when there are few items
-    int lg = 0;
-    while (lg < 5 && lg < S.k && (items << (lg + 1)) <= RES_THREADS) ++lg;
-    const int need = min(RES_THREADS / 32, ((items << lg) + 31) >> 5);
-    float lmax = 0.f;
-    int esum = 0;
-    if (wid < need) {
+    const int sched = __ldg(&steps[s].sched);
+    const int w0 = sched & 15, nw = (sched >> 4) & 15, lg = (sched >> 8) & 15;
+    if (wid >= w0 && wid < w0 + nw) {
+      // this warp's copy of the descriptor
+      const int *src = reinterpret_cast<const int *>(steps + s);
+      int *dst = reinterpret_cast<int *>(&S);
+      for (int w = lane; w < RSTEP_WORDS; w += 32) dst[w] = __ldg(src + w);
+      __syncwarp();
+      const int lb = S.batched_out ? logBc : 0;
+      const int items = (1 << S.w_out) << lb;
+      const int gt = tid - 32 * w0, G = 32 * nw;
+      float lmax;
+      int esum = 0;
       switch (S.m) {
-        case 1: lmax = res_step<1>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
-        case 2: lmax = res_step<2>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
-        case 3: lmax = res_step<3>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
-        case 4: lmax = res_step<4>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
-        case 5: lmax = res_step<5>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
-        case 6: lmax = res_step<6>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
-        case 7: lmax = res_step<7>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
-        default: lmax = res_step<8>(S, sm, meta, hdr, logBc, lb, lg, items, tid, &esum); break;
+        case 1: lmax = res_step<1>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 2: lmax = res_step<2>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 3: lmax = res_step<3>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 4: lmax = res_step<4>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 5: lmax = res_step<5>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 6: lmax = res_step<6>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 7: lmax = res_step<7>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        default: lmax = res_step<8>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
       }
       for (int q = 16; q > 0; q >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
-      if ((tid & 31) == 0) red[wid] = lmax;
+      if (lane == 0) {
+        meta[S.out_meta].wmax[wid - w0] = lmax;
+        if (wid == w0) meta[S.out_meta].exp = esum;
+      }
+      __syncwarp();
     }
-    if (s + 1 < n_steps && tid < RSTEP_WORDS) reinterpret_cast<int *>(&sd[(s + 1) & 1])[tid] = nextw;
-    __syncthreads();
-    if (tid == 0) {  // warp 0 always takes part, so esum is thread 0's
-      float m = 0.f;
-      for (int w = 0; w < need; ++w) m = fmaxf(m, red[w]);
-      meta[S.out_meta].maxbits = __float_as_uint(m);
-      meta[S.out_meta].exp = esum;
-    }
-    __syncthreads();
+    if (sched & SCHED_LAST) __syncthreads();
   }
   if (tid < Bc && b0 + tid < B) {
     const float2 v = reinterpret_cast<const float2 *>(sm + final_soff)[final_batched ? tid : 0];

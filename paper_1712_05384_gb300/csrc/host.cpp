@@ -585,14 +585,33 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
 static int64_t pow2(int r) { return (int64_t)1 << r; }
 
 // Shared-memory layouts of the resident executor for chunks of Bc batch
-// entries: metadata slots first, then an arena holding the batched leaves
-// and every intermediate of the chunk with the stepwise plan's liveness.
+// entries.  Steps are grouped into dependency levels (a step's level is one
+// more than the highest level among the steps producing its inputs); the
+// steps of a level are independent, run concurrently on disjoint warp groups
+// and are followed by one block barrier.  The smem arena holds the leaves and
+// intermediates with level-granular liveness (a level's outputs are placed
+// before any of its inputs are released).
 static void build_resident(qgm_plan *p) {
   p->resident.clear();
   if (p->output_mode != QGM_OUT_BATCH || !p->slice_vars.empty()) return;
   const SimResult &S = p->sim;
   const int nl = (int)p->leaves.size();
-  const int64_t meta_bytes = ((int64_t)p->n_meta * 8 + 15) & ~int64_t(15);
+  const int ns = (int)S.steps.size();
+  // dependency levels
+  std::vector<int> producer(S.tensors.size(), -1), level(ns, 0);
+  int n_levels = 0;
+  for (int si = 0; si < ns; ++si) {
+    int l = 0;
+    for (int id : S.steps[si].inputs)
+      if (producer[id] >= 0) l = std::max(l, level[producer[id]] + 1);
+    level[si] = l;
+    producer[S.steps[si].out] = si;
+    n_levels = std::max(n_levels, l + 1);
+  }
+  std::vector<int> order(ns);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return level[a] < level[b]; });
+  const int64_t meta_bytes = ((int64_t)p->n_meta * (int64_t)(RES_WARPS * 4 + 8) + 15) & ~int64_t(15);
   for (int Bc : {1, 2, 4, 8}) {
     ResidentLayout L;
     L.chunk = Bc;
@@ -620,55 +639,136 @@ static void build_resident(qgm_plan *p) {
         L.jobs.push_back(j);
       }
     }
-    for (size_t si = 0; si < S.steps.size(); ++si) {
-      const StepRec &st = S.steps[si];
-      const SymTensor &ot = S.tensors[st.out];
-      soff[st.out] = arena.alloc(bytes_of(ot));
-      for (int id : st.inputs)
-        if (soff[id] >= 0) arena.release(soff[id], bytes_of(S.tensors[id]));
-      const StepDesc &d = p->steps[si];
-      RStep r{};
-      r.m = d.m;
-      r.k = d.k;
-      r.w_out = d.w_out;
-      r.batched_out = d.batched_out;
-      r.out_soff = (int32_t)(meta_bytes + soff[st.out]);
-      r.out_meta = ot.meta;
-      for (int i = 0; i < d.m; ++i) {
-        const SymTensor &it = S.tensors[st.inputs[i]];
-        RIn &in = r.in[i];
-        in.batched = it.batched ? 1 : 0;
-        in.meta = it.leaf < 0 ? it.meta : -1;
-        in.soff = (int32_t)(meta_bytes + soff[st.inputs[i]]);
-        // split the union runs at the row/summed boundary (bit w_out)
-        int nr = 0, rowbits = 0;
-        uint32_t emask = 0;
-        for (int q = 0; q < d.in[i].nruns; ++q) {
-          int a = d.in[i].src[q], b = a + d.in[i].len[q];
-          if (a < d.w_out) {
-            int hi = std::min(b, d.w_out);
-            if (nr >= RMAXRUN || hi - a > 16) {
-              ok = false;
-              break;
-            }
-            in.prun[nr] = (uint32_t)a | ((uint32_t)rowbits << 8) | (((1u << (hi - a)) - 1u) << 16);
-            rowbits += hi - a;
-            ++nr;
-          }
-          for (int bit = std::max(a, d.w_out); bit < b; ++bit) emask |= 1u << (bit - d.w_out);
-        }
-        in.nruns = (uint8_t)nr;
-        in.rowbits = (uint8_t)rowbits;
-        in.emask = (uint16_t)emask;
+    for (int lv = 0, pos = 0; lv < n_levels && ok; ++lv) {
+      int end = pos;
+      while (end < ns && level[order[end]] == lv) ++end;
+      for (int q = pos; q < end; ++q) {
+        const StepRec &st = S.steps[order[q]];
+        soff[st.out] = arena.alloc(bytes_of(S.tensors[st.out]));
       }
-      L.steps.push_back(r);
+      for (int q = pos; q < end; ++q)
+        for (int id : S.steps[order[q]].inputs)
+          if (soff[id] >= 0) {
+            arena.release(soff[id], bytes_of(S.tensors[id]));
+            soff[id] = -2;  // released (a tensor is consumed once)
+          }
+      // warp groups: each step gets nw warps; longest steps first onto the
+      // least-loaded contiguous warp range
+      struct Job { int q, nw, lg; double cost; };
+      std::vector<Job> jobs;
+      for (int q = pos; q < end; ++q) {
+        const StepDesc &d = p->steps[order[q]];
+        const int64_t items = (int64_t)(1 << d.w_out) * (d.batched_out ? Bc : 1);
+        const int64_t terms = (int64_t)1 << d.k;
+        int nw = (int)std::min<int64_t>(RES_WARPS, std::max<int64_t>(1, (items * terms + 511) / 512));
+        int lg = 0;
+        while (lg < 5 && lg < d.k && (items << (lg + 1)) <= 32 * nw) ++lg;
+        const int64_t per_thread = ((items << lg) + 32 * nw - 1) / (32 * nw);
+        jobs.push_back({q, nw, lg, (double)per_thread * (double)(terms >> lg) * d.m + 40.0});
+      }
+      std::stable_sort(jobs.begin(), jobs.end(), [](const Job &a, const Job &b) { return a.cost > b.cost; });
+      double load[RES_WARPS] = {0};
+      std::vector<int> w0_of(end - pos);
+      for (const Job &j : jobs) {
+        int best = 0;
+        double bl = 1e300;
+        for (int w = 0; w + j.nw <= RES_WARPS; ++w) {
+          double mx = 0;
+          for (int u = w; u < w + j.nw; ++u) mx = std::max(mx, load[u]);
+          if (mx < bl) {
+            bl = mx;
+            best = w;
+          }
+        }
+        for (int u = best; u < best + j.nw; ++u) load[u] = bl + j.cost;
+        w0_of[j.q - pos] = best | (j.nw << 4) | (j.lg << 8);
+      }
+      for (int q = pos; q < end; ++q) {
+        const int si = order[q];
+        const StepRec &st = S.steps[si];
+        const StepDesc &d = p->steps[si];
+        const SymTensor &ot = S.tensors[st.out];
+        RStep r{};
+        r.m = d.m;
+        r.k = d.k;
+        r.w_out = d.w_out;
+        r.batched_out = d.batched_out;
+        r.out_soff = (int32_t)(meta_bytes + soff[st.out]);
+        r.out_meta = ot.meta;
+        r.sched = w0_of[q - pos] | (q == end - 1 ? SCHED_LAST : 0);
+        for (int i = 0; i < d.m && ok; ++i) {
+          const int id = st.inputs[i];
+          const SymTensor &it = S.tensors[id];
+          RIn &in = r.in[i];
+          in.batched = it.batched ? 1 : 0;
+          in.meta = it.leaf < 0 ? it.meta : -1;
+          // the input's offset as allocated (before its release above)
+          in.soff = -1;
+          // split the union runs at the row/summed boundary (bit w_out)
+          int nr = 0, rowbits = 0;
+          uint32_t emask = 0;
+          for (int qq = 0; qq < d.in[i].nruns; ++qq) {
+            int a = d.in[i].src[qq], b = a + d.in[i].len[qq];
+            if (a < d.w_out) {
+              int hi = std::min(b, d.w_out);
+              if (nr >= RMAXRUN || hi - a > 16) {
+                ok = false;
+                break;
+              }
+              in.prun[nr] = (uint32_t)a | ((uint32_t)rowbits << 8) | (((1u << (hi - a)) - 1u) << 16);
+              rowbits += hi - a;
+              ++nr;
+            }
+            for (int bit = std::max(a, d.w_out); bit < b; ++bit) emask |= 1u << (bit - d.w_out);
+          }
+          in.nruns = (uint8_t)nr;
+          in.rowbits = (uint8_t)rowbits;
+          in.emask = (uint16_t)emask;
+        }
+        L.steps.push_back(r);
+      }
+      pos = end;
     }
     if (!ok) break;  // an index map too fragmented for the resident kernel
-    L.final_soff = (int)(meta_bytes + soff[S.final_tensor]);
+    L.final_soff = -1;
     L.final_meta = S.tensors[S.final_tensor].meta;
     L.smem_bytes = meta_bytes + arena.peak;
     if (L.smem_bytes > 200 * 1024) break;  // larger chunks only grow
     p->resident.push_back(L);
+  }
+  // input offsets: replay the allocation to recover every tensor's offset
+  for (ResidentLayout &L : p->resident) {
+    const int Bc = L.chunk;
+    Arena arena;
+    arena.al = 16;
+    std::vector<int64_t> soff(S.tensors.size(), -1);
+    auto bytes_of = [&](const SymTensor &t) {
+      return pow2((int)t.vars.size()) * (t.batched ? Bc : 1) * 8;
+    };
+    for (int li = 0; li < nl; ++li) soff[li] = arena.alloc(bytes_of(S.tensors[li]));
+    std::vector<int64_t> where = soff;
+    for (int lv = 0, pos = 0; lv < n_levels; ++lv) {
+      int end = pos;
+      while (end < ns && level[order[end]] == lv) ++end;
+      for (int q = pos; q < end; ++q) {
+        const StepRec &st = S.steps[order[q]];
+        soff[st.out] = arena.alloc(bytes_of(S.tensors[st.out]));
+        where[st.out] = soff[st.out];
+      }
+      for (int q = pos; q < end; ++q)
+        for (int id : S.steps[order[q]].inputs)
+          if (soff[id] >= 0) {
+            arena.release(soff[id], bytes_of(S.tensors[id]));
+            soff[id] = -2;
+          }
+      pos = end;
+    }
+    for (int q = 0; q < ns; ++q) {
+      const StepRec &st = S.steps[order[q]];
+      for (size_t i = 0; i < st.inputs.size(); ++i)
+        L.steps[q].in[i].soff = (int32_t)(meta_bytes + where[st.inputs[i]]);
+    }
+    L.final_soff = (int)(meta_bytes + where[S.final_tensor]);
   }
 }
 

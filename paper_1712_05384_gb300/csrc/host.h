@@ -103,8 +103,14 @@ struct RIn {
 struct RStep {
   int32_t m, k, w_out, batched_out;
   int32_t out_soff, out_meta;
+  // warps [w0, w0 + nw) run the step with 2^lg lanes per output entry;
+  // bit 16: the last step of its dependency level (a block barrier follows)
+  int32_t sched;
+  int32_t pad_;
   RIn in[MAXIN];
 };
+constexpr int RES_WARPS = 8;
+constexpr int SCHED_LAST = 1 << 16;
 
 struct RLeaf {        // leaf materialised in smem per chunk
   int32_t leaf;       // index into the LeafDesc table
