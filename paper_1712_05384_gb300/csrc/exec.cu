@@ -312,108 +312,113 @@ __device__ __forceinline__ uint32_t pext_small(uint32_t e, uint32_t mask) {
   return r;
 }
 
-// Per-tensor metadata of the resident executor: the maximum of each warp
-// that produced part of the tensor (zero for the others) and the exponent.
-struct RMeta {
-  float wmax[RES_WARPS];
-  int32_t exp;
-  int32_t pad_;
-};
+// Increment tables of one warp for one step: for input i, entry t < 16 is the
+// byte change of the input address when the thread's row counter carries
+// into bit t (row bits above the thread's fixed low bits), entry 16 + t the
+// change when its term counter carries into bit t.
+constexpr int TAB_W = 24;
 
-__device__ __forceinline__ void res_scale(const RMeta *meta, int slot, Header *hdr, float *scale,
-                                          int *e_out) {
-  if (slot < 0) {
-    *scale = 1.f;
-    *e_out = 0;
-    return;
-  }
-  float m = 0.f;
-#pragma unroll
-  for (int w = 0; w < RES_WARPS; ++w) m = fmaxf(m, meta[slot].wmax[w]);
-  const uint32_t bits = __float_as_uint(m);
-  const int E = (int)((bits >> 23) & 0xff);
-  if (E == 0xff) {
-    atomicCAS(&hdr->status, 0, QGM_ERR_NONFINITE);
-    *scale = 1.f;
-    *e_out = 0;
-    return;
-  }
-  if (E == 0) {
-    *scale = 1.f;
-    *e_out = 0;
-    return;
-  }
-  int e = E - 126;
-  if (e > 126) e = 126;
-  *scale = __int_as_float((127 - e) << 23);
-  *e_out = e;
+__device__ __forceinline__ int vbit(const RIn &in, int b) {
+  const int p = in.vpos[b];
+  return p == 0xff ? 0 : (1 << p);
 }
 
-// One elimination step run by a group of G threads (gt = thread index in the
-// group); M inputs known at compile time so the per-input state lives in
-// registers for the whole term loop.
+// One elimination step run by a group of G threads (gt = index in the
+// group).  Each input index is linear in the bits of (row, e): a thread
+// starts from its first item and term and then only adds table entries
+// selected by the trailing zeros of its item and term counters.
 template <int M>
-__device__ __forceinline__ float res_step(const RStep &S, char *sm, const RMeta *meta, Header *hdr,
+__device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *meta, Header *hdr,
                                           int logBc, int lb, int lg, int items, int gt, int G,
-                                          int *esum_out) {
-  int soff[M], bsh[M], rb[M], nr[M];
-  uint32_t est[M], em[M];
-  bool egen[M];
+                                          int lane, int32_t (*tab)[TAB_W], int *esum_out) {
+  const int k = S.k, w = S.w_out;
+  const int tpi = 1 << lg;
+  const int sit = G >> lg;                  // item stride of one thread
+  const int Bco = 1 << lb;
+  const bool incr_rows = sit >= Bco;        // the thread's batch entry is fixed
+  const int r0 = incr_rows ? (__ffs(sit) - 1 - lb) : 0;
+  for (int x = lane; x < M * TAB_W; x += 32) {
+    const int i = x / TAB_W, t = x - i * TAB_W;
+    const RIn &in = S.in[i];
+    const int base = t < 16 ? r0 : w + lg;
+    const int tt = t < 16 ? t : t - 16;
+    const int lim = t < 16 ? w - r0 : k - lg;
+    int val = 0;
+    if (tt < lim) {
+      val = vbit(in, base + tt);
+      for (int b = 0; b < tt; ++b) val -= vbit(in, base + b);
+    }
+    tab[i][t] = val * (8 << (in.batched ? logBc : 0));
+  }
+  __syncwarp();
   float scale[M];
+  int soff[M], bsh[M], eb0[M];
   int esum = 0;
-  const int k = S.k;
-  const uint32_t kfull = (1u << k) - 1u;
+  const int it0 = gt >> lg, g = gt & (tpi - 1);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const RIn &in = S.in[i];
-    soff[i] = in.soff;
     bsh[i] = in.batched ? logBc : 0;
-    rb[i] = in.rowbits;
-    nr[i] = in.nruns;
-    em[i] = in.emask;
-    est[i] = em[i] == kfull ? (1u << rb[i]) : 0u;
-    egen[i] = em[i] != kfull && em[i] != 0u;
+    soff[i] = in.soff;
+    int ei = 0;
+    for (int b = 0; b < lg; ++b)
+      if ((g >> b) & 1) ei += vbit(in, w + b);
+    eb0[i] = (ei << bsh[i]) * 8;
     int e;
-    res_scale(meta, in.meta, hdr, &scale[i], &e);
+    operand_scale(meta, in.meta, hdr, &scale[i], &e);
     esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
   }
   *esum_out = esum;
-  const int terms = 1 << k;
-  const int tpi = 1 << lg;
-  const int g = gt & (tpi - 1);
+  // byte offset of the thread's current item in each input (row part + beta)
+  int rowb[M];
+  const int n_iter = (items * tpi + G - 1) / G;
+  const int tcount = 1 << (k - lg);
   float lmax = 0.f;
   float2 *o = reinterpret_cast<float2 *>(sm + S.out_soff);
-  for (int it0 = 0; it0 < items * tpi; it0 += G) {
-    const int it = (it0 + gt) >> lg;
+  for (int j = 0; j < n_iter; ++j) {
+    const int it = it0 + j * sit;
     const bool live = it < items;
-    float2 acc = make_float2(0.f, 0.f);
-    if (live) {
+    if (j == 0 || !incr_rows) {
       const uint32_t row = (uint32_t)it >> lb;
-      const uint32_t beta = (uint32_t)it & ((1u << lb) - 1u);
-      uint32_t ridx[M];
+      const uint32_t beta = (uint32_t)it & (Bco - 1u);
+      // with fixed batch entry the first row is below 2^r0 (later rows come
+      // from the tables); otherwise every row bit counts
+      const int nb = incr_rows ? min(w, r0) : w;
 #pragma unroll
       for (int i = 0; i < M; ++i) {
-        uint32_t r = 0;
-        for (int q = 0; q < nr[i]; ++q) {
-          const uint32_t pr = S.in[i].prun[q];
-          r |= ((row >> (pr & 0xffu)) & (pr >> 16)) << ((pr >> 8) & 0xffu);
-        }
-        ridx[i] = r;
+        int ri = 0;
+        for (int b = 0; b < nb; ++b)
+          if ((row >> b) & 1u) ri += vbit(S.in[i], b);
+        rowb[i] = soff[i] + (int)(((uint32_t)ri << bsh[i]) | (bsh[i] ? beta : 0u)) * 8;
       }
-      for (int e = g; e < terms; e += tpi) {
+    } else {
+      const int t = __ffs(j) - 1;
+#pragma unroll
+      for (int i = 0; i < M; ++i) rowb[i] += tab[i][t];
+    }
+    float2 acc = make_float2(0.f, 0.f);
+    if (live) {
+      int eb[M];
+#pragma unroll
+      for (int i = 0; i < M; ++i) eb[i] = eb0[i];
+      for (int jt = 0; jt < tcount; ++jt) {
+        if (jt) {
+          const int t = 16 + __ffs(jt) - 1;
+#pragma unroll
+          for (int i = 0; i < M; ++i) eb[i] += tab[i][t];
+        }
         float2 p = make_float2(1.f, 0.f);
 #pragma unroll
         for (int i = 0; i < M; ++i) {
-          const uint32_t idx =
-              egen[i] ? (ridx[i] | (pext_small((uint32_t)e, em[i]) << rb[i])) : ridx[i] + (uint32_t)e * est[i];
-          const float2 v = reinterpret_cast<const float2 *>(sm + soff[i])[(idx << bsh[i]) | (bsh[i] ? beta : 0u)];
+          const float2 v = *reinterpret_cast<const float2 *>(sm + rowb[i] + eb[i]);
           p = cmul(p, make_float2(v.x * scale[i], v.y * scale[i]));
         }
         acc.x += p.x;
         acc.y += p.y;
       }
     }
-    // reduce the tpi partial sums of an item (aligned lane groups)
+    // reduce the tpi partial sums of an item (aligned lane groups; tpi > 1
+    // only when every lane runs exactly one iteration)
     for (int q = 1; q < tpi; q <<= 1) {
       acc.x += __shfl_xor_sync(0xffffffffu, acc.x, q);
       acc.y += __shfl_xor_sync(0xffffffffu, acc.y, q);
@@ -435,12 +440,15 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
                int final_batched, double c_re, double c_im, double2 *out, Header *hdr) {
   extern __shared__ __align__(16) char sm[];
   __shared__ RStep wsd[RES_WARPS];
+  __shared__ int32_t wtab[RES_WARPS][MAXIN][TAB_W];
   const int Bc = 1 << logBc;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int64_t b0 = (int64_t)blockIdx.x * Bc;
-  RMeta *meta = reinterpret_cast<RMeta *>(sm);
-  for (int i = tid; i < n_meta * (int)(sizeof(RMeta) / 4); i += RES_THREADS)
-    reinterpret_cast<int *>(sm)[i] = 0;
+  Meta *meta = reinterpret_cast<Meta *>(sm);
+  for (int i = tid; i < n_meta; i += RES_THREADS) {
+    meta[i].maxbits = 0;
+    meta[i].exp = 0;
+  }
   // leaves of this chunk, one job per leaf row: batched rows take the base
   // entry selected by the output bits of x_beta, unbatched rows the entry
   const float2 *wsf = reinterpret_cast<const float2 *>(ws);
@@ -465,26 +473,27 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
       // this warp's copy of the descriptor
       const int *src = reinterpret_cast<const int *>(steps + s);
       int *dst = reinterpret_cast<int *>(&S);
-      for (int w = lane; w < RSTEP_WORDS; w += 32) dst[w] = __ldg(src + w);
+      for (int q = lane; q < RSTEP_WORDS; q += 32) dst[q] = __ldg(src + q);
       __syncwarp();
       const int lb = S.batched_out ? logBc : 0;
       const int items = (1 << S.w_out) << lb;
       const int gt = tid - 32 * w0, G = 32 * nw;
       float lmax;
       int esum = 0;
+      int32_t(*tab)[TAB_W] = wtab[wid];
       switch (S.m) {
-        case 1: lmax = res_step<1>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
-        case 2: lmax = res_step<2>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
-        case 3: lmax = res_step<3>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
-        case 4: lmax = res_step<4>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
-        case 5: lmax = res_step<5>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
-        case 6: lmax = res_step<6>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
-        case 7: lmax = res_step<7>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
-        default: lmax = res_step<8>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 1: lmax = res_step<1>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
+        case 2: lmax = res_step<2>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
+        case 3: lmax = res_step<3>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
+        case 4: lmax = res_step<4>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
+        case 5: lmax = res_step<5>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
+        case 6: lmax = res_step<6>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
+        case 7: lmax = res_step<7>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
+        default: lmax = res_step<8>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
       }
       for (int q = 16; q > 0; q >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
       if (lane == 0) {
-        meta[S.out_meta].wmax[wid - w0] = lmax;
+        if (lmax > 0.f) atomicMax(&meta[S.out_meta].maxbits, __float_as_uint(lmax));
         if (wid == w0) meta[S.out_meta].exp = esum;
       }
       __syncwarp();

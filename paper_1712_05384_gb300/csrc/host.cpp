@@ -611,7 +611,7 @@ static void build_resident(qgm_plan *p) {
   std::vector<int> order(ns);
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return level[a] < level[b]; });
-  const int64_t meta_bytes = ((int64_t)p->n_meta * (int64_t)(RES_WARPS * 4 + 8) + 15) & ~int64_t(15);
+  const int64_t meta_bytes = ((int64_t)p->n_meta * 8 + 15) & ~int64_t(15);
   for (int Bc : {1, 2, 4, 8}) {
     ResidentLayout L;
     L.chunk = Bc;
@@ -704,26 +704,16 @@ static void build_resident(qgm_plan *p) {
           in.meta = it.leaf < 0 ? it.meta : -1;
           // the input's offset as allocated (before its release above)
           in.soff = -1;
-          // split the union runs at the row/summed boundary (bit w_out)
-          int nr = 0, rowbits = 0;
-          uint32_t emask = 0;
-          for (int qq = 0; qq < d.in[i].nruns; ++qq) {
-            int a = d.in[i].src[qq], b = a + d.in[i].len[qq];
-            if (a < d.w_out) {
-              int hi = std::min(b, d.w_out);
-              if (nr >= RMAXRUN || hi - a > 16) {
-                ok = false;
-                break;
-              }
-              in.prun[nr] = (uint32_t)a | ((uint32_t)rowbits << 8) | (((1u << (hi - a)) - 1u) << 16);
-              rowbits += hi - a;
-              ++nr;
-            }
-            for (int bit = std::max(a, d.w_out); bit < b; ++bit) emask |= 1u << (bit - d.w_out);
+          // union bit -> input bit (union bit of variable a is U-1-a)
+          const int U = (int)st.uni.size();
+          if (U > RMAXBITS || d.w_out > 16) {
+            ok = false;
+            break;
           }
-          in.nruns = (uint8_t)nr;
-          in.rowbits = (uint8_t)rowbits;
-          in.emask = (uint16_t)emask;
+          for (int b = 0; b < RMAXBITS; ++b) in.vpos[b] = 0xff;
+          for (int qq = 0; qq < d.in[i].nruns; ++qq)
+            for (int l = 0; l < d.in[i].len[qq]; ++l)
+              in.vpos[d.in[i].src[qq] + l] = (uint8_t)(d.in[i].dst[qq] + l);
         }
         L.steps.push_back(r);
       }

@@ -85,19 +85,18 @@ struct LeafDesc {
 // Input index = pext(row, runs) | (pext(e, emask) << rowbits): the summed
 // variables are the top bits of the union index and, the input's variables
 // being sorted the same way, the top bits of the input index too.
-constexpr int RMAXRUN = 6;  // row runs of one resident input
+// Where each bit of the union index lands in one resident input's index:
+// vpos[b] for union bit b (row bits 0..w_out-1, then the k summed bits), or
+// 0xff when the input does not hold that variable.  Every input index is
+// linear in the union bits, which the kernel exploits to walk items and
+// terms by table-driven increments.
+constexpr int RMAXBITS = 24;
 struct RIn {
   int32_t soff;      // smem byte offset of the tensor
   int32_t meta;      // smem metadata slot (intermediates), -1 for leaves
   uint8_t batched;
-  uint8_t nruns;     // runs over the row (output) bits only
-  uint8_t rowbits;   // input bits that come from the row
-  uint8_t pad_;
-  uint16_t emask;    // which of the k summed variables the input holds
-  uint16_t pad2_;
-  // run q: bits [src, src + len) of the row go to bits [dst, dst + len) of
-  // the index; packed as src | dst << 8 | ((1 << len) - 1) << 16
-  uint32_t prun[RMAXRUN];
+  uint8_t pad_[3];
+  uint8_t vpos[RMAXBITS];
 };
 
 struct RStep {
