@@ -175,6 +175,20 @@ def test_grid5x5_d20_b1024_sampled(executor):
     assert abs((Np ** 2).mean() - gold["N_sum_p2"]) < 4 * (Np ** 2).std() / math.sqrt(len(Np))
 
 
+def test_grid6x6_d25_b1000_sampled():
+    # 6x6 grid, depth 25, 1000 bitstrings: intermediates up to 2^28 complex64
+    # entries (stepwise executor); 3 outputs against the oracle's elimination
+    c = qi.grid_circuit(6, 6, 25, 0)
+    a, bits, p = run_batch(c, 1000)
+    assert p.info.max_tensor_entries >= 2 ** 26
+    idx = np.array([0, 499, 998])
+    ref = ve.amplitudes(c, bits[idx])
+    rel, ab = errors(a[idx], ref, c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+    Np = (2 ** c.n) * np.abs(a) ** 2
+    assert abs(Np.mean() - 1) < 4 * Np.std() / math.sqrt(len(Np))
+
+
 @pytest.mark.parametrize("executor", EXECS)
 def test_host_api_matches_device_api(executor):
     q = Q()
