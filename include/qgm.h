@@ -145,6 +145,8 @@ typedef struct {
   int32_t n_order;            /* QGM_ORDER_GIVEN: length of `order` */
   const int32_t *order;       /* QGM_ORDER_GIVEN: elimination order (var ids) */
   int32_t executor;           /* QGM_EXEC_* */
+  int32_t gradients;          /* 1: also lay out the adjoint elimination of
+                                 qgm_amplitude_grad (more workspace) */
   int32_t resident_chunk;     /* bitstrings per CTA of the resident executor:
                                  1, 2, 4 or 8; 0 = chosen at bind (fewest
                                  waves x chunk on the bound device) */
@@ -250,7 +252,13 @@ int qgm_amplitudes_static(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, 
  * (synchronises `stream`): QGM_OK, QGM_ERR_NONFINITE or QGM_ERR_TIMEOUT. */
 int qgm_status(qgm_plan *p, void *stream);
 
-/* Gradient (adjoint elimination) for a parametrised circuit: given
+/* Gradient (adjoint elimination) for a parametrised circuit.  The forward
+ * elimination keeps every intermediate; the backward pass runs the steps in
+ * reverse, each step of Eq. par_sum giving the adjoint of each input as the
+ * product of the output's adjoint with the other inputs, summed over the
+ * variables the input does not hold (bucket elimination is a tree, so every
+ * tensor has exactly one consumer).  Needs a plan made with opts.gradients = 1
+ * and one slice.  Given
  * g_b = dL/d(conj a_b) for the B bitstrings (device double[2B]), writes
  * d_grad[i] = dL/dp_i = 2 Re sum_b conj(g_b) da_b/dp_i for the n_params
  * parameters (theta, phi of each RXY gate, see qgm_circuit_param_gates) into

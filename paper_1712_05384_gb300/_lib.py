@@ -38,7 +38,7 @@ class qgm_plan_opts(C.Structure):
     _fields_ = [("order_kind", C.c_int32), ("output_mode", C.c_int32), ("batch", C.c_int64),
                 ("mem_budget_bytes", C.c_int64), ("max_fuse", C.c_int32), ("n_order", C.c_int32),
                 ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
-                ("resident_chunk", C.c_int32)]
+                ("gradients", C.c_int32), ("resident_chunk", C.c_int32)]
 
 
 class qgm_plan_info(C.Structure):
@@ -210,7 +210,7 @@ class Model:
 class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
-                 resident_chunk=0):
+                 resident_chunk=0, gradients=False):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -220,6 +220,7 @@ class Plan:
         o.max_fuse = max_fuse
         o.executor = executor
         o.resident_chunk = resident_chunk
+        o.gradients = int(gradients)
         self._order_buf = None
         if order is not None:
             self._order_buf = np.ascontiguousarray(order, dtype=np.int32)

@@ -282,6 +282,62 @@ __global__ void k_accumulate(const char *ws, int64_t final_off, int final_meta, 
   }
 }
 
+// Adjoint seed: d(final)/d(final) = 1 for every batch entry, exponent 0.
+__global__ void k_seed(float2 *seed, int Bp, Meta *meta, int slot) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Bp; t += gridDim.x * blockDim.x)
+    seed[t] = make_float2(1.f, 0.f);
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    meta[slot].maxbits = __float_as_uint(1.f);
+    meta[slot].exp = 0;
+  }
+}
+
+// dL/dp for one parameter per block (blockIdx.x = 2 gate + which):
+// 2 Re( c * 2^E * sum_b conj(g_b) sum_r adj[r][b] D_p[r, x_b] ), with adj the
+// adjoint of the gate's leaf (exponent E), D_p its derivative table and
+// g_b = dL/d conj(a_b); accumulated in FP64.
+__global__ void k_grad_reduce(const char *ws, const GradParam *gp, const uint64_t *bits, int64_t B,
+                              int Bp, const double2 *g, const Meta *meta, double c_re, double c_im,
+                              double *grad) {
+  __shared__ double red_r[256], red_i[256];
+  const int pidx = blockIdx.x >> 1, which = blockIdx.x & 1;
+  const GradParam P = gp[pidx];
+  const float2 *adj = reinterpret_cast<const float2 *>(ws + P.adj_off);
+  const float2 *db = reinterpret_cast<const float2 *>(ws + P.dbase_off[which]);
+  const int64_t rows = (int64_t)1 << P.n_int;
+  double sr = 0.0, si = 0.0;
+  for (int64_t t = threadIdx.x; t < rows * B; t += blockDim.x) {
+    const int64_t r = t / B, b = t - r * B;
+    const float2 a = adj[r * Bp + b];
+    int ob = 0;
+    if (P.n_out > 0) {
+      const uint64_t x = bits[b];
+      for (int q = 0; q < P.n_out; ++q) ob |= (int)((x >> P.out_qubit[q]) & 1ull) << (P.n_out - 1 - q);
+    }
+    const float2 d = db[(r << P.n_out) | ob];
+    const double xr = (double)a.x * d.x - (double)a.y * d.y;
+    const double xi = (double)a.x * d.y + (double)a.y * d.x;
+    const double2 gb = g[b];
+    sr += gb.x * xr + gb.y * xi;
+    si += gb.x * xi - gb.y * xr;
+  }
+  red_r[threadIdx.x] = sr;
+  red_i[threadIdx.x] = si;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      red_r[threadIdx.x] += red_r[threadIdx.x + h];
+      red_i[threadIdx.x] += red_i[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double sc = ldexp(1.0, meta[P.adj_meta].exp);
+    const double Sr = red_r[0] * sc, Si = red_i[0] * sc;
+    grad[blockIdx.x] = 2.0 * (c_re * Sr - c_im * Si);
+  }
+}
+
 // Zero the FP64 result and the status, restart at slice 0.
 __global__ void k_init(double2 *out, int64_t n_out, Header *hdr) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_out;
@@ -603,7 +659,7 @@ static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, doub
   k_resident<<<(unsigned)G, RES_THREADS, (size_t)L.smem_bytes, st>>>(
       ws, reinterpret_cast<const RStep *>(ws + p->off_rsteps), (int)L.steps.size(),
       reinterpret_cast<const RJob *>(ws + p->off_rsteps + L.steps.size() * sizeof(RStep)),
-      (int)L.jobs.size(), d_bits, B, logBc, p->n_meta, L.final_soff, L.final_meta, p->final_batched,
+      (int)L.jobs.size(), d_bits, B, logBc, p->n_meta_fwd, L.final_soff, L.final_meta, p->final_batched,
       c.real(), c.imag(), d_out, reinterpret_cast<Header *>(x->ws + p->off_header));
 }
 
@@ -700,6 +756,10 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
   if (!p->leafdesc.empty())
     CK(cudaMemcpyAsync(x->ws + p->off_leafdesc, p->leafdesc.data(), p->leafdesc.size() * sizeof(LeafDesc),
                        cudaMemcpyHostToDevice, st));
+  if (p->grad && !p->gparams.empty())
+    CK(cudaMemcpyAsync(x->ws + p->off_gparams, p->gparams.data(), p->gparams.size() * sizeof(GradParam),
+                       cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
   // executor: resident when a layout fits; chunk size by fewest waves x chunk
   x->kind = QGM_EXEC_STEPWISE;
   x->layout = -1;
@@ -858,11 +918,40 @@ int qgm_status(qgm_plan *p, void *stream) {
 
 int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, const double *d_dL_dconja,
                        double *d_grad, double *d_amp, void *stream) {
-  (void)d_bitstrings; (void)B; (void)d_dL_dconja; (void)d_grad; (void)d_amp; (void)stream;
   int rc = check_bound(p, "qgm_amplitude_grad");
   if (rc) return rc;
-  set_error("qgm_amplitude_grad: not built yet");
-  return QGM_ERR_ARG;
+  if (!p->grad) {
+    set_error("qgm_amplitude_grad: the plan was made without opts.gradients");
+    return QGM_ERR_ARG;
+  }
+  if (B < 1 || B > p->batch || !d_bitstrings || !d_dL_dconja || !d_grad) {
+    set_error("qgm_amplitude_grad: need 1 <= B <= %lld and non-null buffers", (long long)p->batch);
+    return QGM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  qgm_exec_state *x = p->exec;
+  char *ws = x->ws;
+  Header *hdr = reinterpret_cast<Header *>(ws + p->off_header);
+  Meta *meta = reinterpret_cast<Meta *>(ws + p->off_meta);
+  double2 *amp = d_amp ? reinterpret_cast<double2 *>(d_amp) : reinterpret_cast<double2 *>(ws + p->off_outstage);
+  const int64_t iblocks = std::min<int64_t>((B + 255) / 256, (int64_t)x->sms * 4);
+  k_init<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(amp, B, hdr);
+  launch_leaves(p, d_bitstrings, B, st);
+  for (const StepDesc &d : p->gfwd) launch_step(p, d, st);
+  const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
+  k_accumulate<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(
+      ws, p->g_final_off, p->g_final_meta, 1, 0, B, amp, meta, hdr, c.real(), c.imag());
+  k_seed<<<(p->Bp + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2 *>(ws + p->g_seed_off), p->Bp, meta,
+                                               p->g_seed_meta);
+  for (const StepDesc &d : p->gbwd) launch_step(p, d, st);
+  const int n_gates = (int)p->gparams.size();
+  if (n_gates > 0)
+    k_grad_reduce<<<2 * n_gates, 256, 0, st>>>(ws, reinterpret_cast<const GradParam *>(ws + p->off_gparams),
+                                               d_bitstrings, B, p->Bp,
+                                               reinterpret_cast<const double2 *>(d_dL_dconja), meta, c.real(),
+                                               c.imag(), d_grad);
+  CK(cudaGetLastError());
+  return QGM_OK;
 }
 
 }  // extern "C"

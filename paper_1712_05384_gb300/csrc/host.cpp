@@ -584,6 +584,76 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
 
 static int64_t pow2(int r) { return (int64_t)1 << r; }
 
+// Table of model factor fi (inputs substituted by 0) on `scope`, optionally
+// with the RXY table replaced by its derivative (which = 0: theta, 1: phi).
+static std::vector<cd> member_table(const Model &m, int fi, const std::vector<int> &scope,
+                                    int deriv_which) {
+  const MFactor &f = m.factors[fi];
+  cd t[4];
+  for (int i = 0; i < 4; ++i) t[i] = f.t[i];
+  if (deriv_which >= 0) {
+    const qgm_gate &g = m.gates[f.gate];
+    const cd I(0.0, 1.0);
+    const double c = std::cos(g.theta / 2), sn = std::sin(g.theta / 2);
+    if (deriv_which == 0) {  // d/dtheta of [[c, -i e^{-i phi} s], [-i e^{i phi} s, c]]
+      t[0] = -0.5 * sn;
+      t[1] = -I * std::exp(-I * g.phi) * (0.5 * c);
+      t[2] = -I * std::exp(I * g.phi) * (0.5 * c);
+      t[3] = -0.5 * sn;
+    } else {  // d/dphi
+      t[0] = 0.0;
+      t[1] = -std::exp(-I * g.phi) * sn;
+      t[2] = std::exp(I * g.phi) * sn;
+      t[3] = 0.0;
+    }
+  }
+  std::vector<char> is_in(m.n_vars, 0);
+  for (int v : m.inputs) is_in[v] = 1;
+  std::vector<int> keep;
+  for (int a = 0; a < f.nv; ++a)
+    if (!is_in[f.v[a]]) keep.push_back(a);
+  std::vector<int> sc;
+  for (int a : keep) sc.push_back(f.v[a]);
+  std::vector<cd> tab((size_t)1 << keep.size());
+  for (size_t i = 0; i < tab.size(); ++i) {
+    int full = 0;
+    for (size_t b = 0; b < keep.size(); ++b)
+      if ((i >> (keep.size() - 1 - b)) & 1) full |= 1 << (f.nv - 1 - keep[b]);
+    tab[i] = t[full];
+  }
+  return expand_table(sc, tab, scope);
+}
+
+// Index map of an operand whose variables `opvars` (most significant first)
+// are a subset of the union `uni` (most significant first), as runs of
+// contiguous union bits landing on contiguous operand bits.
+static bool make_runs(const std::vector<int> &uni, const std::vector<int> &opvars, InDesc &in) {
+  const int U = (int)uni.size(), R = (int)opvars.size();
+  std::vector<int> vpos(U, -1);
+  for (int b = 0; b < U; ++b) {
+    const int v = uni[U - 1 - b];
+    for (int a = 0; a < R; ++a)
+      if (opvars[a] == v) vpos[b] = R - 1 - a;
+  }
+  int nr = 0, b = 0;
+  while (b < U) {
+    if (vpos[b] < 0) {
+      ++b;
+      continue;
+    }
+    const int st = b;
+    ++b;
+    while (b < U && vpos[b] == vpos[b - 1] + 1) ++b;
+    if (nr >= MAXRUN) return false;
+    in.src[nr] = (uint8_t)st;
+    in.len[nr] = (uint8_t)(b - st);
+    in.dst[nr] = (uint8_t)vpos[st];
+    ++nr;
+  }
+  in.nruns = nr;
+  return true;
+}
+
 // Shared-memory layouts of the resident executor for chunks of Bc batch
 // entries.  Steps are grouped into dependency levels (a step's level is one
 // more than the highest level among the steps producing its inputs); the
@@ -921,8 +991,16 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   for (const SymTensor &t : S.tensors)
     if (t.leaf < 0) n_meta = std::max(n_meta, t.meta + 1);
   p->n_meta = n_meta;
+  p->n_meta_fwd = n_meta;
+  p->grad = o.gradients != 0;
+  if (p->grad && (o.output_mode != QGM_OUT_BATCH || !p->slice_vars.empty())) {
+    set_error("qgm_plan_order: gradients need a batch plan without slices");
+    return QGM_ERR_ARG;
+  }
+  // with gradients: one more slot per adjoint (at most one per tensor) + seed
+  const int meta_slots = p->grad ? (int)(n_meta + S.tensors.size() + 2) : n_meta;
   p->off_header = take(256);
-  p->off_meta = take((int64_t)std::max(n_meta, 1) * 8);
+  p->off_meta = take((int64_t)std::max(meta_slots, 1) * 8);
   p->off_leafdesc = take((int64_t)std::max<size_t>(p->leaves.size(), 1) * sizeof(LeafDesc));
   // base tables: (internal vars by position | slice vars | output vars by qubit)
   p->base_tables.clear();
@@ -934,6 +1012,20 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     base_at[li] = base_floats;
     base_floats += 2 * (int64_t)p->leaves[li].table.size();
     base_floats = (base_floats + 3) & ~int64_t(3);
+  }
+  // derivative tables (theta, phi) of the leaves that hold an RXY gate
+  std::vector<int> rxy_member(p->leaves.size(), -1);
+  std::vector<int64_t> dbase_at(p->leaves.size(), -1);
+  if (p->grad) {
+    for (size_t li = 0; li < p->leaves.size(); ++li)
+      for (int fi : p->leaves[li].members)
+        if (m.gates[m.factors[fi].gate].kind == QGM_GATE_RXY) rxy_member[li] = fi;
+    for (size_t li = 0; li < p->leaves.size(); ++li)
+      if (rxy_member[li] >= 0) {
+        dbase_at[li] = base_floats;
+        base_floats += 4 * (int64_t)p->leaves[li].table.size();
+        base_floats = (base_floats + 3) & ~int64_t(3);
+      }
   }
   p->off_base = take(base_floats * 4);
   p->base_tables.assign(base_floats, 0.f);
@@ -963,6 +1055,21 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     for (size_t i = 0; i < tab.size(); ++i) {
       p->base_tables[base_at[li] + 2 * i] = (float)tab[i].real();
       p->base_tables[base_at[li] + 2 * i + 1] = (float)tab[i].imag();
+    }
+    if (p->grad && rxy_member[li] >= 0) {
+      // d(leaf)/dp = (product of the other members) x d(RXY)/dp
+      for (int which = 0; which < 2; ++which) {
+        std::vector<cd> dt(tab.size(), 1.0);
+        for (int fi : L.members) {
+          std::vector<cd> mt = member_table(m, fi, layout, fi == rxy_member[li] ? which : -1);
+          for (size_t i = 0; i < dt.size(); ++i) dt[i] *= mt[i];
+        }
+        const int64_t at = dbase_at[li] + 2 * which * (int64_t)tab.size();
+        for (size_t i = 0; i < dt.size(); ++i) {
+          p->base_tables[at + 2 * i] = (float)dt[i].real();
+          p->base_tables[at + 2 * i + 1] = (float)dt[i].imag();
+        }
+      }
     }
     LeafDesc d{};
     d.base_off = p->off_base + base_at[li] * 4;
@@ -1052,6 +1159,118 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     p->steps.push_back(d);
   }
   build_resident(p);
+  if (p->grad) {
+    // ------------------------------------------- adjoint elimination layout
+    // forward intermediates keep their own region (no reuse); adjoints too
+    int64_t goff = p->ws_bytes - 256;
+    auto gtake = [&](int64_t bytes) {
+      int64_t o2 = goff;
+      goff += (bytes + 255) & ~int64_t(255);
+      return o2;
+    };
+    const int nt = (int)S.tensors.size();
+    std::vector<int64_t> fwd_off(nt, -1);
+    for (int t = 0; t < nt; ++t)
+      fwd_off[t] = S.tensors[t].leaf >= 0 ? S.tensors[t].off : gtake(S.tensors[t].entries * 8);
+    // which tensors lead to a parametrised leaf
+    std::vector<char> need(nt, 0);
+    for (size_t li = 0; li < p->leaves.size(); ++li) need[li] = rxy_member[li] >= 0;
+    for (const StepRec &st : S.steps)
+      for (int id : st.inputs) need[st.out] |= need[id];
+    p->gfwd = p->steps;
+    for (size_t si = 0; si < S.steps.size(); ++si) {
+      StepDesc &d = p->gfwd[si];
+      d.out_off = fwd_off[S.steps[si].out];
+      for (int i = 0; i < d.m; ++i) d.in[i].off = fwd_off[S.steps[si].inputs[i]];
+    }
+    const SymTensor &Fg = S.tensors[S.final_tensor];
+    p->g_final_off = fwd_off[S.final_tensor];
+    p->g_final_meta = Fg.leaf < 0 ? Fg.meta : -1;
+    p->g_final_batched = Fg.batched ? 1 : 0;
+    if (Fg.leaf >= 0 || !Fg.vars.empty() || !Fg.batched) {
+      set_error("internal: gradient needs a batched rank-0 final tensor");
+      return QGM_ERR_ARG;
+    }
+    // adjoints: the seed for the final tensor (ones), then one per needed input
+    std::vector<int64_t> adj_off(nt, -1);
+    std::vector<int> adj_meta(nt, -1);
+    int next_meta = p->n_meta_fwd;
+    adj_off[S.final_tensor] = gtake(Bp * 8);
+    adj_meta[S.final_tensor] = next_meta++;
+    p->g_seed_off = adj_off[S.final_tensor];
+    p->g_seed_meta = adj_meta[S.final_tensor];
+    p->gbwd.clear();
+    for (int si = (int)S.steps.size() - 1; si >= 0; --si) {
+      const StepRec &st = S.steps[si];
+      if (!need[st.out] || adj_off[st.out] < 0) continue;
+      const SymTensor &ot = S.tensors[st.out];
+      for (size_t i = 0; i < st.inputs.size(); ++i) {
+        const int id = st.inputs[i];
+        if (!need[id]) continue;
+        const SymTensor &it = S.tensors[id];
+        // union: the variables summed here first, then the input's own
+        std::vector<int> summed, uni;
+        for (int v : st.uni)
+          if (std::find(it.vars.begin(), it.vars.end(), v) == it.vars.end()) summed.push_back(v);
+        uni = summed;
+        uni.insert(uni.end(), it.vars.begin(), it.vars.end());
+        StepDesc d{};
+        d.k = (int)summed.size();
+        d.w_out = (int)it.vars.size();
+        d.batched_out = 1;
+        adj_off[id] = gtake(pow2(d.w_out) * Bp * 8);
+        adj_meta[id] = next_meta++;
+        d.out_off = adj_off[id];
+        d.out_meta = adj_meta[id];
+        int mm = 0;
+        InDesc &a0 = d.in[mm++];
+        a0.off = adj_off[st.out];
+        a0.meta = adj_meta[st.out];
+        a0.batched = 1;
+        bool ok = make_runs(uni, ot.vars, a0);
+        for (size_t k2 = 0; k2 < st.inputs.size() && ok; ++k2) {
+          if (k2 == i) continue;
+          const SymTensor &kt = S.tensors[st.inputs[k2]];
+          InDesc &ik = d.in[mm++];
+          ik.off = fwd_off[st.inputs[k2]];
+          ik.meta = kt.leaf < 0 ? kt.meta : -1;
+          ik.batched = kt.batched ? 1 : 0;
+          ok = make_runs(uni, kt.vars, ik);
+        }
+        if (!ok) {
+          set_error("internal: adjoint index map with more than %d runs", MAXRUN);
+          return QGM_ERR_ARG;
+        }
+        d.m = mm;
+        p->gbwd.push_back(d);
+      }
+    }
+    // one record per RXY gate, in circuit order
+    p->gparams.clear();
+    for (size_t pi = 0; pi < m.param_factor.size(); ++pi) {
+      const int fi = m.param_factor[pi];
+      int li = -1;
+      for (size_t l = 0; l < p->leaves.size(); ++l)
+        if (rxy_member[l] == fi) li = (int)l;
+      if (li < 0 || adj_off[li] < 0) {
+        set_error("internal: parameter %zu has no adjoint", pi);
+        return QGM_ERR_ARG;
+      }
+      GradParam g{};
+      const int64_t tsz = (int64_t)p->leaves[li].table.size();
+      g.dbase_off[0] = p->off_base + dbase_at[li] * 4;
+      g.dbase_off[1] = p->off_base + (dbase_at[li] + 2 * tsz) * 4;
+      g.adj_off = adj_off[li];
+      g.adj_meta = adj_meta[li];
+      g.n_int = p->leafdesc[li].n_int;
+      g.n_out = p->leafdesc[li].n_out;
+      for (int a = 0; a < MAXLEAFV; ++a) g.out_qubit[a] = p->leafdesc[li].out_qubit[a];
+      p->gparams.push_back(g);
+    }
+    p->off_gparams = gtake((int64_t)std::max<size_t>(p->gparams.size(), 1) * sizeof(GradParam));
+    p->n_meta = next_meta;
+    p->ws_bytes = goff + 256;
+  }
   if (o.executor < 0 || o.executor > 2) {
     set_error("qgm_plan_order: bad executor %d", o.executor);
     return QGM_ERR_ARG;

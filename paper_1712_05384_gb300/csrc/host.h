@@ -46,7 +46,7 @@ struct Model {
 
 // ------------------------------------------------------------------- plan
 constexpr int MAXIN = 8;    // tensors multiplied in one step
-constexpr int MAXRUN = 12;  // contiguous bit runs of an index map
+constexpr int MAXRUN = 16;  // contiguous bit runs of an index map
 constexpr int MAXLEAFV = 4; // variables of a leaf factor (internal+slice+output)
 
 // Index map of one step input: the input's index is the union index with
@@ -138,6 +138,18 @@ struct ResidentLayout {
   int final_soff = -1, final_meta = -1;
 };
 
+// Gradient of one parametrised gate (adjoint elimination): the adjoint of
+// the leaf holding the gate, and the leaf's derivative tables with respect to
+// theta and phi in the leaf's base-table layout.
+struct GradParam {
+  int64_t dbase_off[2];  // complex64 derivative base tables (bytes into the workspace)
+  int64_t adj_off;       // adjoint of the leaf: rows x batch_padded complex64
+  int32_t adj_meta;
+  int32_t n_int, n_out;
+  int32_t out_qubit[MAXLEAFV];
+  int32_t pad_;
+};
+
 struct SymTensor {
   std::vector<int> vars;  // sorted by elimination position
   bool batched = false;
@@ -213,6 +225,14 @@ struct qgm_plan {
   int final_batched = 0;
   int64_t final_off = 0;
   int final_meta = -1;
+  // adjoint elimination (qgm_plan_opts.gradients): forward steps that keep
+  // every intermediate, the seed, backward steps, one record per parameter
+  bool grad = false;
+  std::vector<qgm::StepDesc> gfwd, gbwd;
+  std::vector<qgm::GradParam> gparams;
+  int64_t g_final_off = 0, g_seed_off = 0, off_gparams = 0;
+  int g_final_meta = -1, g_seed_meta = -1, g_final_batched = 0;
+  int n_meta_fwd = 0;
   // resident executor layouts for Bc = 1, 2, 4, 8 (empty when infeasible)
   std::vector<qgm::ResidentLayout> resident;
   int64_t off_rsteps = 0;   // workspace region for the chosen layout's steps
