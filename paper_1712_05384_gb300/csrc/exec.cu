@@ -143,47 +143,118 @@ __global__ void k_build_leaves(char *ws, const LeafDesc *leaves, int n_leaves, M
   }
 }
 
+// Position in an input's index of union bit b (from the input's runs), as
+// the value 2^pos, or 0 when the input does not hold that variable.
+__device__ __forceinline__ int64_t run_bit(const InDesc &in, int b) {
+  for (int q = 0; q < in.nruns; ++q) {
+    const int s0 = in.src[q];
+    if (b >= s0 && b < s0 + in.len[q]) return (int64_t)1 << (in.dst[q] + b - s0);
+  }
+  return 0;
+}
+
+// Increment tables of one launch (every input index is linear in the bits of
+// the union index): when a thread's row counter carries into bit t the byte
+// address of input i moves by rowtab[i][t]; when its term counter carries into
+// bit t, by etab[i][t].  Rows advance by 2^r0, terms by 2^lt.
+constexpr int ROWTAB = 32, ETAB = 16;
+
+__device__ void build_tables(const StepDesc &d, int r0, int lt, int Bp, int64_t (*rowtab)[ROWTAB],
+                             int64_t (*etab)[ETAB], int tid, int nthreads) {
+  for (int x = tid; x < MAXIN * (ROWTAB + ETAB); x += nthreads) {
+    const int i = x / (ROWTAB + ETAB), t = x - i * (ROWTAB + ETAB);
+    if (i >= d.m) continue;
+    const InDesc &in = d.in[i];
+    const int64_t unit = in.batched ? (int64_t)Bp * 8 : 8;
+    const bool row = t < ROWTAB;
+    const int tt = row ? t : t - ROWTAB;
+    const int base = row ? r0 : d.w_out + lt;
+    const int lim = row ? d.w_out - r0 : d.k - lt;
+    int64_t v = 0;
+    if (tt < lim) {
+      v = run_bit(in, base + tt);
+      for (int b = 0; b < tt; ++b) v -= run_bit(in, base + b);
+    }
+    if (row) rowtab[i][tt] = v * unit;
+    else etab[i][tt] = v * unit;
+  }
+}
+
 // Product-sum step, batched output: thread (x, y) = (pair of batch entries,
-// term group); threadIdx.y splits the 2^k summed terms when rows are few.
+// term group).  Rows are walked at stride gridDim.y (a power of two), terms
+// at stride blockDim.y (a power of two); addresses advance by table lookups.
 __global__ void __launch_bounds__(1024)
     k_step_batched(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp) {
   __shared__ float4 part[1024];
+  __shared__ int64_t rowtab[MAXIN][ROWTAB];
+  __shared__ int64_t etab[MAXIN][ETAB];
   const int tx = threadIdx.x, ty = threadIdx.y, T = blockDim.y;
+  const int tid = ty * STEP_THREADS + tx;
+  const int r0 = __ffs(gridDim.y) - 1, lt = __ffs(T) - 1;
+  build_tables(d, r0, lt, Bp, rowtab, etab, tid, STEP_THREADS * T);
   const int bp = (blockIdx.x * STEP_THREADS + tx) * 2;
   const bool active = bp < Bp;
   float scale[MAXIN];
   int esum = 0;
+  int64_t rowb[MAXIN], eb0[MAXIN];
+  const uint64_t j0 = blockIdx.y;
 #pragma unroll
   for (int i = 0; i < MAXIN; ++i) {
+    scale[i] = 1.f;
+    rowb[i] = 0;
+    eb0[i] = 0;
     if (i < d.m) {
+      const InDesc &in = d.in[i];
       int e;
-      operand_scale(meta, d.in[i].meta, hdr, &scale[i], &e);
-      esum += e + (d.in[i].meta >= 0 ? meta[d.in[i].meta].exp : 0);
+      operand_scale(meta, in.meta, hdr, &scale[i], &e);
+      esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
+      const int64_t unit = in.batched ? (int64_t)Bp * 8 : 8;
+      int64_t ri = 0, ei = 0;
+      for (int b = 0; b < r0 && b < d.w_out; ++b)
+        if ((j0 >> b) & 1) ri += run_bit(in, b);
+      for (int b = 0; b < lt; ++b)
+        if ((ty >> b) & 1) ei += run_bit(in, d.w_out + b);
+      rowb[i] = in.off + ri * unit + (in.batched ? (int64_t)bp * 8 : 0);
+      eb0[i] = ei * unit;
     }
   }
-  if (blockIdx.x == 0 && blockIdx.y == 0 && tx == 0 && ty == 0) meta[d.out_meta].exp = esum;
+  if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) meta[d.out_meta].exp = esum;
+  __syncthreads();
   const uint64_t rows = 1ull << d.w_out;
-  const uint64_t terms = 1ull << d.k;
+  const int tcount = 1 << (d.k - lt);
   float lmax = 0.f;
   float2 *out = reinterpret_cast<float2 *>(ws + d.out_off);
-  for (uint64_t j = blockIdx.y; j < rows; j += gridDim.y) {
+  uint64_t it = 0;
+  for (uint64_t j = j0; j < rows; j += gridDim.y, ++it) {
+    if (it) {
+      const int t = __ffsll((long long)it) - 1;
+#pragma unroll
+      for (int i = 0; i < MAXIN; ++i)
+        if (i < d.m) rowb[i] += rowtab[i][t];
+    }
     float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
     if (active) {
-      for (uint64_t e = ty; e < terms; e += T) {
-        const uint64_t f = (e << d.w_out) | j;
+      int64_t eb[MAXIN];
+#pragma unroll
+      for (int i = 0; i < MAXIN; ++i) eb[i] = eb0[i];
+      for (int jt = 0; jt < tcount; ++jt) {
+        if (jt) {
+          const int t = __ffs(jt) - 1;
+#pragma unroll
+          for (int i = 0; i < MAXIN; ++i)
+            if (i < d.m) eb[i] += etab[i][t];
+        }
         float2 p0 = make_float2(1.f, 0.f), p1 = p0;
 #pragma unroll
         for (int i = 0; i < MAXIN; ++i) {
           if (i < d.m) {
-            const InDesc &in = d.in[i];
-            const uint64_t idx = pext_runs(f, in);
-            if (in.batched) {
-              const float4 v = __ldg(reinterpret_cast<const float4 *>(ws + in.off) +
-                                     ((idx * (uint64_t)Bp + bp) >> 1));
+            const char *a = ws + rowb[i] + eb[i];
+            if (d.in[i].batched) {
+              const float4 v = __ldg(reinterpret_cast<const float4 *>(a));
               p0 = cmul(p0, make_float2(v.x * scale[i], v.y * scale[i]));
               p1 = cmul(p1, make_float2(v.z * scale[i], v.w * scale[i]));
             } else {
-              const float2 v = __ldg(reinterpret_cast<const float2 *>(ws + in.off) + idx);
+              const float2 v = __ldg(reinterpret_cast<const float2 *>(a));
               const float2 sv = make_float2(v.x * scale[i], v.y * scale[i]);
               p0 = cmul(p0, sv);
               p1 = cmul(p1, sv);
@@ -213,40 +284,69 @@ __global__ void __launch_bounds__(1024)
   record_max(lmax, meta, d.out_meta);
 }
 
-// Product-sum step without a batch axis: thread = output entry j.
+// Product-sum step without a batch axis: thread = output entry j, rows walked
+// at stride gridDim.x * blockDim.x (a power of two) with table increments.
 __global__ void __launch_bounds__(256)
     k_step_plain(char *ws, const StepDesc d, Meta *meta, Header *hdr) {
+  __shared__ int64_t rowtab[MAXIN][ROWTAB];
+  __shared__ int64_t etab[MAXIN][ETAB];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const int r0 = __ffsll((long long)stride) - 1;
+  build_tables(d, r0, 0, 1, rowtab, etab, threadIdx.x, blockDim.x);
   float scale[MAXIN];
   int esum = 0;
+  int64_t rowb[MAXIN];
+  const uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
   for (int i = 0; i < MAXIN; ++i) {
+    scale[i] = 1.f;
+    rowb[i] = 0;
     if (i < d.m) {
+      const InDesc &in = d.in[i];
       int e;
-      operand_scale(meta, d.in[i].meta, hdr, &scale[i], &e);
-      esum += e + (d.in[i].meta >= 0 ? meta[d.in[i].meta].exp : 0);
+      operand_scale(meta, in.meta, hdr, &scale[i], &e);
+      esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
+      int64_t ri = 0;
+      for (int b = 0; b < r0 && b < d.w_out; ++b)
+        if ((j0 >> b) & 1) ri += run_bit(in, b);
+      rowb[i] = in.off + ri * 8;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) meta[d.out_meta].exp = esum;
+  __syncthreads();
   const uint64_t rows = 1ull << d.w_out;
-  const uint64_t terms = 1ull << d.k;
+  const int tcount = 1 << d.k;
   float lmax = 0.f;
   float2 *out = reinterpret_cast<float2 *>(ws + d.out_off);
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < rows;
-       j += (uint64_t)gridDim.x * blockDim.x) {
+  uint64_t it = 0;
+  for (uint64_t j = j0; j < rows; j += stride, ++it) {
+    if (it) {
+      const int t = __ffsll((long long)it) - 1;
+#pragma unroll
+      for (int i = 0; i < MAXIN; ++i)
+        if (i < d.m) rowb[i] += rowtab[i][t];
+    }
     float2 a = make_float2(0.f, 0.f);
-    for (uint64_t e = 0; e < terms; ++e) {
-      const uint64_t f = (e << d.w_out) | j;
-      float2 p = make_float2(1.f, 0.f);
+    int64_t eb[MAXIN];
+#pragma unroll
+    for (int i = 0; i < MAXIN; ++i) eb[i] = 0;
+    for (int jt = 0; jt < tcount; ++jt) {
+      if (jt) {
+        const int t = __ffs(jt) - 1;
+#pragma unroll
+        for (int i = 0; i < MAXIN; ++i)
+          if (i < d.m) eb[i] += etab[i][t];
+      }
+      float2 pr = make_float2(1.f, 0.f);
 #pragma unroll
       for (int i = 0; i < MAXIN; ++i) {
         if (i < d.m) {
-          const float2 v =
-              __ldg(reinterpret_cast<const float2 *>(ws + d.in[i].off) + pext_runs(f, d.in[i]));
-          p = cmul(p, make_float2(v.x * scale[i], v.y * scale[i]));
+          const float2 v = __ldg(reinterpret_cast<const float2 *>(ws + rowb[i] + eb[i]));
+          pr = cmul(pr, make_float2(v.x * scale[i], v.y * scale[i]));
         }
       }
-      a.x += p.x;
-      a.y += p.y;
+      a.x += pr.x;
+      a.y += pr.y;
     }
     out[j] = a;
     lmax = fmaxf(lmax, absmax2(a));
@@ -606,26 +706,36 @@ static void launch_leaves(qgm_plan *p, const uint64_t *d_bits, int64_t B, cudaSt
       reinterpret_cast<Header *>(ws + p->off_header), d_bits, B, p->Bp);
 }
 
-static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st) {
-  qgm_exec_state *x = p->exec;
-  char *ws = x->ws;
-  Meta *meta = reinterpret_cast<Meta *>(ws + p->off_meta);
-  Header *hdr = reinterpret_cast<Header *>(ws + p->off_header);
+// Grid of one product-sum step: row strides are powers of two so that the
+// kernels can walk rows by table increments.
+static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, Meta *meta, Header *hdr,
+                           cudaStream_t st) {
   const uint64_t rows = 1ull << d.w_out;
+  auto pow2_floor = [](uint64_t v) {
+    uint64_t r = 1;
+    while (r * 2 <= v) r *= 2;
+    return r;
+  };
   if (d.batched_out) {
-    const int bx = (p->Bp / 2 + STEP_THREADS - 1) / STEP_THREADS;
-    const uint64_t cap = (uint64_t)std::max(1, x->sms * 16 / bx);
+    const int bx = (Bp / 2 + STEP_THREADS - 1) / STEP_THREADS;
+    const uint64_t cap = (uint64_t)std::max(1, sms * 16 / bx);
     // split the summed terms over threadIdx.y while the grid is small
     int T = 1;
     while (T < 8 && (T * 2) <= (1 << std::min(d.k, 4)) &&
-           rows * (uint64_t)bx * STEP_THREADS * T < (uint64_t)x->sms * 1024)
+           rows * (uint64_t)bx * STEP_THREADS * T < (uint64_t)sms * 1024)
       T *= 2;
-    dim3 grid(bx, (unsigned)std::min<uint64_t>(rows, std::min<uint64_t>(cap, 65535)));
-    k_step_batched<<<grid, dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, p->Bp);
+    const uint64_t gy = pow2_floor(std::min<uint64_t>(rows, std::min<uint64_t>(cap, 32768)));
+    k_step_batched<<<dim3(bx, (unsigned)gy), dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, Bp);
   } else {
-    const uint64_t blocks = (rows + 255) / 256;
-    k_step_plain<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)x->sms * 8), 256, 0, st>>>(ws, d, meta, hdr);
+    const uint64_t blocks = pow2_floor(std::max<uint64_t>(1, std::min<uint64_t>((rows + 255) / 256, (uint64_t)sms * 8)));
+    k_step_plain<<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr);
   }
+}
+
+static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st) {
+  char *ws = p->exec->ws;
+  launch_step_ws(ws, p->exec->sms, p->Bp, d, reinterpret_cast<Meta *>(ws + p->off_meta),
+                 reinterpret_cast<Header *>(ws + p->off_header), st);
 }
 
 static void launch_accumulate(qgm_plan *p, double2 *d_out, int64_t n_out, cudaStream_t st) {
@@ -1007,22 +1117,7 @@ void static_slice(const qgm_plan *p, char *ws, int sms, const uint64_t *d_bits, 
   const int nl = (int)p->leafdesc.size();
   k_build_leaves<<<std::max(nl, 1), 256, 0, st>>>(ws, reinterpret_cast<const LeafDesc *>(ws + p->off_leafdesc),
                                                    nl, meta, p->n_meta, hdr, d_bits, B, p->Bp);
-  for (const StepDesc &d : p->steps) {
-    const uint64_t rows = 1ull << d.w_out;
-    if (d.batched_out) {
-      const int bx = (p->Bp / 2 + STEP_THREADS - 1) / STEP_THREADS;
-      const uint64_t cap = (uint64_t)std::max(1, sms * 16 / bx);
-      int T = 1;
-      while (T < 8 && (T * 2) <= (1 << std::min(d.k, 4)) &&
-             rows * (uint64_t)bx * STEP_THREADS * T < (uint64_t)sms * 1024)
-        T *= 2;
-      dim3 grid(bx, (unsigned)std::min<uint64_t>(rows, std::min<uint64_t>(cap, 65535)));
-      k_step_batched<<<grid, dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, p->Bp);
-    } else {
-      const uint64_t blocks = (rows + 255) / 256;
-      k_step_plain<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)sms * 8), 256, 0, st>>>(ws, d, meta, hdr);
-    }
-  }
+  for (const StepDesc &d : p->steps) launch_step_ws(ws, sms, p->Bp, d, meta, hdr, st);
   const int64_t blocks = std::min<int64_t>((B + 255) / 256, (int64_t)sms * 8);
   const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
   k_accumulate<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(
