@@ -453,8 +453,6 @@ __global__ void k_init(double2 *out, int64_t n_out, Header *hdr) {
 // global write is the chunk's FP64 amplitudes.  Steps are separated by
 // __syncthreads only: no grid-wide barrier, no launch per step.
 constexpr int RES_THREADS = 256;
-constexpr int RSTEP_WORDS = (int)(sizeof(RStep) / 4);
-static_assert(RSTEP_WORDS <= RES_THREADS, "one descriptor word per thread");
 
 // pext of the summed-variable index e by a k-bit mask (bits kept in order)
 __device__ __forceinline__ uint32_t pext_small(uint32_t e, uint32_t mask) {
@@ -468,65 +466,39 @@ __device__ __forceinline__ uint32_t pext_small(uint32_t e, uint32_t mask) {
   return r;
 }
 
-// Increment tables of one warp for one step: for input i, entry t < 16 is the
-// byte change of the input address when the thread's row counter carries
-// into bit t (row bits above the thread's fixed low bits), entry 16 + t the
-// change when its term counter carries into bit t.
-constexpr int TAB_W = 24;
-
-__device__ __forceinline__ int vbit(const RIn &in, int b) {
-  const int p = in.vpos[b];
-  return p == 0xff ? 0 : (1 << p);
-}
-
 // One elimination step run by a group of G threads (gt = index in the
 // group).  Each input index is linear in the bits of (row, e): a thread
-// starts from its first item and term and then only adds table entries
-// selected by the trailing zeros of its item and term counters.
+// starts from its first item and term and then only adds the planner's
+// table entries selected by the trailing zeros of its item and term counters.
 template <int M>
 __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *meta, Header *hdr,
                                           int logBc, int lb, int lg, int items, int gt, int G,
-                                          int lane, int32_t (*tab)[TAB_W], int *esum_out) {
-  const int k = S.k, w = S.w_out;
+                                          int *esum_out) {
+  const int k = S.k;
   const int tpi = 1 << lg;
-  const int sit = G >> lg;                  // item stride of one thread
-  const int Bco = 1 << lb;
-  const bool incr_rows = sit >= Bco;        // the thread's batch entry is fixed
-  const int r0 = incr_rows ? (__ffs(sit) - 1 - lb) : 0;
-  for (int x = lane; x < M * TAB_W; x += 32) {
-    const int i = x / TAB_W, t = x - i * TAB_W;
-    const RIn &in = S.in[i];
-    const int base = t < 16 ? r0 : w + lg;
-    const int tt = t < 16 ? t : t - 16;
-    const int lim = t < 16 ? w - r0 : k - lg;
-    int val = 0;
-    if (tt < lim) {
-      val = vbit(in, base + tt);
-      for (int b = 0; b < tt; ++b) val -= vbit(in, base + b);
-    }
-    tab[i][t] = val * (8 << (in.batched ? logBc : 0));
-  }
-  __syncwarp();
+  const int sit = G >> lg;                  // item stride of one thread (>= 2^lb)
   float scale[M];
-  int soff[M], bsh[M], eb0[M];
+  int rowb[M], eb0[M];
   int esum = 0;
   const int it0 = gt >> lg, g = gt & (tpi - 1);
+  const uint32_t row0 = (uint32_t)it0 >> lb;
+  const uint32_t beta = (uint32_t)it0 & ((1u << lb) - 1u);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const RIn &in = S.in[i];
-    bsh[i] = in.batched ? logBc : 0;
-    soff[i] = in.soff;
+    int ri = in.soff + (in.batched ? (int)beta * 8 : 0);
+    for (int b = 0; b < in.nlow; ++b)
+      if ((row0 >> b) & 1u) ri += in.lrow[b];
+    rowb[i] = ri;
     int ei = 0;
     for (int b = 0; b < lg; ++b)
-      if ((g >> b) & 1) ei += vbit(in, w + b);
-    eb0[i] = (ei << bsh[i]) * 8;
+      if ((g >> b) & 1) ei += in.lterm[b];
+    eb0[i] = ei;
     int e;
     operand_scale(meta, in.meta, hdr, &scale[i], &e);
     esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
   }
   *esum_out = esum;
-  // byte offset of the thread's current item in each input (row part + beta)
-  int rowb[M];
   const int n_iter = (items * tpi + G - 1) / G;
   const int tcount = 1 << (k - lg);
   float lmax = 0.f;
@@ -534,23 +506,10 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
   for (int j = 0; j < n_iter; ++j) {
     const int it = it0 + j * sit;
     const bool live = it < items;
-    if (j == 0 || !incr_rows) {
-      const uint32_t row = (uint32_t)it >> lb;
-      const uint32_t beta = (uint32_t)it & (Bco - 1u);
-      // with fixed batch entry the first row is below 2^r0 (later rows come
-      // from the tables); otherwise every row bit counts
-      const int nb = incr_rows ? min(w, r0) : w;
-#pragma unroll
-      for (int i = 0; i < M; ++i) {
-        int ri = 0;
-        for (int b = 0; b < nb; ++b)
-          if ((row >> b) & 1u) ri += vbit(S.in[i], b);
-        rowb[i] = soff[i] + (int)(((uint32_t)ri << bsh[i]) | (bsh[i] ? beta : 0u)) * 8;
-      }
-    } else {
+    if (j) {
       const int t = __ffs(j) - 1;
 #pragma unroll
-      for (int i = 0; i < M; ++i) rowb[i] += tab[i][t];
+      for (int i = 0; i < M; ++i) rowb[i] += S.in[i].rinc[t];
     }
     float2 acc = make_float2(0.f, 0.f);
     if (live) {
@@ -559,9 +518,9 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
       for (int i = 0; i < M; ++i) eb[i] = eb0[i];
       for (int jt = 0; jt < tcount; ++jt) {
         if (jt) {
-          const int t = 16 + __ffs(jt) - 1;
+          const int t = __ffs(jt) - 1;
 #pragma unroll
-          for (int i = 0; i < M; ++i) eb[i] += tab[i][t];
+          for (int i = 0; i < M; ++i) eb[i] += S.in[i].tinc[t];
         }
         float2 p = make_float2(1.f, 0.f);
 #pragma unroll
@@ -596,7 +555,6 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
                int final_batched, double c_re, double c_im, double2 *out, Header *hdr) {
   extern __shared__ __align__(16) char sm[];
   __shared__ RStep wsd[RES_WARPS];
-  __shared__ int32_t wtab[RES_WARPS][MAXIN][TAB_W];
   const int Bc = 1 << logBc;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int64_t b0 = (int64_t)blockIdx.x * Bc;
@@ -626,26 +584,26 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
     const int sched = __ldg(&steps[s].sched);
     const int w0 = sched & 15, nw = (sched >> 4) & 15, lg = (sched >> 8) & 15;
     if (wid >= w0 && wid < w0 + nw) {
-      // this warp's copy of the descriptor
+      // this warp's copy of the descriptor (header and the m inputs in use)
       const int *src = reinterpret_cast<const int *>(steps + s);
       int *dst = reinterpret_cast<int *>(&S);
-      for (int q = lane; q < RSTEP_WORDS; q += 32) dst[q] = __ldg(src + q);
+      const int words = __ldg(&steps[s].bytes) >> 2;
+      for (int q = lane; q < words; q += 32) dst[q] = __ldg(src + q);
       __syncwarp();
       const int lb = S.batched_out ? logBc : 0;
       const int items = (1 << S.w_out) << lb;
       const int gt = tid - 32 * w0, G = 32 * nw;
       float lmax;
       int esum = 0;
-      int32_t(*tab)[TAB_W] = wtab[wid];
-      switch (S.m) {
-        case 1: lmax = res_step<1>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
-        case 2: lmax = res_step<2>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
-        case 3: lmax = res_step<3>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
-        case 4: lmax = res_step<4>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
-        case 5: lmax = res_step<5>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
-        case 6: lmax = res_step<6>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
-        case 7: lmax = res_step<7>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
-        default: lmax = res_step<8>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, lane, tab, &esum); break;
+            switch (S.m) {
+        case 1: lmax = res_step<1>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 2: lmax = res_step<2>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 3: lmax = res_step<3>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 4: lmax = res_step<4>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 5: lmax = res_step<5>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 6: lmax = res_step<6>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        case 7: lmax = res_step<7>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
+        default: lmax = res_step<8>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
       }
       for (int q = 16; q > 0; q >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
       if (lane == 0) {

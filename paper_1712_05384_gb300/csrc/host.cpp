@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <cstddef>
 #include <numeric>
 
 #include "host.h"
@@ -732,7 +733,10 @@ static void build_resident(qgm_plan *p) {
         const int64_t terms = (int64_t)1 << d.k;
         int nw = (int)std::min<int64_t>(RES_WARPS, std::max<int64_t>(1, (items * terms + 511) / 512));
         int lg = 0;
-        while (lg < 5 && lg < d.k && (items << (lg + 1)) <= 32 * nw) ++lg;
+        const int Bco = d.batched_out ? Bc : 1;
+        // more lanes per entry while entries are few, keeping a thread's
+        // batch entry fixed (its item stride (32 nw) >> lg stays >= Bco)
+        while (lg < 5 && lg < d.k && (items << (lg + 1)) <= 32 * nw && ((32 * nw) >> (lg + 1)) >= Bco) ++lg;
         const int64_t per_thread = ((items << lg) + 32 * nw - 1) / (32 * nw);
         jobs.push_back({q, nw, lg, (double)per_thread * (double)(terms >> lg) * d.m + 40.0});
       }
@@ -774,17 +778,45 @@ static void build_resident(qgm_plan *p) {
           in.meta = it.leaf < 0 ? it.meta : -1;
           // the input's offset as allocated (before its release above)
           in.soff = -1;
-          // union bit -> input bit (union bit of variable a is U-1-a)
           const int U = (int)st.uni.size();
-          if (U > RMAXBITS || d.w_out > 16) {
+          if (U > 32 || d.w_out > 16) {
             ok = false;
             break;
           }
-          for (int b = 0; b < RMAXBITS; ++b) in.vpos[b] = 0xff;
+          // value (element offset) of union bit b in this input, or 0
+          std::vector<int64_t> v(U, 0);
           for (int qq = 0; qq < d.in[i].nruns; ++qq)
-            for (int l = 0; l < d.in[i].len[qq]; ++l)
-              in.vpos[d.in[i].src[qq] + l] = (uint8_t)(d.in[i].dst[qq] + l);
+            for (int l = 0; l < d.in[i].len[qq]; ++l) v[d.in[i].src[qq] + l] = (int64_t)1 << (d.in[i].dst[qq] + l);
+          const int bsh = it.batched ? (int)std::log2(Bc) : 0;
+          const int64_t unit = (int64_t)8 << bsh;
+          const int sched_lg = (w0_of[q - pos] >> 8) & 15, sched_nw = (w0_of[q - pos] >> 4) & 15;
+          const int Bco = d.batched_out ? Bc : 1;
+          const int sit = (32 * sched_nw) >> sched_lg;
+          int r0 = 0;
+          while ((1 << (r0 + 1)) <= sit / Bco) ++r0;
+          in.nlow = std::min(r0, d.w_out);
+          for (int t = 0; t < 16; ++t) {
+            int64_t val = 0;
+            if (t < d.w_out - r0) {
+              val = v[r0 + t];
+              for (int b = 0; b < t; ++b) val -= v[r0 + b];
+            }
+            in.rinc[t] = (int32_t)(val * unit);
+          }
+          for (int t = 0; t < 8; ++t) {
+            int64_t val = 0;
+            if (t < d.k - sched_lg) {
+              val = v[d.w_out + sched_lg + t];
+              for (int b = 0; b < t; ++b) val -= v[d.w_out + sched_lg + b];
+            }
+            in.tinc[t] = (int32_t)(val * unit);
+          }
+          for (int b = 0; b < 8; ++b) {
+            in.lrow[b] = b < in.nlow ? (int32_t)(v[b] * unit) : 0;
+            in.lterm[b] = b < sched_lg ? (int32_t)(v[d.w_out + b] * unit) : 0;
+          }
         }
+        r.bytes = (int32_t)(offsetof(RStep, in) + d.m * sizeof(RIn));
         L.steps.push_back(r);
       }
       pos = end;

@@ -85,18 +85,22 @@ struct LeafDesc {
 // Input index = pext(row, runs) | (pext(e, emask) << rowbits): the summed
 // variables are the top bits of the union index and, the input's variables
 // being sorted the same way, the top bits of the input index too.
-// Where each bit of the union index lands in one resident input's index:
-// vpos[b] for union bit b (row bits 0..w_out-1, then the k summed bits), or
-// 0xff when the input does not hold that variable.  Every input index is
-// linear in the union bits, which the kernel exploits to walk items and
-// terms by table-driven increments.
-constexpr int RMAXBITS = 24;
+// One input of a resident step with its address tables precomputed by the
+// planner (every input index is linear in the bits of the union index; all
+// entries are byte offsets in shared memory):
+//   lrow[b]  value of row bit b (b < r0), for a thread's first row;
+//   lterm[b] value of summed bit b (b < lg), for a thread's first term;
+//   rinc[t]  change when the thread's row counter carries into bit t;
+//   tinc[t]  change when its term counter carries into bit t.
 struct RIn {
   int32_t soff;      // smem byte offset of the tensor
   int32_t meta;      // smem metadata slot (intermediates), -1 for leaves
-  uint8_t batched;
-  uint8_t pad_[3];
-  uint8_t vpos[RMAXBITS];
+  int32_t batched;
+  int32_t nlow;      // entries of lrow in use (min(r0, w_out))
+  int32_t rinc[16];
+  int32_t tinc[8];
+  int32_t lrow[8];
+  int32_t lterm[8];
 };
 
 struct RStep {
@@ -105,7 +109,7 @@ struct RStep {
   // warps [w0, w0 + nw) run the step with 2^lg lanes per output entry;
   // bit 16: the last step of its dependency level (a block barrier follows)
   int32_t sched;
-  int32_t pad_;
+  int32_t bytes;     // bytes of this descriptor in use (header + m inputs)
   RIn in[MAXIN];
 };
 constexpr int RES_WARPS = 8;
