@@ -466,20 +466,36 @@ __device__ __forceinline__ uint32_t pext_small(uint32_t e, uint32_t mask) {
   return r;
 }
 
+// Product of the M inputs at one term; with PER_LOAD each value is scaled as
+// it is loaded, otherwise the caller applies one combined scale per entry.
+template <int M, bool PER_LOAD>
+__device__ __forceinline__ float2 res_term(const char *sm, const int *rowb, const int *eb,
+                                           const float *scale) {
+  float2 p = *reinterpret_cast<const float2 *>(sm + rowb[0] + eb[0]);
+  if (PER_LOAD) p = make_float2(p.x * scale[0], p.y * scale[0]);
+#pragma unroll
+  for (int i = 1; i < M; ++i) {
+    float2 v = *reinterpret_cast<const float2 *>(sm + rowb[i] + eb[i]);
+    if (PER_LOAD) v = make_float2(v.x * scale[i], v.y * scale[i]);
+    p = cmul(p, v);
+  }
+  return p;
+}
+
 // One elimination step run by a group of G threads (gt = index in the
 // group).  Each input index is linear in the bits of (row, e): a thread
 // starts from its first item and term and then only adds the planner's
 // table entries selected by the trailing zeros of its item and term counters.
-template <int M>
-__device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *meta, Header *hdr,
-                                          int logBc, int lb, int lg, int items, int gt, int G,
-                                          int *esum_out) {
+// When the inputs' scale exponents sum to a representable power of two the
+// raw product is scaled once per entry (no input's raw values can overflow:
+// each stored tensor is a sum of at most 2^8 products of values below 1).
+template <int M, bool PER_LOAD>
+__device__ __forceinline__ float res_step_body(const RStep &S, char *sm, const float *scale, float comb,
+                                               int lb, int lg, int items, int gt, int G) {
   const int k = S.k;
   const int tpi = 1 << lg;
   const int sit = G >> lg;                  // item stride of one thread (>= 2^lb)
-  float scale[M];
   int rowb[M], eb0[M];
-  int esum = 0;
   const int it0 = gt >> lg, g = gt & (tpi - 1);
   const uint32_t row0 = (uint32_t)it0 >> lb;
   const uint32_t beta = (uint32_t)it0 & ((1u << lb) - 1u);
@@ -494,11 +510,7 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
     for (int b = 0; b < lg; ++b)
       if ((g >> b) & 1) ei += in.lterm[b];
     eb0[i] = ei;
-    int e;
-    operand_scale(meta, in.meta, hdr, &scale[i], &e);
-    esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
   }
-  *esum_out = esum;
   const int n_iter = (items * tpi + G - 1) / G;
   const int tcount = 1 << (k - lg);
   float lmax = 0.f;
@@ -516,21 +528,35 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
       int eb[M];
 #pragma unroll
       for (int i = 0; i < M; ++i) eb[i] = eb0[i];
-      for (int jt = 0; jt < tcount; ++jt) {
-        if (jt) {
-          const int t = __ffs(jt) - 1;
+      if (tcount == 1) {
+        acc = res_term<M, PER_LOAD>(sm, rowb, eb, scale);
+      } else {
+        // two terms per iteration: counter values jt (even) and jt + 1
+        // differ in bit 0 only (increment tinc[0]); from jt + 1 to jt + 2
+        // the carry lands on bit ffs(jt + 2) - 1
+        float2 acc2 = make_float2(0.f, 0.f);
+        for (int jt = 0; jt < tcount; jt += 2) {
+          if (jt) {
+            const int t = __ffs(jt) - 1;
 #pragma unroll
-          for (int i = 0; i < M; ++i) eb[i] += S.in[i].tinc[t];
-        }
-        float2 p = make_float2(1.f, 0.f);
+            for (int i = 0; i < M; ++i) eb[i] += S.in[i].tinc[t];
+          }
+          int eb2[M];
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-          const float2 v = *reinterpret_cast<const float2 *>(sm + rowb[i] + eb[i]);
-          p = cmul(p, make_float2(v.x * scale[i], v.y * scale[i]));
+          for (int i = 0; i < M; ++i) eb2[i] = eb[i] + S.in[i].tinc[0];
+          const float2 p1 = res_term<M, PER_LOAD>(sm, rowb, eb, scale);
+          const float2 p2 = res_term<M, PER_LOAD>(sm, rowb, eb2, scale);
+          acc.x += p1.x;
+          acc.y += p1.y;
+          acc2.x += p2.x;
+          acc2.y += p2.y;
+          #pragma unroll
+          for (int i = 0; i < M; ++i) eb[i] = eb2[i];
         }
-        acc.x += p.x;
-        acc.y += p.y;
+        acc.x += acc2.x;
+        acc.y += acc2.y;
       }
+      if (!PER_LOAD) acc = make_float2(acc.x * comb, acc.y * comb);
     }
     // reduce the tpi partial sums of an item (aligned lane groups; tpi > 1
     // only when every lane runs exactly one iteration)
@@ -544,6 +570,29 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
     }
   }
   return lmax;
+}
+
+template <int M>
+__device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *meta, Header *hdr,
+                                          int logBc, int lb, int lg, int items, int gt, int G,
+                                          int *esum_out) {
+  (void)logBc;
+  float scale[M];
+  int esum = 0, es = 0;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const RIn &in = S.in[i];
+    int e;
+    operand_scale(meta, in.meta, hdr, &scale[i], &e);
+    es += e;
+    esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
+  }
+  *esum_out = esum;
+  if (es >= -120 && es <= 120) {
+    const float comb = __int_as_float((127 - es) << 23);
+    return res_step_body<M, false>(S, sm, scale, comb, lb, lg, items, gt, G);
+  }
+  return res_step_body<M, true>(S, sm, scale, 1.f, lb, lg, items, gt, G);
 }
 
 // The whole pass for one chunk of Bc bitstrings.  Steps come in dependency
