@@ -655,6 +655,38 @@ static bool make_runs(const std::vector<int> &uni, const std::vector<int> &opvar
   return true;
 }
 
+// Offline placement of tensors whose lifetimes [born, dies] (dependency
+// levels, inclusive) are known: largest first, each at the lowest 16-byte
+// aligned offset not used by an already placed tensor of overlapping
+// lifetime.  Returns the peak byte extent.
+static int64_t pack_lifetimes(const std::vector<int64_t> &size, const std::vector<int> &born,
+                              const std::vector<int> &dies, std::vector<int64_t> &off) {
+  const int n = (int)size.size();
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return size[a] > size[b]; });
+  off.assign(n, -1);
+  std::vector<int> placed;
+  int64_t peak = 0;
+  for (int t : idx) {
+    if (size[t] <= 0) continue;
+    const int64_t sz = (size[t] + 15) & ~int64_t(15);
+    std::vector<std::pair<int64_t, int64_t>> busy;  // [start, end) of conflicting tensors
+    for (int u : placed)
+      if (!(dies[u] < born[t] || dies[t] < born[u])) busy.push_back({off[u], off[u] + ((size[u] + 15) & ~int64_t(15))});
+    std::sort(busy.begin(), busy.end());
+    int64_t cand = 0;
+    for (auto &b : busy) {
+      if (b.first >= cand + sz) break;
+      cand = std::max(cand, b.second);
+    }
+    off[t] = cand;
+    peak = std::max(peak, cand + sz);
+    placed.push_back(t);
+  }
+  return peak;
+}
+
 // Shared-memory layouts of the resident executor for chunks of Bc batch
 // entries.  Steps are grouped into dependency levels (a step's level is one
 // more than the highest level among the steps producing its inputs); the
@@ -683,18 +715,25 @@ static void build_resident(qgm_plan *p) {
   std::iota(order.begin(), order.end(), 0);
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return level[a] < level[b]; });
   const int64_t meta_bytes = ((int64_t)p->n_meta * 8 + 15) & ~int64_t(15);
+  // lifetimes in levels: leaves from the start, outputs from their level,
+  // each until the level of its one consumer (the final tensor to the end)
+  std::vector<int> born(S.tensors.size(), -1), dies(S.tensors.size(), n_levels);
+  for (int si = 0; si < ns; ++si) {
+    born[S.steps[si].out] = level[si];
+    for (int id : S.steps[si].inputs) dies[id] = level[si];
+  }
   for (int Bc : {1, 2, 4, 8}) {
     ResidentLayout L;
     L.chunk = Bc;
-    Arena arena;
-    arena.al = 16;
-    std::vector<int64_t> soff(S.tensors.size(), -1);
     auto bytes_of = [&](const SymTensor &t) {
       return pow2((int)t.vars.size()) * (t.batched ? Bc : 1) * 8;
     };
+    std::vector<int64_t> tsize(S.tensors.size()), where;
+    for (size_t t = 0; t < S.tensors.size(); ++t) tsize[t] = bytes_of(S.tensors[t]);
+    const int64_t arena_peak = pack_lifetimes(tsize, born, dies, where);
+    std::vector<int64_t> soff = where;
     bool ok = true;
     for (int li = 0; li < nl; ++li) {
-      soff[li] = arena.alloc(bytes_of(S.tensors[li]));
       const bool bt = S.tensors[li].batched;
       L.leaves.push_back({li, (int32_t)(meta_bytes + soff[li]), bt ? 1 : 0, 0});
       const LeafDesc &d = p->leafdesc[li];
@@ -713,16 +752,6 @@ static void build_resident(qgm_plan *p) {
     for (int lv = 0, pos = 0; lv < n_levels && ok; ++lv) {
       int end = pos;
       while (end < ns && level[order[end]] == lv) ++end;
-      for (int q = pos; q < end; ++q) {
-        const StepRec &st = S.steps[order[q]];
-        soff[st.out] = arena.alloc(bytes_of(S.tensors[st.out]));
-      }
-      for (int q = pos; q < end; ++q)
-        for (int id : S.steps[order[q]].inputs)
-          if (soff[id] >= 0) {
-            arena.release(soff[id], bytes_of(S.tensors[id]));
-            soff[id] = -2;  // released (a tensor is consumed once)
-          }
       // warp groups: each step gets nw warps; longest steps first onto the
       // least-loaded contiguous warp range
       struct Job { int q, nw, lg; double cost; };
@@ -776,8 +805,7 @@ static void build_resident(qgm_plan *p) {
           RIn &in = r.in[i];
           in.batched = it.batched ? 1 : 0;
           in.meta = it.leaf < 0 ? it.meta : -1;
-          // the input's offset as allocated (before its release above)
-          in.soff = -1;
+          in.soff = (int32_t)(meta_bytes + where[id]);
           const int U = (int)st.uni.size();
           if (U > 32 || d.w_out > 16) {
             ok = false;
@@ -822,45 +850,11 @@ static void build_resident(qgm_plan *p) {
       pos = end;
     }
     if (!ok) break;  // an index map too fragmented for the resident kernel
-    L.final_soff = -1;
+    L.final_soff = (int)(meta_bytes + where[S.final_tensor]);
     L.final_meta = S.tensors[S.final_tensor].meta;
-    L.smem_bytes = meta_bytes + arena.peak;
+    L.smem_bytes = meta_bytes + arena_peak;
     if (L.smem_bytes > 200 * 1024) break;  // larger chunks only grow
     p->resident.push_back(L);
-  }
-  // input offsets: replay the allocation to recover every tensor's offset
-  for (ResidentLayout &L : p->resident) {
-    const int Bc = L.chunk;
-    Arena arena;
-    arena.al = 16;
-    std::vector<int64_t> soff(S.tensors.size(), -1);
-    auto bytes_of = [&](const SymTensor &t) {
-      return pow2((int)t.vars.size()) * (t.batched ? Bc : 1) * 8;
-    };
-    for (int li = 0; li < nl; ++li) soff[li] = arena.alloc(bytes_of(S.tensors[li]));
-    std::vector<int64_t> where = soff;
-    for (int lv = 0, pos = 0; lv < n_levels; ++lv) {
-      int end = pos;
-      while (end < ns && level[order[end]] == lv) ++end;
-      for (int q = pos; q < end; ++q) {
-        const StepRec &st = S.steps[order[q]];
-        soff[st.out] = arena.alloc(bytes_of(S.tensors[st.out]));
-        where[st.out] = soff[st.out];
-      }
-      for (int q = pos; q < end; ++q)
-        for (int id : S.steps[order[q]].inputs)
-          if (soff[id] >= 0) {
-            arena.release(soff[id], bytes_of(S.tensors[id]));
-            soff[id] = -2;
-          }
-      pos = end;
-    }
-    for (int q = 0; q < ns; ++q) {
-      const StepRec &st = S.steps[order[q]];
-      for (size_t i = 0; i < st.inputs.size(); ++i)
-        L.steps[q].in[i].soff = (int32_t)(meta_bytes + where[st.inputs[i]]);
-    }
-    L.final_soff = (int)(meta_bytes + where[S.final_tensor]);
   }
 }
 
