@@ -184,20 +184,24 @@ __device__ void build_tables(const StepDesc &d, int r0, int lt, int Bp, int64_t 
 // term group).  Rows are walked at stride gridDim.y (a power of two), terms
 // at stride blockDim.y (a power of two); addresses advance by table lookups.
 __global__ void __launch_bounds__(1024)
-    k_step_batched(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp) {
+    k_step_batched(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp, int logP) {
   __shared__ float4 part[1024];
   __shared__ int64_t rowtab[MAXIN][ROWTAB];
   __shared__ int64_t etab[MAXIN][ETAB];
   const int tx = threadIdx.x, ty = threadIdx.y, T = blockDim.y;
   const int tid = ty * STEP_THREADS + tx;
-  const int r0 = __ffs(gridDim.y) - 1, lt = __ffs(T) - 1;
+  // wide batch (logP < 0): a row spans gridDim.x blocks of pairs; narrow
+  // batch: a block covers 128 / 2^logP rows, 2^logP pair slots each
+  const int rpb_log = logP < 0 ? 0 : 7 - logP;
+  const uint64_t rstride = (uint64_t)gridDim.y << rpb_log;
+  const int r0 = __ffsll((long long)rstride) - 1, lt = __ffs(T) - 1;
   build_tables(d, r0, lt, Bp, rowtab, etab, tid, STEP_THREADS * T);
-  const int bp = (blockIdx.x * STEP_THREADS + tx) * 2;
+  const int bp = logP < 0 ? (blockIdx.x * STEP_THREADS + tx) * 2 : (tx & ((1 << logP) - 1)) * 2;
   const bool active = bp < Bp;
   float scale[MAXIN];
   int esum = 0;
   int64_t rowb[MAXIN], eb0[MAXIN];
-  const uint64_t j0 = blockIdx.y;
+  const uint64_t j0 = logP < 0 ? blockIdx.y : ((uint64_t)blockIdx.y << rpb_log) + (tx >> logP);
 #pragma unroll
   for (int i = 0; i < MAXIN; ++i) {
     scale[i] = 1.f;
@@ -225,7 +229,11 @@ __global__ void __launch_bounds__(1024)
   float lmax = 0.f;
   float2 *out = reinterpret_cast<float2 *>(ws + d.out_off);
   uint64_t it = 0;
-  for (uint64_t j = j0; j < rows; j += gridDim.y, ++it) {
+  // every thread of the block runs the same number of row iterations (the
+  // term-group reduction below synchronises the block)
+  const uint64_t jb0 = logP < 0 ? j0 : ((uint64_t)blockIdx.y << rpb_log);
+  for (uint64_t jb = jb0; jb < rows; jb += rstride, ++it) {
+    const uint64_t j = j0 + it * rstride;
     if (it) {
       const int t = __ffsll((long long)it) - 1;
 #pragma unroll
@@ -233,7 +241,8 @@ __global__ void __launch_bounds__(1024)
         if (i < d.m) rowb[i] += rowtab[i][t];
     }
     float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
-    if (active) {
+    const bool live = active && j < rows;
+    if (live) {
       int64_t eb[MAXIN];
 #pragma unroll
       for (int i = 0; i < MAXIN; ++i) eb[i] = eb0[i];
@@ -276,7 +285,7 @@ __global__ void __launch_bounds__(1024)
       }
       __syncthreads();
     }
-    if (active && ty == 0) {
+    if (live && ty == 0) {
       reinterpret_cast<float4 *>(out)[(j * (uint64_t)Bp + bp) >> 1] = make_float4(a0.x, a0.y, a1.x, a1.y);
       lmax = fmaxf(lmax, fmaxf(absmax2(a0), absmax2(a1)));
     }
@@ -724,15 +733,23 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, Meta *m
     return r;
   };
   if (d.batched_out) {
-    const int bx = (Bp / 2 + STEP_THREADS - 1) / STEP_THREADS;
+    const int pairs = Bp / 2;
+    int logP = -1;  // narrow batch: 2^logP pair slots per row, 128 / 2^logP rows per block
+    if (pairs <= 64) {
+      logP = 0;
+      while ((1 << logP) < pairs) ++logP;
+    }
+    const int bx = logP < 0 ? (pairs + STEP_THREADS - 1) / STEP_THREADS : 1;
+    const uint64_t rpb = logP < 0 ? 1 : (uint64_t)(STEP_THREADS >> logP);
+    const uint64_t row_blocks = (rows + rpb - 1) / rpb;
     const uint64_t cap = (uint64_t)std::max(1, sms * 16 / bx);
     // split the summed terms over threadIdx.y while the grid is small
     int T = 1;
     while (T < 8 && (T * 2) <= (1 << std::min(d.k, 4)) &&
-           rows * (uint64_t)bx * STEP_THREADS * T < (uint64_t)sms * 1024)
+           row_blocks * (uint64_t)bx * STEP_THREADS * T < (uint64_t)sms * 1024)
       T *= 2;
-    const uint64_t gy = pow2_floor(std::min<uint64_t>(rows, std::min<uint64_t>(cap, 32768)));
-    k_step_batched<<<dim3(bx, (unsigned)gy), dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, Bp);
+    const uint64_t gy = pow2_floor(std::min<uint64_t>(row_blocks, std::min<uint64_t>(cap, 32768)));
+    k_step_batched<<<dim3(bx, (unsigned)gy), dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, Bp, logP);
   } else {
     const uint64_t blocks = pow2_floor(std::max<uint64_t>(1, std::min<uint64_t>((rows + 255) / 256, (uint64_t)sms * 8)));
     k_step_plain<<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr);
