@@ -145,6 +145,8 @@ typedef struct {
   int32_t n_order;            /* QGM_ORDER_GIVEN: length of `order` */
   const int32_t *order;       /* QGM_ORDER_GIVEN: elimination order (var ids) */
   int32_t executor;           /* QGM_EXEC_* */
+  int32_t no_gemm;            /* 1: run GEMM-shaped steps with the product-sum
+                                 kernel instead of the tiled GEMM kernel */
   int32_t gradients;          /* 1: also lay out the adjoint elimination of
                                  qgm_amplitude_grad (more workspace) */
   int32_t resident_chunk;     /* bitstrings per CTA of the resident executor:
@@ -173,6 +175,8 @@ typedef struct {
   double bytes_per_slice;     /* algorithmic bytes (inputs read + output written) */
   double flops_per_slice;     /* algorithmic real flops of the products and sums */
   double max_step_bytes;      /* algorithmic bytes of the largest step */
+  int32_t n_gemm_steps;       /* steps run by the tiled GEMM kernel */
+  int32_t pad_;
 } qgm_plan_info;
 
 /* Elimination order, slicing, step list and memory layout (Sec. IV, App. A).

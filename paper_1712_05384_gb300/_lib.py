@@ -38,7 +38,8 @@ class qgm_plan_opts(C.Structure):
     _fields_ = [("order_kind", C.c_int32), ("output_mode", C.c_int32), ("batch", C.c_int64),
                 ("mem_budget_bytes", C.c_int64), ("max_fuse", C.c_int32), ("n_order", C.c_int32),
                 ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
-                ("gradients", C.c_int32), ("resident_chunk", C.c_int32)]
+                ("no_gemm", C.c_int32), ("gradients", C.c_int32),
+                ("resident_chunk", C.c_int32)]
 
 
 class qgm_plan_info(C.Structure):
@@ -47,7 +48,7 @@ class qgm_plan_info(C.Structure):
                 ("n_slices", C.c_int64), ("max_tensor_entries", C.c_int64),
                 ("workspace_bytes", C.c_int64), ("arena_bytes", C.c_int64),
                 ("bytes_per_slice", C.c_double), ("flops_per_slice", C.c_double),
-                ("max_step_bytes", C.c_double)]
+                ("max_step_bytes", C.c_double), ("n_gemm_steps", C.c_int32), ("pad_", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -210,7 +211,7 @@ class Model:
 class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
-                 resident_chunk=0, gradients=False):
+                 resident_chunk=0, gradients=False, gemm=True):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -221,6 +222,7 @@ class Plan:
         o.executor = executor
         o.resident_chunk = resident_chunk
         o.gradients = int(gradients)
+        o.no_gemm = 0 if gemm else 1
         self._order_buf = None
         if order is not None:
             self._order_buf = np.ascontiguousarray(order, dtype=np.int32)

@@ -363,6 +363,97 @@ __global__ void __launch_bounds__(256)
   record_max(lmax, meta, d.out_meta);
 }
 
+// ---------------------------------------------------------------------------
+// GEMM-shaped step: out[s, m, n] = sum_k A[s, m, k] B[s, n, k] for each
+// shared kept index s and batch entry (grid z and y), 64 x 64 output tiles
+// (grid x), K in chunks of 16 staged in shared memory, a 4 x 4 complex tile
+// per thread in registers.  Operand and output addresses come from the bit
+// positions of the m, n, k, s variables in each tensor's own index.
+constexpr int GT = 64, GK = 16;
+
+__device__ __forceinline__ int64_t lin_bits(uint64_t x, const uint8_t *pos, int nb) {
+  int64_t r = 0;
+  for (int b = 0; b < nb; ++b)
+    if ((x >> b) & 1) r += (int64_t)1 << pos[b];
+  return r;
+}
+
+__global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *meta, Header *hdr, int Bp) {
+  __shared__ float2 As[GK][GT];
+  __shared__ float2 Bs[GK][GT];
+  __shared__ int64_t oAm[GT], oBn[GT], oOm[GT], oOn[GT], oAk[GK], oBk[GK];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int lnt = g.nn - 6;
+  const uint64_t tm = (uint64_t)blockIdx.x >> lnt, tn = (uint64_t)blockIdx.x & ((1ull << lnt) - 1);
+  const int beta = blockIdx.y;
+  const uint64_t sidx = blockIdx.z;
+  const int64_t uA = g.a_bat ? (int64_t)Bp * 8 : 8, uB = g.b_bat ? (int64_t)Bp * 8 : 8,
+                uO = g.o_bat ? (int64_t)Bp * 8 : 8;
+  const int64_t baseA = g.a_off + lin_bits(sidx, g.sA, g.ns) * uA + (g.a_bat ? beta * 8 : 0);
+  const int64_t baseB = g.b_off + lin_bits(sidx, g.sB, g.ns) * uB + (g.b_bat ? beta * 8 : 0);
+  const int64_t baseO = g.o_off + lin_bits(sidx, g.sO, g.ns) * uO + (g.o_bat ? beta * 8 : 0);
+  if (tid < GT) {
+    oAm[tid] = lin_bits(tm * GT + tid, g.mA, g.nm) * uA;
+    oOm[tid] = lin_bits(tm * GT + tid, g.mO, g.nm) * uO;
+  } else if (tid < 2 * GT) {
+    const int j = tid - GT;
+    oBn[j] = lin_bits(tn * GT + j, g.nB, g.nn) * uB;
+    oOn[j] = lin_bits(tn * GT + j, g.nO, g.nn) * uO;
+  }
+  float sa, sb;
+  int ea, eb;
+  operand_scale(meta, g.a_meta, hdr, &sa, &ea);
+  operand_scale(meta, g.b_meta, hdr, &sb, &eb);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
+    meta[g.o_meta].exp = ea + eb + (g.a_meta >= 0 ? meta[g.a_meta].exp : 0) +
+                         (g.b_meta >= 0 ? meta[g.b_meta].exp : 0);
+  float2 acc[4][4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+  const int nkc = 1 << (g.nk - 4);
+  for (int kc = 0; kc < nkc; ++kc) {
+    __syncthreads();  // the previous chunk's tiles and tables are consumed
+    if (tid < GK) oAk[tid] = lin_bits((uint64_t)kc * GK + tid, g.kA, g.nk) * uA;
+    else if (tid < 2 * GK) oBk[tid - GK] = lin_bits((uint64_t)kc * GK + tid - GK, g.kB, g.nk) * uB;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q, i = e & (GT - 1), j = e >> 6;
+      const float2 va = __ldg(reinterpret_cast<const float2 *>(ws + baseA + oAm[i] + oAk[j]));
+      const float2 vb = __ldg(reinterpret_cast<const float2 *>(ws + baseB + oBn[i] + oBk[j]));
+      As[j][i] = make_float2(va.x * sa, va.y * sa);
+      Bs[j][i] = make_float2(vb.x * sb, vb.y * sb);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GK; ++kk) {
+      float2 a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+          acc[r][c].x = fmaf(a[r].x, b[c].x, fmaf(-a[r].y, b[c].y, acc[r][c].x));
+          acc[r][c].y = fmaf(a[r].x, b[c].y, fmaf(a[r].y, b[c].x, acc[r][c].y));
+        }
+    }
+  }
+  float lmax = 0.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      *reinterpret_cast<float2 *>(ws + baseO + oOm[ty * 4 + r] + oOn[tx * 4 + c]) = acc[r][c];
+      lmax = fmaxf(lmax, absmax2(acc[r][c]));
+    }
+  record_max(lmax, meta, g.o_meta);
+}
+
 // out[x] += F[x] * 2^exp * c in FP64 (one slice's partial amplitudes), then
 // advance the slice counter.
 __global__ void k_accumulate(const char *ws, int64_t final_off, int final_meta, int final_batched,
@@ -724,9 +815,15 @@ static void launch_leaves(qgm_plan *p, const uint64_t *d_bits, int64_t B, cudaSt
 
 // Grid of one product-sum step: row strides are powers of two so that the
 // kernels can walk rows by table increments.
-static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, Meta *meta, Header *hdr,
-                           cudaStream_t st) {
+static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const GemmDesc *gemms, Meta *meta,
+                           Header *hdr, cudaStream_t st) {
   const uint64_t rows = 1ull << d.w_out;
+  if (d.gemm >= 0 && gemms) {
+    const GemmDesc &g = gemms[d.gemm];
+    const unsigned tiles = 1u << ((g.nm - 6) + (g.nn - 6));
+    k_gemm<<<dim3(tiles, g.o_bat ? Bp : 1, 1u << g.ns), 256, 0, st>>>(ws, g, meta, hdr, Bp);
+    return;
+  }
   auto pow2_floor = [](uint64_t v) {
     uint64_t r = 1;
     while (r * 2 <= v) r *= 2;
@@ -758,7 +855,7 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, Meta *m
 
 static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st) {
   char *ws = p->exec->ws;
-  launch_step_ws(ws, p->exec->sms, p->Bp, d, reinterpret_cast<Meta *>(ws + p->off_meta),
+  launch_step_ws(ws, p->exec->sms, p->Bp, d, p->gemms.data(), reinterpret_cast<Meta *>(ws + p->off_meta),
                  reinterpret_cast<Header *>(ws + p->off_header), st);
 }
 
@@ -1141,7 +1238,7 @@ void static_slice(const qgm_plan *p, char *ws, int sms, const uint64_t *d_bits, 
   const int nl = (int)p->leafdesc.size();
   k_build_leaves<<<std::max(nl, 1), 256, 0, st>>>(ws, reinterpret_cast<const LeafDesc *>(ws + p->off_leafdesc),
                                                    nl, meta, p->n_meta, hdr, d_bits, B, p->Bp);
-  for (const StepDesc &d : p->steps) launch_step_ws(ws, sms, p->Bp, d, meta, hdr, st);
+  for (const StepDesc &d : p->steps) launch_step_ws(ws, sms, p->Bp, d, p->gemms.data(), meta, hdr, st);
   const int64_t blocks = std::min<int64_t>((B + 255) / 256, (int64_t)sms * 8);
   const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
   k_accumulate<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(

@@ -479,7 +479,7 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     place((int)T.size() - 1);
   }
   int n_meta = 0;
-  auto emit = [&](std::vector<int> inputs, int k) -> int {
+  auto emit = [&](std::vector<int> inputs, int k, bool gemm = false) -> int {
     // union of the inputs' variables, sorted by position
     std::vector<int> uni;
     bool batched = false;
@@ -516,8 +516,9 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     T.push_back(out);
     int oid = (int)T.size() - 1;
     s.out = oid;
+    s.gemm = gemm;
     if (want_steps) R.steps.push_back(s);
-    else R.steps.push_back(StepRec{{}, {}, k, oid, batched, s.bytes, s.flops});
+    else R.steps.push_back(StepRec{{}, {}, k, oid, batched, s.bytes, s.flops, gemm});
     return oid;
   };
   // more than MAXIN inputs: multiply the smallest ones together first
@@ -562,7 +563,50 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       ++k;
     }
     shrink(inputs);
-    int oid = emit(inputs, k);
+    // GEMM-shaped step: the two largest inputs hold every summed variable
+    // and every other input fits inside one of them (it is multiplied into
+    // that operand first, a product step with nothing summed)
+    bool gemm = false;
+    if (p->gemm_ok && k >= 4 && inputs.size() >= 2) {
+      std::vector<int> by = inputs;
+      std::stable_sort(by.begin(), by.end(), [&](int a, int b) { return T[a].vars.size() > T[b].vars.size(); });
+      const int A = by[0], Bt = by[1];
+      auto holds = [&](int id, int v) {
+        return std::find(T[id].vars.begin(), T[id].vars.end(), v) != T[id].vars.end();
+      };
+      bool ok = T[A].vars.size() >= 10 && T[Bt].vars.size() >= 10;
+      for (int a = 0; a < k && ok; ++a) ok = holds(A, uni[a]) && holds(Bt, uni[a]);
+      std::vector<int> toA = {A}, toB = {Bt};
+      for (size_t q = 2; q < by.size() && ok; ++q) {
+        bool inA = true, inB = true;
+        for (int v : T[by[q]].vars) {
+          inA = inA && holds(A, v);
+          inB = inB && holds(Bt, v);
+        }
+        if (T[by[q]].vars.size() > 8 || (!inA && !inB)) ok = false;
+        else if (inB && (!inA || T[Bt].entries < T[A].entries)) toB.push_back(by[q]);
+        else toA.push_back(by[q]);
+      }
+      int nm = 0, nn = 0;
+      for (size_t a = k; a < uni.size() && ok; ++a) {
+        const bool ha = holds(A, uni[a]), hb = holds(Bt, uni[a]);
+        if (!ha && !hb) ok = false;
+        nm += ha && !hb;
+        nn += hb && !ha;
+      }
+      if (ok && nm >= 6 && nn >= 6 && nm < GMAXB && nn < GMAXB) {
+        auto premul = [&](std::vector<int> &grp) {
+          if (grp.size() == 1) return grp[0];
+          int id = emit(grp, 0);
+          for (int v : T[id].vars) live[v]++;
+          return id;
+        };
+        const int a2 = premul(toA), b2 = premul(toB);
+        inputs = {a2, b2};
+        gemm = true;
+      }
+    }
+    int oid = emit(inputs, k, gemm);
     place(oid);
   }
   // final product over the remaining tensors (scalars per batch entry, or
@@ -883,6 +927,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     p->Bp = 1;
   }
   const int max_fuse = o.max_fuse > 0 ? std::min(o.max_fuse, 16) : 8;
+  p->gemm_ok = o.no_gemm == 0;
   const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)64 << 30;
 
   reduce_factors(m, p->leaves, p->constant, p->half_pow_total);
@@ -1139,9 +1184,60 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
 
   // step descriptors
   p->steps.clear();
+  p->gemms.clear();
   p->executor_pref = o.executor;
   for (const StepRec &s : S.steps) {
     StepDesc d{};
+    d.gemm = -1;
+    if (s.gemm) {
+      // operand and output bit positions of each kind of variable
+      const SymTensor &A = S.tensors[s.inputs[0]], &B = S.tensors[s.inputs[1]], &O = S.tensors[s.out];
+      auto bitpos = [](const SymTensor &t, int v) {
+        const int a = (int)(std::find(t.vars.begin(), t.vars.end(), v) - t.vars.begin());
+        return a < (int)t.vars.size() ? (int)t.vars.size() - 1 - a : -1;
+      };
+      std::vector<int> mv, nv, kv, sv;
+      for (size_t a = 0; a < s.uni.size(); ++a) {
+        const int v = s.uni[a];
+        const int pa = bitpos(A, v), pb = bitpos(B, v);
+        if ((int)a < s.k) kv.push_back(v);
+        else if (pa >= 0 && pb >= 0) sv.push_back(v);
+        else if (pa >= 0) mv.push_back(v);
+        else nv.push_back(v);
+      }
+      std::sort(mv.begin(), mv.end(), [&](int x, int y) { return bitpos(A, x) < bitpos(A, y); });
+      std::sort(nv.begin(), nv.end(), [&](int x, int y) { return bitpos(B, x) < bitpos(B, y); });
+      std::sort(kv.begin(), kv.end(), [&](int x, int y) { return bitpos(A, x) < bitpos(A, y); });
+      std::sort(sv.begin(), sv.end(), [&](int x, int y) { return bitpos(O, x) < bitpos(O, y); });
+      GemmDesc g{};
+      g.a_off = A.off;
+      g.b_off = B.off;
+      g.o_off = O.off;
+      g.a_meta = A.leaf < 0 ? A.meta : -1;
+      g.b_meta = B.leaf < 0 ? B.meta : -1;
+      g.o_meta = O.meta;
+      g.a_bat = A.batched;
+      g.b_bat = B.batched;
+      g.o_bat = O.batched;
+      g.nm = (int)mv.size();
+      g.nn = (int)nv.size();
+      g.nk = (int)kv.size();
+      g.ns = (int)sv.size();
+      if (g.nm >= GMAXB || g.nn >= GMAXB || g.nk >= GMAXB || g.ns >= GMAXB || g.ns > 16) {
+        set_error("internal: GEMM step too wide");
+        return QGM_ERR_ARG;
+      }
+      for (int b = 0; b < g.nm; ++b) { g.mA[b] = (uint8_t)bitpos(A, mv[b]); g.mO[b] = (uint8_t)bitpos(O, mv[b]); }
+      for (int b = 0; b < g.nn; ++b) { g.nB[b] = (uint8_t)bitpos(B, nv[b]); g.nO[b] = (uint8_t)bitpos(O, nv[b]); }
+      for (int b = 0; b < g.nk; ++b) { g.kA[b] = (uint8_t)bitpos(A, kv[b]); g.kB[b] = (uint8_t)bitpos(B, kv[b]); }
+      for (int b = 0; b < g.ns; ++b) {
+        g.sA[b] = (uint8_t)bitpos(A, sv[b]);
+        g.sB[b] = (uint8_t)bitpos(B, sv[b]);
+        g.sO[b] = (uint8_t)bitpos(O, sv[b]);
+      }
+      d.gemm = (int)p->gemms.size();
+      p->gemms.push_back(g);
+    }
     d.m = (int)s.inputs.size();
     d.k = s.k;
     const int U = (int)s.uni.size();
@@ -1206,6 +1302,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     p->gfwd = p->steps;
     for (size_t si = 0; si < S.steps.size(); ++si) {
       StepDesc &d = p->gfwd[si];
+      d.gemm = -1;
       d.out_off = fwd_off[S.steps[si].out];
       for (int i = 0; i < d.m; ++i) d.in[i].off = fwd_off[S.steps[si].inputs[i]];
     }
@@ -1241,6 +1338,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
         uni = summed;
         uni.insert(uni.end(), it.vars.begin(), it.vars.end());
         StepDesc d{};
+        d.gemm = -1;
         d.k = (int)summed.size();
         d.w_out = (int)it.vars.size();
         d.batched_out = 1;
@@ -1468,6 +1566,8 @@ int qgm_plan_get_info(const qgm_plan *p, qgm_plan_info *info) {
   info->bytes_per_slice = p->sim.bytes;
   info->flops_per_slice = p->sim.flops;
   info->max_step_bytes = p->sim.max_step_bytes;
+  info->n_gemm_steps = (int32_t)p->gemms.size();
+  info->pad_ = 0;
   return QGM_OK;
 }
 

@@ -66,8 +66,24 @@ struct StepDesc {
   int32_t batched_out;
   int64_t out_off;
   int32_t out_meta;
-  int32_t pad_;
+  int32_t gemm;         // index of the step's GemmDesc, or -1
   InDesc in[MAXIN];
+};
+
+// A GEMM-shaped step: out[s, m, n] = sum_k A[s, m, k] B[s, n, k] with s the
+// kept variables both operands hold, m (n) the kept variables only A (B)
+// holds and k the summed variables (both hold all of them).  Each operand
+// and the output are addressed through the bit positions of those
+// variables in their own index (no transposition); the batch axis, when
+// present, stays innermost.
+constexpr int GMAXB = 24;
+struct GemmDesc {
+  int64_t a_off, b_off, o_off;
+  int32_t a_meta, b_meta, o_meta;
+  int32_t a_bat, b_bat, o_bat;
+  int32_t nm, nn, nk, ns;
+  uint8_t mA[GMAXB], mO[GMAXB], nB[GMAXB], nO[GMAXB];
+  uint8_t kA[GMAXB], kB[GMAXB], sA[GMAXB], sB[GMAXB], sO[GMAXB];
 };
 
 // Leaf factor built on the device per slice: base table over
@@ -170,6 +186,7 @@ struct StepRec {
   int out = -1;
   bool batched = false;
   double bytes = 0, flops = 0;
+  bool gemm = false;        // two operands, run by the GEMM kernel
 };
 
 struct LeafFactor {          // merged factor after fixing the inputs
@@ -220,6 +237,7 @@ struct qgm_plan {
   qgm::SimResult sim;
   // device layout
   std::vector<qgm::StepDesc> steps;
+  std::vector<qgm::GemmDesc> gemms;
   std::vector<qgm::LeafDesc> leafdesc;
   std::vector<float> base_tables;  // interleaved complex64
   int n_meta = 0;
@@ -241,6 +259,7 @@ struct qgm_plan {
   std::vector<qgm::ResidentLayout> resident;
   int64_t off_rsteps = 0;   // workspace region for the chosen layout's steps
   int executor_pref = 0;    // qgm_plan_opts.executor
+  bool gemm_ok = true;      // GEMM-shaped steps run by the GEMM kernel
   qgm_exec_state *exec = nullptr;
 };
 

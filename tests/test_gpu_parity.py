@@ -240,3 +240,48 @@ def test_resident_chunks_agree(chunk):
     a = p.amplitudes_host(bits)
     rel, ab = errors(a, ref, c.n)
     assert rel < REL_TOL and ab < ABS_TOL
+
+
+@pytest.mark.parametrize("rows,cols,depth,B", [(4, 5, 30, 16), (4, 6, 34, 6)])
+def test_gemm_steps_vs_state_vector(rows, cols, depth, B):
+    # depths at which the plan has GEMM-shaped steps (two operands sharing
+    # every summed variable); the tiled GEMM kernel and the product-sum
+    # kernel must both agree with the state vector
+    q = Q()
+    c = qi.grid_circuit(rows, cols, depth, 0)
+    bits = qi.bitstrings(c.n, B, 0)
+    ref = sv.amplitudes(c, bits)
+    for gemm in (True, False):
+        p = q.Plan(q.Model(q.Circuit.grid(rows, cols, depth, 0)), order_kind=1, batch=B,
+                   executor=1, gemm=gemm)
+        assert (p.info.n_gemm_steps > 0) == gemm
+        a = p.bind().amplitudes_host(bits)
+        rel, ab = errors(a, ref, c.n)
+        assert rel < REL_TOL and ab < ABS_TOL, (gemm, rel, ab)
+
+
+def test_grid5x9_d40_two_plans_and_porter_thomas():
+    # 5x9 grid, depth 40: no oracle finishes it, so (1) the same amplitudes
+    # from an unsliced and a sliced plan, (2) depth 16 of the same grid
+    # against the oracle, (3) Porter-Thomas moments over 256 amplitudes
+    q = Q()
+    m = q.Model(q.Circuit.grid(5, 9, 40, 0))
+    bits = qi.bitstrings(45, 256, 0)
+    p1 = q.Plan(m, order_kind=1, batch=4)
+    assert p1.info.n_gemm_steps > 0
+    p1.bind()
+    a1 = p1.amplitudes_host(bits[:4])
+    p2 = q.Plan(m, order_kind=1, batch=4, mem_budget_bytes=p1.info.arena_bytes // 3)
+    assert p2.info.n_slices > 1
+    a2 = p2.bind().amplitudes_host(bits[:4])
+    del p2
+    assert np.max(np.abs(a1 - a2)) * 2 ** 22.5 < 1e-5
+    c16 = qi.grid_circuit(5, 9, 16, 0)
+    a16 = q.Plan(q.Model(q.Circuit.grid(5, 9, 16, 0)), batch=4).bind().amplitudes_host(bits[:4])
+    rel, ab = errors(a16, ve.amplitudes(c16, bits[:4]), 45)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+    A = np.concatenate([p1.amplitudes_host(bits[4 * k:4 * k + 4]) for k in range(64)])
+    Np = 2 ** 45 * np.abs(A) ** 2
+    se1, se2 = Np.std() / 16, (Np ** 2).std() / 16
+    assert abs(Np.mean() - 1) < 4 * se1
+    assert abs((Np ** 2).mean() - 2) < 4 * se2
