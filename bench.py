@@ -200,9 +200,11 @@ def main():
     if B == 0:
         raise SystemExit("the benchmark runs batch workloads")
     c_py = qi.grid_circuit(rows, cols, depth, 0, param=param)
-    # weak scaling: each rank takes its own batch of B bitstrings
+    # weak scaling: each rank takes its own batch of B bitstrings (a
+    # contiguous block of the job's B * world; no data-path collective)
+    from paper_1712_05384_gb300 import shard
     all_bits = qi.bitstrings(c_py.n, B * world, 0)
-    bits = all_bits[rank * B:(rank + 1) * B]
+    bits = shard.shard(all_bits, rank, world)
     plan = q.Plan(q.Model(q.Circuit.grid(rows, cols, depth, 0, param)), batch=B,
                   executor=args.executor).bind()
     info = plan.info

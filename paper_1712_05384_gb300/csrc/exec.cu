@@ -90,13 +90,18 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ float absmax2(float2 a) { return fmaxf(fabsf(a.x), fabsf(a.y)); }
+// Maximum that keeps NaN (fmaxf would drop it): a NaN entry must reach the
+// tensor's recorded maximum so that the consumer flags QGM_ERR_NONFINITE.
+// NaN's bit pattern also orders above every finite value and Inf as unsigned.
+__device__ __forceinline__ float fmax_nan(float a, float b) { return (a > b || a != a) ? a : b; }
+
+__device__ __forceinline__ float absmax2(float2 a) { return fmax_nan(fabsf(a.x), fabsf(a.y)); }
 
 // Block-wide max of non-negative floats, then one atomicMax on the slot
 // (non-negative IEEE floats order like their unsigned bit patterns).
 __device__ __forceinline__ void record_max(float v, Meta *meta, int slot) {
   __shared__ float red[32];
-  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  for (int o = 16; o > 0; o >>= 1) v = fmax_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
   const int t = threadIdx.y * blockDim.x + threadIdx.x;
   const int lane = t & 31, wid = t >> 5;
   if (lane == 0) red[wid] = v;
@@ -104,8 +109,8 @@ __device__ __forceinline__ void record_max(float v, Meta *meta, int slot) {
   if (wid == 0) {
     const int nw = (blockDim.x * blockDim.y + 31) >> 5;
     v = lane < nw ? red[lane] : 0.f;
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0 && v > 0.f) atomicMax(&meta[slot].maxbits, __float_as_uint(v));
+    for (int o = 16; o > 0; o >>= 1) v = fmax_nan(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0 && (v > 0.f || v != v)) atomicMax(&meta[slot].maxbits, __float_as_uint(v));
   }
 }
 
@@ -287,7 +292,7 @@ __global__ void __launch_bounds__(1024)
     }
     if (live && ty == 0) {
       reinterpret_cast<float4 *>(out)[(j * (uint64_t)Bp + bp) >> 1] = make_float4(a0.x, a0.y, a1.x, a1.y);
-      lmax = fmaxf(lmax, fmaxf(absmax2(a0), absmax2(a1)));
+      lmax = fmax_nan(lmax, fmax_nan(absmax2(a0), absmax2(a1)));
     }
   }
   record_max(lmax, meta, d.out_meta);
@@ -358,7 +363,7 @@ __global__ void __launch_bounds__(256)
       a.y += pr.y;
     }
     out[j] = a;
-    lmax = fmaxf(lmax, absmax2(a));
+    lmax = fmax_nan(lmax, absmax2(a));
   }
   record_max(lmax, meta, d.out_meta);
 }
@@ -449,7 +454,7 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       *reinterpret_cast<float2 *>(ws + baseO + oOm[ty * 4 + r] + oOn[tx * 4 + c]) = acc[r][c];
-      lmax = fmaxf(lmax, absmax2(acc[r][c]));
+      lmax = fmax_nan(lmax, absmax2(acc[r][c]));
     }
   record_max(lmax, meta, g.o_meta);
 }
@@ -461,6 +466,9 @@ __global__ void k_accumulate(const char *ws, int64_t final_off, int final_meta, 
                              Header *hdr, double c_re, double c_im) {
   const float2 *F = reinterpret_cast<const float2 *>(ws + final_off);
   const int e = final_meta >= 0 ? meta[final_meta].exp : 0;
+  if (final_meta >= 0 && blockIdx.x == 0 && threadIdx.x == 0 &&
+      ((meta[final_meta].maxbits >> 23) & 0xff) == 0xff)
+    atomicCAS(&hdr->status, 0, QGM_ERR_NONFINITE);
   const double s = ldexp(1.0, e);
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_out;
        x += (int64_t)gridDim.x * blockDim.x) {
@@ -666,7 +674,7 @@ __device__ __forceinline__ float res_step_body(const RStep &S, char *sm, const f
     }
     if (live && g == 0) {
       o[it] = acc;
-      lmax = fmaxf(lmax, absmax2(acc));
+      lmax = fmax_nan(lmax, absmax2(acc));
     }
   }
   return lmax;
@@ -696,22 +704,30 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
 }
 
 // The whole pass for one chunk of Bc bitstrings.  Steps come in dependency
-// levels; within a level each step runs on its own warp group with no block
-// barrier, and one __syncthreads closes the level.
+// levels; each warp walks its own list of (step, level) entries, runs the
+// steps assigned to it with no block barrier inside a level, and every warp
+// closes each level with the same __syncthreads.  The next entry's
+// descriptor is fetched into registers while the current step computes.
+constexpr int PREW = 6;  // descriptor words per lane held in registers
+
 __global__ void __launch_bounds__(RES_THREADS, 5)
-    k_resident(const char *ws, const RStep *steps, int n_steps, const RJob *jobs, int n_jobs,
-               const uint64_t *bits, int64_t B, int logBc, int n_meta, int final_soff, int final_meta,
-               int final_batched, double c_re, double c_im, double2 *out, Header *hdr) {
+    k_resident(const char *ws, const RStep *steps, const RJob *jobs, int n_jobs, const uint32_t *wlist_g,
+               int n_wl, const int32_t *wstart_g, int n_levels, int wlist_soff, const uint64_t *bits,
+               int64_t B, int logBc, int n_meta, int final_soff, int final_meta, int final_batched,
+               double c_re, double c_im, double2 *out, Header *hdr) {
   extern __shared__ __align__(16) char sm[];
   __shared__ RStep wsd[RES_WARPS];
   const int Bc = 1 << logBc;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   const int64_t b0 = (int64_t)blockIdx.x * Bc;
   Meta *meta = reinterpret_cast<Meta *>(sm);
+  uint32_t *wl = reinterpret_cast<uint32_t *>(sm + wlist_soff);
   for (int i = tid; i < n_meta; i += RES_THREADS) {
     meta[i].maxbits = 0;
     meta[i].exp = 0;
   }
+  for (int i = tid; i < n_wl; i += RES_THREADS) wl[i] = __ldg(wlist_g + i);
+  const int e0 = __ldg(wstart_g + wid), e1 = __ldg(wstart_g + wid + 1);
   // leaves of this chunk, one job per leaf row: batched rows take the base
   // entry selected by the output bits of x_beta, unbatched rows the entry
   const float2 *wsf = reinterpret_cast<const float2 *>(ws);
@@ -729,22 +745,40 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
   }
   __syncthreads();
   RStep &S = wsd[wid];
-  for (int s = 0; s < n_steps; ++s) {
-    const int sched = __ldg(&steps[s].sched);
-    const int w0 = sched & 15, nw = (sched >> 4) & 15, lg = (sched >> 8) & 15;
-    if (wid >= w0 && wid < w0 + nw) {
-      // this warp's copy of the descriptor (header and the m inputs in use)
-      const int *src = reinterpret_cast<const int *>(steps + s);
+  int pre[PREW];
+  auto prefetch = [&](uint32_t entry) {
+    const int *src = reinterpret_cast<const int *>(steps + (entry & 0xfffu));
+    const int words = (int)(entry >> 22);
+#pragma unroll
+    for (int r = 0; r < PREW; ++r) {
+      const int idx = lane + 32 * r;
+      pre[r] = idx < words ? __ldg(src + idx) : 0;
+    }
+  };
+  int e = e0;
+  if (e < e1) prefetch(wl[e]);
+  for (int L = 0; L < n_levels; ++L) {
+    while (e < e1 && (int)((wl[e] >> 12) & 0x3ffu) == L) {
+      const uint32_t entry = wl[e];
+      const int words = (int)(entry >> 22);
       int *dst = reinterpret_cast<int *>(&S);
-      const int words = __ldg(&steps[s].bytes) >> 2;
-      for (int q = lane; q < words; q += 32) dst[q] = __ldg(src + q);
+#pragma unroll
+      for (int r = 0; r < PREW; ++r) {
+        const int idx = lane + 32 * r;
+        if (idx < words) dst[idx] = pre[r];
+      }
+      const int *src = reinterpret_cast<const int *>(steps + (entry & 0xfffu));
+      for (int idx = lane + 32 * PREW; idx < words; idx += 32) dst[idx] = __ldg(src + idx);
       __syncwarp();
+      ++e;
+      if (e < e1) prefetch(wl[e]);
+      const int w0 = S.sched & 15, nw = (S.sched >> 4) & 15, lg = (S.sched >> 8) & 15;
       const int lb = S.batched_out ? logBc : 0;
       const int items = (1 << S.w_out) << lb;
       const int gt = tid - 32 * w0, G = 32 * nw;
       float lmax;
       int esum = 0;
-            switch (S.m) {
+      switch (S.m) {
         case 1: lmax = res_step<1>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
         case 2: lmax = res_step<2>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
         case 3: lmax = res_step<3>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
@@ -754,15 +788,16 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
         case 7: lmax = res_step<7>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
         default: lmax = res_step<8>(S, sm, meta, hdr, logBc, lb, lg, items, gt, G, &esum); break;
       }
-      for (int q = 16; q > 0; q >>= 1) lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
+      for (int q = 16; q > 0; q >>= 1) lmax = fmax_nan(lmax, __shfl_xor_sync(0xffffffffu, lmax, q));
       if (lane == 0) {
-        if (lmax > 0.f) atomicMax(&meta[S.out_meta].maxbits, __float_as_uint(lmax));
+        if (lmax > 0.f || lmax != lmax) atomicMax(&meta[S.out_meta].maxbits, __float_as_uint(lmax));
         if (wid == w0) meta[S.out_meta].exp = esum;
       }
       __syncwarp();
     }
-    if (sched & SCHED_LAST) __syncthreads();
+    __syncthreads();
   }
+  if (tid == 0 && ((meta[final_meta].maxbits >> 23) & 0xff) == 0xff) atomicCAS(&hdr->status, 0, QGM_ERR_NONFINITE);
   if (tid < Bc && b0 + tid < B) {
     const float2 v = reinterpret_cast<const float2 *>(sm + final_soff)[final_batched ? tid : 0];
     const double sc = ldexp(1.0, meta[final_meta].exp);
@@ -887,10 +922,14 @@ static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, doub
   const int64_t G = (B + L.chunk - 1) / L.chunk;
   const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
   const char *ws = x->ws;
+  const char *rs = ws + p->off_rsteps;
+  const RJob *jobs = reinterpret_cast<const RJob *>(rs + L.steps.size() * sizeof(RStep));
+  const uint32_t *wl = reinterpret_cast<const uint32_t *>(rs + L.steps.size() * sizeof(RStep) +
+                                                          L.jobs.size() * sizeof(RJob));
+  const int32_t *wst = reinterpret_cast<const int32_t *>(wl + L.wlist.size());
   k_resident<<<(unsigned)G, RES_THREADS, (size_t)L.smem_bytes, st>>>(
-      ws, reinterpret_cast<const RStep *>(ws + p->off_rsteps), (int)L.steps.size(),
-      reinterpret_cast<const RJob *>(ws + p->off_rsteps + L.steps.size() * sizeof(RStep)),
-      (int)L.jobs.size(), d_bits, B, logBc, p->n_meta_fwd, L.final_soff, L.final_meta, p->final_batched,
+      ws, reinterpret_cast<const RStep *>(rs), jobs, (int)L.jobs.size(), wl, (int)L.wlist.size(), wst,
+      L.n_levels, L.wlist_soff, d_bits, B, logBc, p->n_meta_fwd, L.final_soff, L.final_meta, p->final_batched,
       c.real(), c.imag(), d_out, reinterpret_cast<Header *>(x->ws + p->off_header));
 }
 
@@ -1019,9 +1058,13 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
       CK(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
       CK(cudaMemcpyAsync(x->ws + p->off_rsteps, L.steps.data(), L.steps.size() * sizeof(RStep),
                          cudaMemcpyHostToDevice, st));
+      char *rs = x->ws + p->off_rsteps;
+      const size_t jo = L.steps.size() * sizeof(RStep), wo = jo + L.jobs.size() * sizeof(RJob);
       if (!L.jobs.empty())
-        CK(cudaMemcpyAsync(x->ws + p->off_rsteps + L.steps.size() * sizeof(RStep), L.jobs.data(),
-                           L.jobs.size() * sizeof(RJob), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(rs + jo, L.jobs.data(), L.jobs.size() * sizeof(RJob), cudaMemcpyHostToDevice, st));
+      if (!L.wlist.empty())
+        CK(cudaMemcpyAsync(rs + wo, L.wlist.data(), L.wlist.size() * 4, cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(rs + wo + L.wlist.size() * 4, L.wstart, sizeof(L.wstart), cudaMemcpyHostToDevice, st));
       CK(cudaStreamSynchronize(st));
       x->kind = QGM_EXEC_RESIDENT;
     } else if (p->executor_pref == QGM_EXEC_RESIDENT) {

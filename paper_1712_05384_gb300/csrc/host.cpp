@@ -897,6 +897,35 @@ static void build_resident(qgm_plan *p) {
     L.final_soff = (int)(meta_bytes + where[S.final_tensor]);
     L.final_meta = S.tensors[S.final_tensor].meta;
     L.smem_bytes = meta_bytes + arena_peak;
+    // per-warp work lists, then move the arena behind them in shared memory
+    L.n_levels = n_levels;
+    {
+      std::vector<std::vector<uint32_t>> per(RES_WARPS);
+      for (size_t q = 0; q < L.steps.size(); ++q) {
+        const RStep &r = L.steps[q];
+        const int w0 = r.sched & 15, nw = (r.sched >> 4) & 15;
+        const uint32_t words = (uint32_t)(r.bytes / 4);
+        const uint32_t lvl = (uint32_t)level[order[q]];
+        if (q >= 4096 || lvl >= 1024 || words >= 1024) ok = false;
+        for (int w = w0; w < w0 + nw; ++w) per[w].push_back((uint32_t)q | (lvl << 12) | (words << 22));
+      }
+      L.wstart[0] = 0;
+      for (int w = 0; w < RES_WARPS; ++w) {
+        L.wlist.insert(L.wlist.end(), per[w].begin(), per[w].end());
+        L.wstart[w + 1] = (int32_t)L.wlist.size();
+      }
+      const int64_t shift = ((int64_t)L.wlist.size() * 4 + 15) & ~int64_t(15);
+      L.wlist_soff = (int)meta_bytes;
+      for (RStep &r : L.steps) {
+        r.out_soff += (int32_t)shift;
+        for (int i = 0; i < r.m; ++i) r.in[i].soff += (int32_t)shift;
+      }
+      for (RJob &j : L.jobs) j.dst += (int32_t)shift;
+      for (RLeaf &lf : L.leaves) lf.soff += (int32_t)shift;
+      L.final_soff += (int)shift;
+      L.smem_bytes += shift;
+    }
+    if (!ok) break;
     if (L.smem_bytes > 200 * 1024) break;  // larger chunks only grow
     p->resident.push_back(L);
   }
@@ -1173,7 +1202,8 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     for (size_t li = 0; li < p->leaves.size(); ++li)
       njobs += (int64_t)1 << (S.tensors[li].vars.size());
     p->off_rsteps = take((int64_t)(S.steps.size() + 1) * sizeof(RStep) +
-                         (int64_t)(p->leaves.size() + 1) * sizeof(RLeaf) + (njobs + 1) * sizeof(RJob));
+                         (int64_t)(p->leaves.size() + 1) * sizeof(RLeaf) + (njobs + 1) * sizeof(RJob) +
+                         ((int64_t)S.steps.size() * RES_WARPS + RES_WARPS + 8) * 4);
   }
   p->off_arena = take(0);
   for (SymTensor &t : S.tensors)

@@ -48,6 +48,7 @@ struct Model {
 constexpr int MAXIN = 8;    // tensors multiplied in one step
 constexpr int MAXRUN = 16;  // contiguous bit runs of an index map
 constexpr int MAXLEAFV = 4; // variables of a leaf factor (internal+slice+output)
+constexpr int RES_WARPS = 8; // warps of a resident CTA
 
 // Index map of one step input: the input's index is the union index with
 // the bits of absent variables squeezed out (a "pext" by contiguous runs).
@@ -128,7 +129,6 @@ struct RStep {
   int32_t bytes;     // bytes of this descriptor in use (header + m inputs)
   RIn in[MAXIN];
 };
-constexpr int RES_WARPS = 8;
 constexpr int SCHED_LAST = 1 << 16;
 
 struct RLeaf {        // leaf materialised in smem per chunk
@@ -149,12 +149,18 @@ struct RJob {
   uint8_t batched;
 };
 
+// Work list of the warps: entry = step | level << 12 | descriptor words << 22;
+// warp w owns entries [wstart[w], wstart[w + 1]), ordered by level.
 struct ResidentLayout {
   int chunk = 0;            // Bc
   int64_t smem_bytes = 0;   // dynamic shared memory per CTA
   std::vector<RStep> steps;
   std::vector<RLeaf> leaves;
   std::vector<RJob> jobs;
+  std::vector<uint32_t> wlist;
+  int32_t wstart[RES_WARPS + 1] = {0};
+  int n_levels = 0;
+  int wlist_soff = 0;       // smem byte offset of the work lists
   int final_soff = -1, final_meta = -1;
 };
 

@@ -285,3 +285,21 @@ def test_grid5x9_d40_two_plans_and_porter_thomas():
     se1, se2 = Np.std() / 16, (Np ** 2).std() / 16
     assert abs(Np.mean() - 1) < 4 * se1
     assert abs((Np ** 2).mean() - 2) < 4 * se2
+
+
+@pytest.mark.parametrize("executor", EXECS)
+def test_nonfinite_gate_sets_status(executor):
+    # failure detection without a GPU fault: a NaN gate angle makes NaN
+    # tables; the first tensor holding NaN is flagged through the status word
+    q = Q()
+    c = qi.grid_circuit(3, 3, 10, 1, param=True)
+    gates = list(c.gates)
+    g = gates[c.param_gates[0]]
+    gates[c.param_gates[0]] = qi.Gate(g.kind, g.cycle, g.q0, g.q1, float("nan"), g.phi)
+    p = q.Plan(q.Model(q.Circuit.from_gates(9, gates)), batch=8, executor=executor).bind()
+    d_bits = torch.from_numpy(qi.bitstrings(9, 8, 1).astype(np.int64)).cuda()
+    d_out = torch.empty(16, dtype=torch.float64, device="cuda")
+    p.amplitudes(d_bits, d_out)
+    torch.cuda.synchronize()
+    assert p.status() == -5          # QGM_ERR_NONFINITE, and cleared by the read
+    assert p.status() == 0
