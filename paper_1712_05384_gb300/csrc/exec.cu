@@ -706,9 +706,7 @@ __device__ __forceinline__ float res_step(const RStep &S, char *sm, const Meta *
 // The whole pass for one chunk of Bc bitstrings.  Steps come in dependency
 // levels; each warp walks its own list of (step, level) entries, runs the
 // steps assigned to it with no block barrier inside a level, and every warp
-// closes each level with the same __syncthreads.  The next entry's
-// descriptor is fetched into registers while the current step computes.
-constexpr int PREW = 6;  // descriptor words per lane held in registers
+// closes each level with the same __syncthreads.
 
 __global__ void __launch_bounds__(RES_THREADS, 5)
     k_resident(const char *ws, const RStep *steps, const RJob *jobs, int n_jobs, const uint32_t *wlist_g,
@@ -745,33 +743,16 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
   }
   __syncthreads();
   RStep &S = wsd[wid];
-  int pre[PREW];
-  auto prefetch = [&](uint32_t entry) {
-    const int *src = reinterpret_cast<const int *>(steps + (entry & 0xfffu));
-    const int words = (int)(entry >> 22);
-#pragma unroll
-    for (int r = 0; r < PREW; ++r) {
-      const int idx = lane + 32 * r;
-      pre[r] = idx < words ? __ldg(src + idx) : 0;
-    }
-  };
   int e = e0;
-  if (e < e1) prefetch(wl[e]);
   for (int L = 0; L < n_levels; ++L) {
     while (e < e1 && (int)((wl[e] >> 12) & 0x3ffu) == L) {
       const uint32_t entry = wl[e];
       const int words = (int)(entry >> 22);
       int *dst = reinterpret_cast<int *>(&S);
-#pragma unroll
-      for (int r = 0; r < PREW; ++r) {
-        const int idx = lane + 32 * r;
-        if (idx < words) dst[idx] = pre[r];
-      }
       const int *src = reinterpret_cast<const int *>(steps + (entry & 0xfffu));
-      for (int idx = lane + 32 * PREW; idx < words; idx += 32) dst[idx] = __ldg(src + idx);
+      for (int idx = lane; idx < words; idx += 32) dst[idx] = __ldg(src + idx);
       __syncwarp();
       ++e;
-      if (e < e1) prefetch(wl[e]);
       const int w0 = S.sched & 15, nw = (S.sched >> 4) & 15, lg = (S.sched >> 8) & 15;
       const int lb = S.batched_out ? logBc : 0;
       const int items = (1 << S.w_out) << lb;
