@@ -176,7 +176,7 @@ typedef struct {
   double flops_per_slice;     /* algorithmic real flops of the products and sums */
   double max_step_bytes;      /* algorithmic bytes of the largest step */
   int32_t n_gemm_steps;       /* steps run by the tiled GEMM kernel */
-  int32_t pad_;
+  int32_t n_tile_steps;       /* batched steps run with a register tile */
 } qgm_plan_info;
 
 /* Elimination order, slicing, step list and memory layout (Sec. IV, App. A).

@@ -298,6 +298,197 @@ __global__ void __launch_bounds__(1024)
   record_max(lmax, meta, d.out_meta);
 }
 
+// Product-sum step, batched output, with a register tile: the step's output
+// bits that the largest input does not hold (tile_pos, t <= 3 of them) are
+// enumerated inside a thread, so each loaded element of every input that
+// lacks those bits serves all 2^t outputs.  Rows are counted over the other
+// output bits ("outer" bits) and walked by table increments as in
+// k_step_batched; one thread = one pair of batch entries (no term split).
+__global__ void __launch_bounds__(STEP_THREADS)
+    k_step_tile(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp, int logP) {
+  __shared__ int64_t rowtab[MAXIN][ROWTAB];
+  __shared__ int64_t etab[MAXIN][ETAB];
+  __shared__ int64_t toff[MAXIN][8];
+  __shared__ int64_t outtab[ROWTAB];
+  __shared__ int64_t tout[8];
+  __shared__ int32_t tile_in[MAXIN];
+  __shared__ uint8_t obits[64];
+  const int tx = threadIdx.x;
+  const int t = d.tile_t, ncomb = 1 << t;
+  const int w_eff = d.w_out - t;
+  if (tx == 0) {
+    int c = 0;
+    for (int b = 0; b < d.w_out; ++b) {
+      bool tile = false;
+      for (int q = 0; q < t; ++q) tile |= d.tile_pos[q] == b;
+      if (!tile) obits[c++] = (uint8_t)b;
+    }
+  }
+  __syncthreads();
+  const int rpb_log = logP < 0 ? 0 : 7 - logP;
+  const uint64_t rstride = (uint64_t)gridDim.y << rpb_log;
+  const int r0 = __ffsll((long long)rstride) - 1;
+  // tables over the outer bits, the summed bits, and the tile combinations
+  for (int x = tx; x < MAXIN * (ROWTAB + ETAB + 8); x += STEP_THREADS) {
+    const int i = x / (ROWTAB + ETAB + 8), q = x - i * (ROWTAB + ETAB + 8);
+    if (i >= d.m) continue;
+    const InDesc &in = d.in[i];
+    const int64_t unit = in.batched ? (int64_t)Bp * 8 : 8;
+    int64_t v = 0;
+    if (q < ROWTAB) {
+      if (q < w_eff - r0) {
+        v = run_bit(in, obits[r0 + q]);
+        for (int b = 0; b < q; ++b) v -= run_bit(in, obits[r0 + b]);
+      }
+      rowtab[i][q] = v * unit;
+    } else if (q < ROWTAB + ETAB) {
+      const int tt = q - ROWTAB;
+      if (tt < d.k) {
+        v = run_bit(in, d.w_out + tt);
+        for (int b = 0; b < tt; ++b) v -= run_bit(in, d.w_out + b);
+      }
+      etab[i][tt] = v * unit;
+    } else {
+      const int c = q - ROWTAB - ETAB;
+      for (int b = 0; b < t; ++b)
+        if ((c >> b) & 1) v += run_bit(in, d.tile_pos[b]);
+      toff[i][c] = v * unit;
+    }
+  }
+  if (tx < ROWTAB) {
+    int64_t v = 0;
+    if (tx < w_eff - r0) {
+      v = (int64_t)1 << obits[r0 + tx];
+      for (int b = 0; b < tx; ++b) v -= (int64_t)1 << obits[r0 + b];
+    }
+    outtab[tx] = v * (int64_t)Bp * 8;
+  } else if (tx < ROWTAB + 8) {
+    const int c = tx - ROWTAB;
+    int64_t v = 0;
+    for (int b = 0; b < t; ++b)
+      if ((c >> b) & 1) v += (int64_t)1 << d.tile_pos[b];
+    tout[c] = v * (int64_t)Bp * 8;
+  } else if (tx < ROWTAB + 8 + MAXIN) {
+    const int i = tx - ROWTAB - 8;
+    int h = 0;
+    if (i < d.m)
+      for (int b = 0; b < t; ++b) h |= run_bit(d.in[i], d.tile_pos[b]) != 0;
+    tile_in[i] = h;
+  }
+  const int bp = logP < 0 ? (blockIdx.x * STEP_THREADS + tx) * 2 : (tx & ((1 << logP) - 1)) * 2;
+  const bool active = bp < Bp;
+  float scale[MAXIN];
+  int esum = 0;
+  int64_t rowb[MAXIN];
+  const uint64_t j0 = logP < 0 ? blockIdx.y : ((uint64_t)blockIdx.y << rpb_log) + (tx >> logP);
+  __syncthreads();
+  int64_t orow = 0;
+  for (int b = 0; b < r0 && b < w_eff; ++b)
+    if ((j0 >> b) & 1) orow += ((int64_t)1 << obits[b]) * (int64_t)Bp * 8;
+  orow += (int64_t)bp * 8;
+#pragma unroll
+  for (int i = 0; i < MAXIN; ++i) {
+    scale[i] = 1.f;
+    rowb[i] = 0;
+    if (i < d.m) {
+      const InDesc &in = d.in[i];
+      int e;
+      operand_scale(meta, in.meta, hdr, &scale[i], &e);
+      esum += e + (in.meta >= 0 ? meta[in.meta].exp : 0);
+      const int64_t unit = in.batched ? (int64_t)Bp * 8 : 8;
+      int64_t ri = 0;
+      for (int b = 0; b < r0 && b < w_eff; ++b)
+        if ((j0 >> b) & 1) ri += run_bit(in, obits[b]);
+      rowb[i] = in.off + ri * unit + (in.batched ? (int64_t)bp * 8 : 0);
+    }
+  }
+  if (blockIdx.x == 0 && blockIdx.y == 0 && tx == 0) meta[d.out_meta].exp = esum;
+  const uint64_t rows = 1ull << w_eff;
+  const int tcount = 1 << d.k;
+  float lmax = 0.f;
+  char *outb = ws + d.out_off;
+  uint64_t it = 0;
+  const uint64_t jb0 = logP < 0 ? j0 : ((uint64_t)blockIdx.y << rpb_log);
+  for (uint64_t jb = jb0; jb < rows; jb += rstride, ++it) {
+    const uint64_t j = j0 + it * rstride;
+    if (it) {
+      const int tb = __ffsll((long long)it) - 1;
+#pragma unroll
+      for (int i = 0; i < MAXIN; ++i)
+        if (i < d.m) rowb[i] += rowtab[i][tb];
+      orow += outtab[tb];
+    }
+    if (!active || j >= rows) continue;
+    float4 acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t eb[MAXIN];
+#pragma unroll
+    for (int i = 0; i < MAXIN; ++i) eb[i] = 0;
+    for (int jt = 0; jt < tcount; ++jt) {
+      if (jt) {
+        const int tb = __ffs(jt) - 1;
+#pragma unroll
+        for (int i = 0; i < MAXIN; ++i)
+          if (i < d.m) eb[i] += etab[i][tb];
+      }
+      // product of the inputs that hold no tile bit (shared by all outputs)
+      float2 s0 = make_float2(1.f, 0.f), s1 = s0;
+#pragma unroll
+      for (int i = 0; i < MAXIN; ++i) {
+        if (i < d.m && !tile_in[i]) {
+          const char *a = ws + rowb[i] + eb[i];
+          if (d.in[i].batched) {
+            const float4 v = __ldg(reinterpret_cast<const float4 *>(a));
+            s0 = cmul(s0, make_float2(v.x * scale[i], v.y * scale[i]));
+            s1 = cmul(s1, make_float2(v.z * scale[i], v.w * scale[i]));
+          } else {
+            const float2 v = __ldg(reinterpret_cast<const float2 *>(a));
+            const float2 sv = make_float2(v.x * scale[i], v.y * scale[i]);
+            s0 = cmul(s0, sv);
+            s1 = cmul(s1, sv);
+          }
+        }
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c < ncomb) {
+          float2 p0 = s0, p1 = s1;
+#pragma unroll
+          for (int i = 0; i < MAXIN; ++i) {
+            if (i < d.m && tile_in[i]) {
+              const char *a = ws + rowb[i] + eb[i] + toff[i][c];
+              if (d.in[i].batched) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(a));
+                p0 = cmul(p0, make_float2(v.x * scale[i], v.y * scale[i]));
+                p1 = cmul(p1, make_float2(v.z * scale[i], v.w * scale[i]));
+              } else {
+                const float2 v = __ldg(reinterpret_cast<const float2 *>(a));
+                const float2 sv = make_float2(v.x * scale[i], v.y * scale[i]);
+                p0 = cmul(p0, sv);
+                p1 = cmul(p1, sv);
+              }
+            }
+          }
+          acc[c].x += p0.x;
+          acc[c].y += p0.y;
+          acc[c].z += p1.x;
+          acc[c].w += p1.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c < ncomb) {
+        *reinterpret_cast<float4 *>(outb + orow + tout[c]) = acc[c];
+        lmax = fmax_nan(lmax, fmax_nan(fmax_nan(fabsf(acc[c].x), fabsf(acc[c].y)),
+                                       fmax_nan(fabsf(acc[c].z), fabsf(acc[c].w))));
+      }
+    }
+  }
+  record_max(lmax, meta, d.out_meta);
+}
+
 // Product-sum step without a batch axis: thread = output entry j, rows walked
 // at stride gridDim.x * blockDim.x (a power of two) with table increments.
 __global__ void __launch_bounds__(256)
@@ -861,6 +1052,14 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
     while (T < 8 && (T * 2) <= (1 << std::min(d.k, 4)) &&
            row_blocks * (uint64_t)bx * STEP_THREADS * T < (uint64_t)sms * 1024)
       T *= 2;
+    if (d.tile_t > 0) {
+      // rows are counted over the output bits outside the tile
+      const uint64_t orows = rows >> d.tile_t;
+      const uint64_t oblocks = (orows + rpb - 1) / rpb;
+      const uint64_t gy = pow2_floor(std::min<uint64_t>(oblocks, std::min<uint64_t>(cap, 32768)));
+      k_step_tile<<<dim3(bx, (unsigned)gy), STEP_THREADS, 0, st>>>(ws, d, meta, hdr, Bp, logP);
+      return;
+    }
     const uint64_t gy = pow2_floor(std::min<uint64_t>(row_blocks, std::min<uint64_t>(cap, 32768)));
     k_step_batched<<<dim3(bx, (unsigned)gy), dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, Bp, logP);
   } else {

@@ -1308,6 +1308,22 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
       }
       in.nruns = nr;
     }
+    // register tile for large batched steps whose output has bits the
+    // largest input lacks (those outputs reuse its loaded values)
+    d.tile_t = 0;
+    if (d.batched_out && d.gemm < 0) {
+      int big = 0;
+      for (int i = 1; i < d.m; ++i)
+        if (S.tensors[s.inputs[i]].entries > S.tensors[s.inputs[big]].entries) big = i;
+      const SymTensor &bt = S.tensors[s.inputs[big]];
+      if (bt.batched && bt.entries * 8 >= ((int64_t)1 << 22)) {
+        for (int b = 0; b < d.w_out && d.tile_t < 3; ++b) {
+          const int v = s.uni[U - 1 - b];
+          if (std::find(bt.vars.begin(), bt.vars.end(), v) == bt.vars.end()) d.tile_pos[d.tile_t++] = (uint8_t)b;
+        }
+        if (d.w_out - d.tile_t < 1) d.tile_t = 0;
+      }
+    }
     p->steps.push_back(d);
   }
   build_resident(p);
@@ -1333,6 +1349,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     for (size_t si = 0; si < S.steps.size(); ++si) {
       StepDesc &d = p->gfwd[si];
       d.gemm = -1;
+      d.tile_t = 0;
       d.out_off = fwd_off[S.steps[si].out];
       for (int i = 0; i < d.m; ++i) d.in[i].off = fwd_off[S.steps[si].inputs[i]];
     }
@@ -1369,6 +1386,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
         uni.insert(uni.end(), it.vars.begin(), it.vars.end());
         StepDesc d{};
         d.gemm = -1;
+        d.tile_t = 0;
         d.k = (int)summed.size();
         d.w_out = (int)it.vars.size();
         d.batched_out = 1;
@@ -1597,7 +1615,8 @@ int qgm_plan_get_info(const qgm_plan *p, qgm_plan_info *info) {
   info->flops_per_slice = p->sim.flops;
   info->max_step_bytes = p->sim.max_step_bytes;
   info->n_gemm_steps = (int32_t)p->gemms.size();
-  info->pad_ = 0;
+  info->n_tile_steps = 0;
+  for (const StepDesc &d : p->steps) info->n_tile_steps += d.tile_t > 0;
   return QGM_OK;
 }
 

@@ -68,6 +68,11 @@ struct StepDesc {
   int64_t out_off;
   int32_t out_meta;
   int32_t gemm;         // index of the step's GemmDesc, or -1
+  // register tile: output bits (union positions < w_out) that the largest
+  // input does not hold; a thread loads that input once per term and forms
+  // the 2^tile_t outputs that share it
+  int32_t tile_t;
+  uint8_t tile_pos[4];
   InDesc in[MAXIN];
 };
 

@@ -303,3 +303,17 @@ def test_nonfinite_gate_sets_status(executor):
     torch.cuda.synchronize()
     assert p.status() == -5          # QGM_ERR_NONFINITE, and cleared by the read
     assert p.status() == 0
+
+
+def test_register_tiled_steps_vs_state_vector():
+    # 4x5 grid, depth 24, 1024 bitstrings on the stepwise executor: several
+    # expanding steps run with a register tile; all amplitudes vs the state
+    # vector, and identical to the plain batched kernel's up to rounding
+    q = Q()
+    c = qi.grid_circuit(4, 5, 24, 0)
+    bits = qi.bitstrings(c.n, 1024, 0)
+    p = q.Plan(q.Model(q.Circuit.grid(4, 5, 24, 0)), batch=1024, executor=1)
+    assert p.info.n_tile_steps > 0
+    a = p.bind().amplitudes_host(bits)
+    rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
