@@ -191,6 +191,11 @@ int qgm_plan_get_slice_vars(const qgm_plan *p, int32_t *vars, int64_t cap, int64
  * variables of the output), k[s] (variables summed), n_in[s], batched[s]. */
 int qgm_plan_get_steps(const qgm_plan *p, int32_t *out_rank, int32_t *k, int32_t *n_in,
                        int32_t *batched, int64_t cap);
+/* Kernel that runs step s in the stepwise executor: 0 product-sum without a
+ * batch axis, 1 batched product-sum, 2 batched with a register tile, 3 tiled
+ * GEMM. */
+int qgm_plan_get_step_kernels(const qgm_plan *p, int32_t *kind, int64_t cap);
+
 /* Algorithmic cost of step s: bytes[s] (inputs read once + output written,
  * complex64) and flops[s] (real flops of the products and sums). */
 int qgm_plan_get_step_cost(const qgm_plan *p, double *bytes, double *flops, int64_t cap);

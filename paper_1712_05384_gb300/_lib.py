@@ -75,6 +75,7 @@ _SIGS = {
     "qgm_plan_get_order": [_P, _I32P, C.c_int64, _I64P],
     "qgm_plan_get_slice_vars": [_P, _I32P, C.c_int64, _I64P],
     "qgm_plan_get_steps": [_P, _I32P, _I32P, _I32P, _I32P, C.c_int64],
+    "qgm_plan_get_step_kernels": [_P, _I32P, C.c_int64],
     "qgm_plan_get_step_cost": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64],
     "qgm_plan_profile": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), _P],
     "qgm_plan_free": [_P],
@@ -256,6 +257,13 @@ class Plan:
         arrs = [np.zeros(max(n, 1), dtype=np.int32) for _ in range(4)]
         check(lib().qgm_plan_get_steps(self._h, *[a.ctypes.data_as(_I32P) for a in arrs], n))
         return {k: a[:n] for k, a in zip(("out_rank", "k", "n_in", "batched"), arrs)}
+
+    def step_kernels(self):
+        """Per step: 0 plain, 1 batched, 2 batched with register tile, 3 GEMM."""
+        n = self.info.n_steps
+        a = np.zeros(max(n, 1), dtype=np.int32)
+        check(lib().qgm_plan_get_step_kernels(self._h, a.ctypes.data_as(_I32P), n))
+        return a[:n]
 
     def step_costs(self):
         n = self.info.n_steps

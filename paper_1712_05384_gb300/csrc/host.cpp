@@ -1657,6 +1657,18 @@ int qgm_plan_get_steps(const qgm_plan *p, int32_t *out_rank, int32_t *k, int32_t
   return QGM_OK;
 }
 
+int qgm_plan_get_step_kernels(const qgm_plan *p, int32_t *kind, int64_t cap) {
+  if (!p || !kind) {
+    set_error("qgm_plan_get_step_kernels: null argument");
+    return QGM_ERR_ARG;
+  }
+  for (int64_t s = 0; s < std::min<int64_t>(cap, (int64_t)p->steps.size()); ++s) {
+    const StepDesc &d = p->steps[s];
+    kind[s] = d.gemm >= 0 ? 3 : (d.tile_t > 0 ? 2 : (d.batched_out ? 1 : 0));
+  }
+  return QGM_OK;
+}
+
 int qgm_plan_get_step_cost(const qgm_plan *p, double *bytes, double *flops, int64_t cap) {
   if (!p) {
     set_error("qgm_plan_get_step_cost: null argument");
