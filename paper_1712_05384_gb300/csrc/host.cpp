@@ -1322,6 +1322,16 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
           if (std::find(bt.vars.begin(), bt.vars.end(), v) == bt.vars.end()) d.tile_pos[d.tile_t++] = (uint8_t)b;
         }
         if (d.w_out - d.tile_t < 1) d.tile_t = 0;
+        // inputs holding tile bits are reloaded for every tile entry: only
+        // worth it when they are small next to the largest input
+        for (int i = 0; i < d.m && d.tile_t > 0; ++i) {
+          if (i == big) continue;
+          const SymTensor &it = S.tensors[s.inputs[i]];
+          bool holds = false;
+          for (int q = 0; q < d.tile_t; ++q)
+            holds |= std::find(it.vars.begin(), it.vars.end(), s.uni[U - 1 - d.tile_pos[q]]) != it.vars.end();
+          if (holds && it.entries * 8 > bt.entries) d.tile_t = 0;
+        }
       }
     }
     p->steps.push_back(d);
