@@ -257,6 +257,25 @@ int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int6
 int qgm_amplitudes_static(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
                           void *stream);
 
+/* Cross-entropy benchmarking statistics (App. B) of B amplitudes a_b (device
+ * double[2B], e.g. qgm_amplitudes' output): with p = |a|^2 and N = 2^n,
+ * cross_entropy = -(1/B) sum log p (Eq. cee), alpha = (H0 - S)/(H0 - H) with
+ * the Porter-Thomas H0 = log N + gamma, H = log N - 1 + gamma (Eq. ae),
+ * mean_Np and second_moment = mean (N p)^2.  Sums are FP64 on the device
+ * (d_scratch: caller-owned device double[4]); synchronises `stream`. */
+typedef struct {
+  double cross_entropy, alpha, mean_Np, second_moment;
+} qgm_xeb_result;
+int qgm_xeb_stats(const double *d_amps, int64_t B, int n_qubits, double *d_scratch,
+                  qgm_xeb_result *out, void *stream);
+
+/* Sampling from a computed set (App. C): m indices into the t amplitudes of
+ * d_amps (device double[2t]) drawn with probability p_j / sum p, by inverse
+ * transform of u_i = (SplitMix64(seed) draw i) >> 11 * 2^-53.  d_scratch:
+ * caller-owned device double[t] (cumulative sums); d_idx: device int64[m]. */
+int qgm_sample_from_set(const double *d_amps, int64_t t, int64_t m, uint64_t seed, double *d_scratch,
+                        int64_t *d_idx, void *stream);
+
 /* Reads and clears the device status word of the bound workspace
  * (synchronises `stream`): QGM_OK, QGM_ERR_NONFINITE or QGM_ERR_TIMEOUT. */
 int qgm_status(qgm_plan *p, void *stream);

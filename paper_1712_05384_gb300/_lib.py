@@ -42,6 +42,11 @@ class qgm_plan_opts(C.Structure):
                 ("resident_chunk", C.c_int32)]
 
 
+class qgm_xeb_result(C.Structure):
+    _fields_ = [("cross_entropy", C.c_double), ("alpha", C.c_double), ("mean_Np", C.c_double),
+                ("second_moment", C.c_double)]
+
+
 class qgm_plan_info(C.Structure):
     _fields_ = [("order_kind", C.c_int32), ("n_free", C.c_int32), ("max_clique", C.c_int32),
                 ("n_steps", C.c_int32), ("n_slice_vars", C.c_int32), ("batch_padded", C.c_int32),
@@ -87,6 +92,8 @@ _SIGS = {
     "qgm_plan_get_executor": [_P, _I32P, _I32P, _I64P],
     "qgm_amplitudes_static": [_P, _P, C.c_int64, _P, _P],
     "qgm_amplitude_grad": [_P, _P, C.c_int64, _P, _P, _P, _P],
+    "qgm_xeb_stats": [_P, C.c_int64, C.c_int, _P, C.POINTER(qgm_xeb_result), _P],
+    "qgm_sample_from_set": [_P, C.c_int64, C.c_int64, C.c_uint64, _P, _P, _P],
     "qgm_last_error": [],
 }
 _VOID = {"qgm_circuit_free", "qgm_model_free", "qgm_plan_free"}
@@ -328,3 +335,18 @@ class Plan:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.qgm_plan_free(self._h)
             self._h = None
+
+
+# ---------------------------------------------------------------- App. B, C
+def xeb_stats(d_amps, B, n_qubits, d_scratch, stream=None):
+    """Cross-entropy statistics of B device amplitudes (see qgm_xeb_stats)."""
+    r = qgm_xeb_result()
+    check(lib().qgm_xeb_stats(_ptr(d_amps), B, n_qubits, _ptr(d_scratch), C.byref(r), _stream(stream)))
+    return {k: getattr(r, k) for k, _ in r._fields_}
+
+
+def sample_from_set(d_amps, t, m, seed, d_scratch, d_idx, stream=None):
+    """m indices drawn from the t amplitudes with p/sum p (see qgm_sample_from_set)."""
+    check(lib().qgm_sample_from_set(_ptr(d_amps), t, m, seed, _ptr(d_scratch), _ptr(d_idx),
+                                    _stream(stream)))
+    return d_idx

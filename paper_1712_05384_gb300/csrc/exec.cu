@@ -737,6 +737,78 @@ __global__ void k_grad_reduce(const char *ws, const GradParam *gp, const uint64_
   }
 }
 
+// ---------------------------------------------------------------------------
+// Cross-entropy statistics (App. B): FP64 sums of log p, N p and (N p)^2 over
+// the amplitudes, one block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_xeb(const double2 *a, int64_t B, double N, double *sums) {
+  __shared__ double r0[1024], r1[1024], r2[1024];
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (int64_t b = threadIdx.x; b < B; b += blockDim.x) {
+    const double p = a[b].x * a[b].x + a[b].y * a[b].y;
+    s0 += log(p);
+    s1 += N * p;
+    s2 += (N * p) * (N * p);
+  }
+  r0[threadIdx.x] = s0;
+  r1[threadIdx.x] = s1;
+  r2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) {
+      r0[threadIdx.x] += r0[threadIdx.x + h];
+      r1[threadIdx.x] += r1[threadIdx.x + h];
+      r2[threadIdx.x] += r2[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    sums[0] = r0[0];
+    sums[1] = r1[0];
+    sums[2] = r2[0];
+  }
+}
+
+// Cumulative sums of p_j = |a_j|^2 (one block: each thread sums a contiguous
+// chunk, a block scan of the chunk totals, then each chunk is written out).
+__global__ void __launch_bounds__(1024) k_cumsum_p(const double2 *a, int64_t t, double *cdf) {
+  __shared__ double part[1024];
+  const int64_t chunk = (t + blockDim.x - 1) / blockDim.x;
+  const int64_t lo = threadIdx.x * chunk, hi = lo + chunk < t ? lo + chunk : t;
+  double s = 0;
+  for (int64_t j = lo; j < hi; ++j) s += a[j].x * a[j].x + a[j].y * a[j].y;
+  part[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int i = 1; i < (int)blockDim.x; ++i) part[i] += part[i - 1];
+  __syncthreads();
+  double run = threadIdx.x ? part[threadIdx.x - 1] : 0.0;
+  for (int64_t j = lo; j < hi; ++j) {
+    run += a[j].x * a[j].x + a[j].y * a[j].y;
+    cdf[j] = run;
+  }
+}
+
+// Draw i: u = the i-th output of SplitMix64(seed) (counter form: the state
+// after i + 1 golden-ratio increments, then the two mixing rounds), top 53
+// bits; index = first j with cdf[j] / total > u.
+__global__ void k_sample(const double *cdf, int64_t t, int64_t m, uint64_t seed, int64_t *idx) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)(i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    const double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    const double total = cdf[t - 1];
+    int64_t lo = 0, hi = t - 1;
+    while (lo < hi) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (cdf[mid] / total > u) hi = mid;
+      else lo = mid + 1;
+    }
+    idx[i] = lo;
+  }
+}
+
 // Zero the FP64 result and the status, restart at slice 0.
 __global__ void k_init(double2 *out, int64_t n_out, Header *hdr) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_out;
@@ -1356,6 +1428,43 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
   CK(cudaEventSynchronize(ev[n]));
   for (int i = 0; i < n; ++i) CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
   for (auto &e : ev) cudaEventDestroy(e);
+  return QGM_OK;
+}
+
+int qgm_xeb_stats(const double *d_amps, int64_t B, int n_qubits, double *d_scratch, qgm_xeb_result *out,
+                  void *stream) {
+  if (!d_amps || !d_scratch || !out || B < 1 || n_qubits < 1 || n_qubits > 64) {
+    set_error("qgm_xeb_stats: bad arguments");
+    return QGM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double N = std::ldexp(1.0, n_qubits);
+  k_xeb<<<1, 1024, 0, st>>>(reinterpret_cast<const double2 *>(d_amps), B, N, d_scratch);
+  CK(cudaGetLastError());
+  double h[3];
+  CK(cudaMemcpyAsync(h, d_scratch, sizeof h, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double gamma = 0.5772156649015329, logN = n_qubits * std::log(2.0);
+  const double S = -h[0] / (double)B;
+  out->cross_entropy = S;
+  out->alpha = ((logN + gamma) - S) / ((logN + gamma) - (logN - 1 + gamma));
+  out->mean_Np = h[1] / (double)B;
+  out->second_moment = h[2] / (double)B;
+  return QGM_OK;
+}
+
+int qgm_sample_from_set(const double *d_amps, int64_t t, int64_t m, uint64_t seed, double *d_scratch,
+                        int64_t *d_idx, void *stream) {
+  if (!d_amps || !d_scratch || !d_idx || t < 1 || m < 0) {
+    set_error("qgm_sample_from_set: bad arguments");
+    return QGM_ERR_ARG;
+  }
+  if (m == 0) return QGM_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  k_cumsum_p<<<1, 1024, 0, st>>>(reinterpret_cast<const double2 *>(d_amps), t, d_scratch);
+  const int64_t blocks = std::min<int64_t>((m + 255) / 256, 4096);
+  k_sample<<<(unsigned)blocks, 256, 0, st>>>(d_scratch, t, m, seed, d_idx);
+  CK(cudaGetLastError());
   return QGM_OK;
 }
 
