@@ -149,6 +149,9 @@ typedef struct {
                                  kernel instead of the tiled GEMM kernel */
   int32_t gradients;          /* 1: also lay out the adjoint elimination of
                                  qgm_amplitude_grad (more workspace) */
+  uint64_t open_mask;         /* QGM_OUT_BATCH: qubits whose outputs stay open
+                                 (Eq. psi_x without their deltas): each bitstring
+                                 then yields 2^popcount(open_mask) amplitudes */
   int32_t resident_chunk;     /* bitstrings per CTA of the resident executor:
                                  1, 2, 4 or 8; 0 = chosen at bind (fewest
                                  waves x chunk on the bound device) */
@@ -212,7 +215,9 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
 
 /* Amplitudes of B <= opts.batch bitstrings (Sec. III-IV; App. A):
  * d_bitstrings: device uint64[B]; d_out: device double[2B] (re, im) written
- * with <x_b|C|0^n> for b < B.  Runs every step of the plan, all slices, on
+ * with <x_b|C|0^n> for b < B.  With k = popcount(opts.open_mask) > 0, d_out
+ * holds B * 2^k amplitudes: entry b * 2^k + c is x_b with its open qubits
+ * set from c (bit i of c = the i-th lowest open qubit).  Runs every step of the plan, all slices, on
  * `stream` (asynchronous; the first call with a given pointer set also
  * builds a CUDA graph).  Requires QGM_OUT_BATCH and a bound workspace.
  * Errors: QGM_ERR_ARG (mode, B, unbound), QGM_ERR_CUDA. */

@@ -38,7 +38,7 @@ class qgm_plan_opts(C.Structure):
     _fields_ = [("order_kind", C.c_int32), ("output_mode", C.c_int32), ("batch", C.c_int64),
                 ("mem_budget_bytes", C.c_int64), ("max_fuse", C.c_int32), ("n_order", C.c_int32),
                 ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
-                ("no_gemm", C.c_int32), ("gradients", C.c_int32),
+                ("no_gemm", C.c_int32), ("gradients", C.c_int32), ("open_mask", C.c_uint64),
                 ("resident_chunk", C.c_int32)]
 
 
@@ -219,7 +219,7 @@ class Model:
 class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
-                 resident_chunk=0, gradients=False, gemm=True):
+                 resident_chunk=0, gradients=False, gemm=True, open_mask=0):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -231,6 +231,9 @@ class Plan:
         o.resident_chunk = resident_chunk
         o.gradients = int(gradients)
         o.no_gemm = 0 if gemm else 1
+        o.open_mask = open_mask
+        # amplitudes per bitstring: its open qubits run over all 2^k values
+        self.n_open = bin(open_mask).count("1") if output_mode == OUT_BATCH else 0
         self._order_buf = None
         if order is not None:
             self._order_buf = np.ascontiguousarray(order, dtype=np.int32)
@@ -299,11 +302,13 @@ class Plan:
         return d_out
 
     def amplitudes_host(self, bits: np.ndarray, stream=None) -> np.ndarray:
+        """Amplitudes of host bitstrings: shape (B,), or (B, 2^k) with k open qubits."""
         bits = np.ascontiguousarray(bits, dtype=np.uint64)
-        out = np.zeros(2 * len(bits), dtype=np.float64)
+        out = np.zeros(2 * (len(bits) << self.n_open), dtype=np.float64)
         check(lib().qgm_amplitudes_host(self._h, bits.ctypes.data, len(bits), out.ctypes.data,
                                         _stream(stream)))
-        return out[0::2] + 1j * out[1::2]
+        a = out[0::2] + 1j * out[1::2]
+        return a.reshape(len(bits), 1 << self.n_open) if self.n_open else a
 
     def eliminate(self, d_out, stream=None):
         check(lib().qgm_eliminate(self._h, _ptr(d_out), _stream(stream)))

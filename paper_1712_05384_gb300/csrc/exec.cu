@@ -654,7 +654,7 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
 // advance the slice counter.
 __global__ void k_accumulate(const char *ws, int64_t final_off, int final_meta, int final_batched,
                              int open_mode, int64_t n_out, double2 *out, const Meta *meta,
-                             Header *hdr, double c_re, double c_im) {
+                             Header *hdr, double c_re, double c_im, int rows_log, int Bp) {
   const float2 *F = reinterpret_cast<const float2 *>(ws + final_off);
   const int e = final_meta >= 0 ? meta[final_meta].exp : 0;
   if (final_meta >= 0 && blockIdx.x == 0 && threadIdx.x == 0 &&
@@ -665,8 +665,12 @@ __global__ void k_accumulate(const char *ws, int64_t final_off, int final_meta, 
        x += (int64_t)gridDim.x * blockDim.x) {
     // open outputs: x is the row of the final tensor; a batch: x is the
     // batch entry of its single row (a final tensor without a batch axis is
-    // the same for every entry)
-    const int64_t src = open_mode ? x : (final_batched ? x : 0);
+    // the same for every entry); a batch with open outputs: x = b * 2^k + row
+    int64_t src;
+    if (open_mode == 1) src = x;
+    else if (open_mode == 2)
+      src = final_batched ? (x & ((1ll << rows_log) - 1)) * Bp + (x >> rows_log) : (x & ((1ll << rows_log) - 1));
+    else src = final_batched ? x : 0;
     const float2 v = F[src];
     const double re = (double)v.x * s, im = (double)v.y * s;
     double2 o = out[x];
@@ -1152,9 +1156,10 @@ static void launch_accumulate(qgm_plan *p, double2 *d_out, int64_t n_out, cudaSt
   // the fixed-gate tables had 2^{-1/2} pulled out half_pow_total times
   const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
   k_accumulate<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(
-      ws, p->final_off, p->final_meta, p->final_batched, p->output_mode == QGM_OUT_OPEN ? 1 : 0,
-      n_out, d_out, reinterpret_cast<const Meta *>(ws + p->off_meta),
-      reinterpret_cast<Header *>(ws + p->off_header), c.real(), c.imag());
+      ws, p->final_off, p->final_meta, p->final_batched,
+      p->output_mode == QGM_OUT_OPEN ? 1 : (p->open_in_batch ? 2 : 0), n_out, d_out,
+      reinterpret_cast<const Meta *>(ws + p->off_meta), reinterpret_cast<Header *>(ws + p->off_header), c.real(),
+      c.imag(), p->open_in_batch, p->Bp);
 }
 
 // Enqueue one slice: leaves, steps, accumulation.
@@ -1350,7 +1355,8 @@ int qgm_amplitudes(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double 
     set_error("qgm_amplitudes: need 1 <= B <= %lld and non-null buffers", (long long)p->batch);
     return QGM_ERR_ARG;
   }
-  return run(p, d_bitstrings, B, reinterpret_cast<double2 *>(d_out), B, static_cast<cudaStream_t>(stream));
+  return run(p, d_bitstrings, B, reinterpret_cast<double2 *>(d_out), B << p->open_in_batch,
+             static_cast<cudaStream_t>(stream));
 }
 
 int qgm_amplitudes_host(qgm_plan *p, const uint64_t *h_bitstrings, int64_t B, double *h_out,
@@ -1366,9 +1372,9 @@ int qgm_amplitudes_host(qgm_plan *p, const uint64_t *h_bitstrings, int64_t B, do
   uint64_t *d_bits = reinterpret_cast<uint64_t *>(p->exec->ws + p->off_bits);
   double2 *d_out = reinterpret_cast<double2 *>(p->exec->ws + p->off_outstage);
   CK(cudaMemcpyAsync(d_bits, h_bitstrings, B * sizeof(uint64_t), cudaMemcpyHostToDevice, st));
-  rc = run(p, d_bits, B, d_out, B, st);
+  rc = run(p, d_bits, B, d_out, B << p->open_in_batch, st);
   if (rc) return rc;
-  CK(cudaMemcpyAsync(h_out, d_out, B * sizeof(double2), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(h_out, d_out, (B << p->open_in_batch) * sizeof(double2), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   return QGM_OK;
 }
@@ -1414,7 +1420,7 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
   std::vector<cudaEvent_t> ev(n + 1);
   for (auto &e : ev) CK(cudaEventCreate(&e));
   Header *hdr = reinterpret_cast<Header *>(p->exec->ws + p->off_header);
-  k_init<<<1, 256, 0, st>>>(reinterpret_cast<double2 *>(d_out), B, hdr);
+  k_init<<<1, 256, 0, st>>>(reinterpret_cast<double2 *>(d_out), B << p->open_in_batch, hdr);
   CK(cudaEventRecord(ev[0], st));
   launch_leaves(p, d_bitstrings, B, st);
   CK(cudaEventRecord(ev[1], st));
@@ -1422,7 +1428,7 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
     launch_step(p, p->steps[s], st);
     CK(cudaEventRecord(ev[2 + s], st));
   }
-  launch_accumulate(p, reinterpret_cast<double2 *>(d_out), B, st);
+  launch_accumulate(p, reinterpret_cast<double2 *>(d_out), B << p->open_in_batch, st);
   CK(cudaEventRecord(ev[n], st));
   CK(cudaGetLastError());
   CK(cudaEventSynchronize(ev[n]));
@@ -1503,7 +1509,7 @@ int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, con
   for (const StepDesc &d : p->gfwd) launch_step(p, d, st);
   const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
   k_accumulate<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(
-      ws, p->g_final_off, p->g_final_meta, 1, 0, B, amp, meta, hdr, c.real(), c.imag());
+      ws, p->g_final_off, p->g_final_meta, 1, 0, B, amp, meta, hdr, c.real(), c.imag(), 0, p->Bp);
   k_seed<<<(p->Bp + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2 *>(ws + p->g_seed_off), p->Bp, meta,
                                                p->g_seed_meta);
   for (const StepDesc &d : p->gbwd) launch_step(p, d, st);
@@ -1574,7 +1580,8 @@ void static_slice(const qgm_plan *p, char *ws, int sms, const uint64_t *d_bits, 
   const int64_t blocks = std::min<int64_t>((B + 255) / 256, (int64_t)sms * 8);
   const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
   k_accumulate<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(
-      ws, p->final_off, p->final_meta, p->final_batched, 0, B, d_out, meta, hdr, c.real(), c.imag());
+      ws, p->final_off, p->final_meta, p->final_batched, p->open_in_batch ? 2 : 0, B << p->open_in_batch, d_out,
+      meta, hdr, c.real(), c.imag(), p->open_in_batch, p->Bp);
 }
 
 }  // namespace
@@ -1613,7 +1620,7 @@ extern "C" int qgm_amplitudes_static(qgm_plan *p, const uint64_t *d_bitstrings, 
   Header *hdr = reinterpret_cast<Header *>(ws + p->off_header);
   double2 *out = reinterpret_cast<double2 *>(d_out);
   const int64_t iblocks = std::min<int64_t>((B + 255) / 256, (int64_t)sms * 4);
-  k_init<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(out, B, hdr);
+  k_init<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(out, B << p->open_in_batch, hdr);
   const int64_t nslices = (int64_t)1 << p->slice_vars.size();
   for (int64_t s = 0; s < nslices; ++s) static_slice(p, ws, sms, d_bitstrings, B, out, st);
   CK(cudaGetLastError());

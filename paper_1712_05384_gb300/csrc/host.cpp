@@ -740,7 +740,7 @@ static int64_t pack_lifetimes(const std::vector<int64_t> &size, const std::vecto
 // before any of its inputs are released).
 static void build_resident(qgm_plan *p) {
   p->resident.clear();
-  if (p->output_mode != QGM_OUT_BATCH || !p->slice_vars.empty()) return;
+  if (p->output_mode != QGM_OUT_BATCH || !p->slice_vars.empty() || p->open_in_batch) return;
   const SimResult &S = p->sim;
   const int nl = (int)p->leaves.size();
   const int ns = (int)S.steps.size();
@@ -963,11 +963,18 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   p->var_role.assign(m.n_vars, 0);
   for (int v : m.inputs) p->var_role[v] = 1;
   p->open_vars.clear();
+  if (o.output_mode == QGM_OUT_BATCH && m.n < 64 && (o.open_mask >> m.n) != 0) {
+    set_error("qgm_plan_order: open_mask names qubits beyond n = %d", m.n);
+    return QGM_ERR_ARG;
+  }
+  p->open_in_batch = 0;
   for (int q = m.n - 1; q >= 0; --q) {
     int v = m.outputs[q];
     if (p->var_role[v] == 1) continue;  // qubit without gates: output = input
-    if (o.output_mode == QGM_OUT_BATCH) p->var_role[v] = 2;
+    const bool open_here = o.output_mode == QGM_OUT_BATCH && ((o.open_mask >> q) & 1);
+    if (o.output_mode == QGM_OUT_BATCH && !open_here) p->var_role[v] = 2;
     else {
+      p->open_in_batch += open_here;
       p->var_role[v] = 3;
       p->open_vars.push_back(v);
     }
@@ -1093,7 +1100,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   p->n_meta = n_meta;
   p->n_meta_fwd = n_meta;
   p->grad = o.gradients != 0;
-  if (p->grad && (o.output_mode != QGM_OUT_BATCH || !p->slice_vars.empty())) {
+  if (p->grad && (o.output_mode != QGM_OUT_BATCH || !p->slice_vars.empty() || p->open_in_batch)) {
     set_error("qgm_plan_order: gradients need a batch plan without slices");
     return QGM_ERR_ARG;
   }
@@ -1194,7 +1201,11 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   const SymTensor &F = S.tensors[S.final_tensor];
   p->final_entries = pow2((int)F.vars.size());
   p->final_batched = F.batched ? 1 : 0;
-  int64_t out_elems = o.output_mode == QGM_OUT_BATCH ? Bp : p->final_entries;
+  if (p->open_in_batch > 20) {
+    set_error("qgm_plan_order: at most 20 open outputs in a batch plan");
+    return QGM_ERR_ARG;
+  }
+  int64_t out_elems = o.output_mode == QGM_OUT_BATCH ? (Bp << p->open_in_batch) : p->final_entries;
   p->off_outstage = take(out_elems * 16);
   p->off_acc = take(out_elems * 16);
   {

@@ -255,6 +255,7 @@ struct qgm_plan {
   int64_t off_header = 0, off_meta = 0, off_leafdesc = 0, off_base = 0, off_leaf = 0, off_bits = 0,
           off_outstage = 0, off_acc = 0, off_arena = 0, ws_bytes = 0;
   int64_t final_entries = 0;     // rows of the final tensor (2^n_open or 1)
+  int open_in_batch = 0;         // open output qubits of a batch plan (k)
   int final_batched = 0;
   int64_t final_off = 0;
   int final_meta = -1;

@@ -131,3 +131,22 @@ def test_steps_are_consistent():
     assert (st["n_in"] >= 1).all() and (st["n_in"] <= 8).all()
     assert (st["k"] >= 0).all() and st["k"].sum() == p.info.n_free
     assert st["out_rank"][-1] == 0 and st["batched"][-1] == 1
+
+
+def test_partially_open_outputs_plan():
+    # Eq. psi_x with the deltas of k chosen outputs omitted: those variables
+    # are never eliminated and the final tensor keeps them (k axes) beside
+    # the batch axis
+    m = Q.Model(Q.Circuit.grid(4, 4, 12, 0))
+    closed = Q.Plan(m, batch=8)
+    mask = (1 << 1) | (1 << 6) | (1 << 13)
+    p = Q.Plan(m, batch=8, open_mask=mask)
+    assert p.n_open == 3
+    st = p.steps()
+    # output variables are fixed by the bitstring or open: neither is eliminated
+    assert st["k"].sum() == p.info.n_free == closed.info.n_free
+    assert st["out_rank"][-1] == 3 and st["batched"][-1] == 1
+    with pytest.raises(Q.QgmError):
+        Q.Plan(m, batch=8, open_mask=1 << 16)          # no qubit 16 on a 4x4 grid
+    with pytest.raises(Q.QgmError):
+        Q.Plan(m, batch=8, open_mask=mask, gradients=True)
