@@ -34,7 +34,7 @@ L2_BYTES = 129 * 2 ** 20
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
 # the sha1 of the kernel source it was taken on (null once the source changed).
-NCU_TRAFFIC = {"aa1d23d69959": 312576.0}   # k_resident, profiles/k_resident_grid5x5_d20_b1024.md
+NCU_TRAFFIC = {}
 
 
 def parse():
@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid5x5_d20_b1024", choices=sorted(qi.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--executor", type=int, default=0, help="0 auto, 1 stepwise, 2 resident")
+    ap.add_argument("--executor", type=int, default=0, help="0 auto, 1 stepwise, 2 resident, 3 compiled resident")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
 
@@ -69,8 +69,9 @@ def peaks():
 
 def kernel_hash():
     h = hashlib.sha1()
-    with open(os.path.join(ROOT, "paper_1712_05384_gb300", "csrc", "exec.cu"), "rb") as f:
-        h.update(f.read())
+    for name in ("exec.cu", "jit.cpp"):
+        with open(os.path.join(ROOT, "paper_1712_05384_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:12]
 
 
@@ -276,7 +277,7 @@ def main():
         ms += plan.profile(d_bits, d_out, B=B, stream=stream)
     ms /= reps
     traffic = NCU_TRAFFIC.get(kernel_hash())
-    if ex_kind == q.EXEC_RESIDENT:
+    if ex_kind in (q.EXEC_RESIDENT, q.EXEC_COMPILED):
         # all intermediates live in shared memory: bound by the SM's FP32/ALU
         # issue, peak = 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
         k_ms = float(ms[0])
@@ -284,8 +285,8 @@ def main():
         achieved = float(step_flops.sum()) / (k_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": f"k_resident (whole pass, {ex_chunk} bitstring(s) per CTA, "
-                          f"{ex_smem} B shared memory)",
+                "kernel": f"{'qgm_resident_plan (compiled for this plan)' if ex_kind == q.EXEC_COMPILED else 'k_resident'}"
+                          f" (whole pass, {ex_chunk} bitstring(s) per CTA, {ex_smem} B shared memory)",
                 "algorithmic_flops_per_pass": float(step_flops.sum()),
                 "algorithmic_bytes_per_pass": float(step_bytes.sum()),
                 "kernel_ms_per_pass": k_ms,
@@ -311,7 +312,7 @@ def main():
                    "batch_per_gpu": B, "seed": 0, "order": info.order_kind,
                    "max_clique": info.max_clique, "steps_per_pass": info.n_steps,
                    "slices": info.n_slices, "parallelism": f"replicas{world}",
-                   "executor": {1: "stepwise", 2: "resident"}.get(ex_kind), "chunk": ex_chunk,
+                   "executor": {1: "stepwise", 2: "resident", 3: "compiled resident"}.get(ex_kind), "chunk": ex_chunk,
                    "l2": "flushed between timed steps (264 MB write, untimed)"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * B,
                 "d2h_bytes_per_step": 16 * B},

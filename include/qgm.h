@@ -149,6 +149,10 @@ typedef struct {
                                  kernel instead of the tiled GEMM kernel */
   int32_t gradients;          /* 1: also lay out the adjoint elimination of
                                  qgm_amplitude_grad (more workspace) */
+  int32_t trees;              /* 1: buckets of three or more inputs may run as
+                                 contraction trees (pairs multiplied first, each
+                                 variable summed once no other factor holds it)
+                                 when that needs clearly fewer products */
   uint64_t open_mask;         /* QGM_OUT_BATCH: qubits whose outputs stay open
                                  (Eq. psi_x without their deltas): each bitstring
                                  then yields 2^popcount(open_mask) amplitudes */
@@ -158,10 +162,15 @@ typedef struct {
 } qgm_plan_opts;
 
 enum {
-  QGM_EXEC_AUTO = 0,      /* resident when a chunk's live set fits in shared memory */
+  QGM_EXEC_AUTO = 0,      /* compiled resident, else resident, when a chunk's live
+                             set fits in shared memory; else stepwise */
   QGM_EXEC_STEPWISE = 1,  /* one kernel per step over the whole batch (CUDA graph) */
-  QGM_EXEC_RESIDENT = 2   /* one persistent launch: each CTA runs all steps for a
-                             chunk of bitstrings out of shared memory */
+  QGM_EXEC_RESIDENT = 2,  /* one persistent launch: each CTA runs all steps for a
+                             chunk of bitstrings out of shared memory, reading a
+                             descriptor per step */
+  QGM_EXEC_COMPILED = 3   /* the resident launch with a kernel generated for this
+                             plan and compiled at bind time (NVRTC): offsets,
+                             index maps and the warp schedule are constants */
 };
 
 typedef struct {
@@ -240,8 +249,9 @@ int qgm_eliminate(qgm_plan *p, double *d_out, void *stream);
 int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
                      float *ms, void *stream);
 
-/* Executor chosen at bind time: *kind (QGM_EXEC_STEPWISE or _RESIDENT), the
- * bitstrings per CTA *chunk and the dynamic shared memory per CTA (resident). */
+/* Executor chosen at bind time: *kind (QGM_EXEC_STEPWISE, _RESIDENT or
+ * _COMPILED), the bitstrings per CTA *chunk and the dynamic shared memory per
+ * CTA (resident and compiled). */
 int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int64_t *smem_bytes);
 
 /* No counterpart in the paper: an allocation-free variant of qgm_amplitudes

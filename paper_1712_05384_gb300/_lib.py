@@ -21,7 +21,7 @@ ERRORS = {-1: "QGM_ERR_ARG", -2: "QGM_ERR_OOM", -3: "QGM_ERR_CUDA", -4: "QGM_ERR
 
 ORDER_AUTO, ORDER_MINFILL, ORDER_VERTICAL, ORDER_VERTICAL_T, ORDER_GIVEN = range(5)
 OUT_BATCH, OUT_OPEN = 0, 1
-EXEC_AUTO, EXEC_STEPWISE, EXEC_RESIDENT = 0, 1, 2
+EXEC_AUTO, EXEC_STEPWISE, EXEC_RESIDENT, EXEC_COMPILED = 0, 1, 2, 3
 
 
 class qgm_gate(C.Structure):
@@ -38,7 +38,8 @@ class qgm_plan_opts(C.Structure):
     _fields_ = [("order_kind", C.c_int32), ("output_mode", C.c_int32), ("batch", C.c_int64),
                 ("mem_budget_bytes", C.c_int64), ("max_fuse", C.c_int32), ("n_order", C.c_int32),
                 ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
-                ("no_gemm", C.c_int32), ("gradients", C.c_int32), ("open_mask", C.c_uint64),
+                ("no_gemm", C.c_int32), ("gradients", C.c_int32), ("trees", C.c_int32),
+                ("open_mask", C.c_uint64),
                 ("resident_chunk", C.c_int32)]
 
 
@@ -219,7 +220,7 @@ class Model:
 class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
-                 resident_chunk=0, gradients=False, gemm=True, open_mask=0):
+                 resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=False):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -232,6 +233,7 @@ class Plan:
         o.gradients = int(gradients)
         o.no_gemm = 0 if gemm else 1
         o.open_mask = open_mask
+        o.trees = int(trees)
         # amplitudes per bitstring: its open qubits run over all 2^k values
         self.n_open = bin(open_mask).count("1") if output_mode == OUT_BATCH else 0
         self._order_buf = None

@@ -7,7 +7,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libqgm.so")
-SOURCES = ["host.cpp", "exec.cu"]
+SOURCES = ["host.cpp", "jit.cpp", "exec.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 
@@ -28,7 +28,7 @@ def build(verbose: bool = False, force: bool = False) -> str:
     tmp = LIB + ".tmp"
     cmd = [nvcc(), "-O3", "-std=c++17", ARCH, "-lineinfo", "-shared", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include"), "-I", CSRC,
-           "--threads", "2", "-o", tmp] + srcs
+           "--threads", "3", "-o", tmp] + srcs + ["-ldl"]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -28,6 +28,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "host.h"
@@ -1056,6 +1057,11 @@ __global__ void __launch_bounds__(RES_THREADS, 5)
 
 }  // namespace
 
+namespace qgm {
+bool jit_kernel(const std::string &src, const std::string &name, int device, cudaKernel_t *out,
+                std::string *err);
+}
+
 struct qgm_exec_state {
   int device = -1;
   char *ws = nullptr;
@@ -1067,6 +1073,8 @@ struct qgm_exec_state {
   int sms = 148;
   int kind = QGM_EXEC_STEPWISE;
   int layout = -1;  // index into qgm_plan::resident
+  cudaKernel_t jit = nullptr;  // compiled resident kernel (QGM_EXEC_COMPILED)
+  std::string jit_error;       // why the compiled kernel is not used, if so
 };
 
 static int cuda_fail(cudaError_t e, const char *what) {
@@ -1184,6 +1192,17 @@ static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, doub
   const uint32_t *wl = reinterpret_cast<const uint32_t *>(rs + L.steps.size() * sizeof(RStep) +
                                                           L.jobs.size() * sizeof(RJob));
   const int32_t *wst = reinterpret_cast<const int32_t *>(wl + L.wlist.size());
+  if (x->kind == QGM_EXEC_COMPILED) {
+    const char *ws_c = ws;
+    int n_jobs = (int)L.jobs.size();
+    long long Bl = (long long)B;
+    double cr = c.real(), ci = c.imag();
+    Header *hdr = reinterpret_cast<Header *>(x->ws + p->off_header);
+    void *args[] = {&ws_c, &jobs, &n_jobs, &d_bits, &Bl, &cr, &ci, &d_out, &hdr};
+    cudaLaunchKernel(reinterpret_cast<const void *>(x->jit), dim3((unsigned)G), dim3(RES_THREADS), args,
+                     (size_t)L.smem_bytes, st);
+    return;
+  }
   k_resident<<<(unsigned)G, RES_THREADS, (size_t)L.smem_bytes, st>>>(
       ws, reinterpret_cast<const RStep *>(rs), jobs, (int)L.jobs.size(), wl, (int)L.wlist.size(), wst,
       L.n_levels, L.wlist_soff, d_bits, B, logBc, p->n_meta_fwd, L.final_soff, L.final_meta, p->final_batched,
@@ -1193,7 +1212,7 @@ static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, doub
 static int run(qgm_plan *p, const uint64_t *d_bits, int64_t B, double2 *d_out, int64_t n_out,
                cudaStream_t st) {
   qgm_exec_state *x = p->exec;
-  if (x->kind == QGM_EXEC_RESIDENT) {
+  if (x->kind == QGM_EXEC_RESIDENT || x->kind == QGM_EXEC_COMPILED) {
     launch_resident(p, d_bits, B, d_out, st);
     CK(cudaGetLastError());
     return QGM_OK;
@@ -1324,7 +1343,23 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
       CK(cudaMemcpyAsync(rs + wo + L.wlist.size() * 4, L.wstart, sizeof(L.wstart), cudaMemcpyHostToDevice, st));
       CK(cudaStreamSynchronize(st));
       x->kind = QGM_EXEC_RESIDENT;
-    } else if (p->executor_pref == QGM_EXEC_RESIDENT) {
+      if (p->executor_pref == QGM_EXEC_AUTO || p->executor_pref == QGM_EXEC_COMPILED) {
+        // the same pass as a kernel generated for this plan: as many CTAs per
+        // SM as shared memory allows (at most 6, keeping 42 registers a thread)
+        const int minb = (int)std::max<int64_t>(1, std::min<int64_t>(6, (228 * 1024) / (L.smem_bytes + 1024)));
+        const std::string src = resident_source(p, L, "qgm_resident_plan", minb);
+        cudaKernel_t k = nullptr;
+        if (jit_kernel(src, "qgm_resident_plan", x->device, &k, &x->jit_error)) {
+          CK(cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes,
+                                             x->device));
+          x->jit = k;
+          x->kind = QGM_EXEC_COMPILED;
+        } else if (p->executor_pref == QGM_EXEC_COMPILED) {
+          set_error("qgm_plan_bind: compiled resident kernel unavailable: %s", x->jit_error.c_str());
+          return QGM_ERR_ARG;
+        }
+      }
+    } else if (p->executor_pref == QGM_EXEC_RESIDENT || p->executor_pref == QGM_EXEC_COMPILED) {
       set_error("qgm_plan_bind: no resident layout fits this device's shared memory");
       return QGM_ERR_ARG;
     }
@@ -1339,8 +1374,9 @@ int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int6
   }
   const qgm_exec_state *x = p->exec;
   if (kind) *kind = x->kind;
-  if (chunk) *chunk = x->kind == QGM_EXEC_RESIDENT ? p->resident[x->layout].chunk : (int32_t)p->Bp;
-  if (smem_bytes) *smem_bytes = x->kind == QGM_EXEC_RESIDENT ? p->resident[x->layout].smem_bytes : 0;
+  const bool res = x->kind == QGM_EXEC_RESIDENT || x->kind == QGM_EXEC_COMPILED;
+  if (chunk) *chunk = res ? p->resident[x->layout].chunk : (int32_t)p->Bp;
+  if (smem_bytes) *smem_bytes = res ? p->resident[x->layout].smem_bytes : 0;
   return QGM_OK;
 }
 
@@ -1402,7 +1438,7 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int n = (int)p->steps.size() + 2;
-  if (p->exec->kind == QGM_EXEC_RESIDENT) {
+  if (p->exec->kind == QGM_EXEC_RESIDENT || p->exec->kind == QGM_EXEC_COMPILED) {
     cudaEvent_t a, b;
     CK(cudaEventCreate(&a));
     CK(cudaEventCreate(&b));

@@ -3,6 +3,7 @@
 // list of bucket elimination (Sec. IV, App. A), and the device layout the
 // kernels in exec.cu consume.
 #include <algorithm>
+#include <functional>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -478,17 +479,26 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     T.push_back(t);
     place((int)T.size() - 1);
   }
+  const bool trees = p->trees_ok;
   int n_meta = 0;
-  auto emit = [&](std::vector<int> inputs, int k, bool gemm = false) -> int {
-    // union of the inputs' variables, sorted by position
-    std::vector<int> uni;
+  auto by_pos = [&](int a, int b) { return pos[a] < pos[b]; };
+  // One step: out = sum over `summed` of the product of the inputs.  The
+  // step's union lists the summed variables first, then the kept ones, each
+  // in elimination order; the output keeps the kept ones in that order.
+  auto emit = [&](std::vector<int> inputs, std::vector<int> summed, bool gemm = false) -> int {
+    std::vector<int> all;
     bool batched = false;
     for (int id : inputs) {
-      for (int v : T[id].vars) uni.push_back(v);
+      for (int v : T[id].vars) all.push_back(v);
       batched |= T[id].batched;
     }
-    std::sort(uni.begin(), uni.end(), [&](int a, int b) { return pos[a] < pos[b]; });
-    uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
+    std::sort(all.begin(), all.end(), by_pos);
+    all.erase(std::unique(all.begin(), all.end()), all.end());
+    std::sort(summed.begin(), summed.end(), by_pos);
+    std::vector<int> uni = summed;
+    for (int v : all)
+      if (!std::binary_search(summed.begin(), summed.end(), v, by_pos)) uni.push_back(v);
+    const int k = (int)summed.size();
     SymTensor out;
     out.vars.assign(uni.begin() + k, uni.end());
     out.batched = batched;
@@ -512,7 +522,6 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     R.flops += s.flops;
     R.max_step_bytes = std::max(R.max_step_bytes, s.bytes);
     R.max_entries = std::max(R.max_entries, out.entries);
-    R.max_clique = std::max(R.max_clique, (int)uni.size());
     T.push_back(out);
     int oid = (int)T.size() - 1;
     s.out = oid;
@@ -521,6 +530,11 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     else R.steps.push_back(StepRec{{}, {}, k, oid, batched, s.bytes, s.flops, gemm});
     return oid;
   };
+  // an intermediate consumed inside the same bucket holds its variables live
+  auto hold = [&](int id) {
+    for (int v : T[id].vars) live[v]++;
+    return id;
+  };
   // more than MAXIN inputs: multiply the smallest ones together first
   auto shrink = [&](std::vector<int> &inputs) {
     while ((int)inputs.size() > MAXIN) {
@@ -528,10 +542,151 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
                        [&](int a, int b) { return T[a].entries < T[b].entries; });
       std::vector<int> two = {inputs[0], inputs[1]};
       inputs.erase(inputs.begin(), inputs.begin() + 2);
-      int id = emit(two, 0);
-      for (int v : T[id].vars) live[v]++;
-      inputs.push_back(id);
+      inputs.push_back(hold(emit(two, {})));
     }
+  };
+  auto holds = [&](int id, int v) {
+    return std::find(T[id].vars.begin(), T[id].vars.end(), v) != T[id].vars.end();
+  };
+  // One contraction (a bucket, or a node of a bucket's contraction tree).
+  // GEMM-shaped: the two largest inputs hold every summed variable and every
+  // other input fits inside one of them (it is multiplied into that operand
+  // first, a product step with nothing summed).
+  auto contract = [&](std::vector<int> inputs, const std::vector<int> &summed) -> int {
+    shrink(inputs);
+    const int k = (int)summed.size();
+    if (p->gemm_ok && k >= 4 && inputs.size() >= 2) {
+      std::vector<int> by = inputs;
+      std::stable_sort(by.begin(), by.end(), [&](int a, int b) { return T[a].vars.size() > T[b].vars.size(); });
+      const int A = by[0], Bt = by[1];
+      bool ok = T[A].vars.size() >= 10 && T[Bt].vars.size() >= 10;
+      for (int v : summed) ok = ok && holds(A, v) && holds(Bt, v);
+      std::vector<int> toA = {A}, toB = {Bt};
+      for (size_t q = 2; q < by.size() && ok; ++q) {
+        bool inA = true, inB = true;
+        for (int v : T[by[q]].vars) {
+          inA = inA && holds(A, v);
+          inB = inB && holds(Bt, v);
+        }
+        if (T[by[q]].vars.size() > 8 || (!inA && !inB)) ok = false;
+        else if (inB && (!inA || T[Bt].entries < T[A].entries)) toB.push_back(by[q]);
+        else toA.push_back(by[q]);
+      }
+      int nm = 0, nn = 0;
+      std::vector<int> kept;
+      for (int id : inputs)
+        for (int v : T[id].vars)
+          if (std::find(summed.begin(), summed.end(), v) == summed.end() &&
+              std::find(kept.begin(), kept.end(), v) == kept.end())
+            kept.push_back(v);
+      for (int v : kept) {
+        if (!ok) break;
+        const bool ha = holds(A, v), hb = holds(Bt, v);
+        if (!ha && !hb) ok = false;
+        nm += ha && !hb;
+        nn += hb && !ha;
+      }
+      if (ok && nm >= 6 && nn >= 6 && nm < GMAXB && nn < GMAXB) {
+        auto premul = [&](std::vector<int> &grp) { return grp.size() == 1 ? grp[0] : hold(emit(grp, {})); };
+        const int a2 = premul(toA), b2 = premul(toB);
+        return emit({a2, b2}, summed, true);
+      }
+    }
+    return emit(inputs, summed);
+  };
+  // Contraction tree of a bucket with three or more inputs (App. A sums the
+  // bucket's product in one go; multiplying pairs first and summing each
+  // variable as soon as no other factor holds it gives the same sum with
+  // fewer products).  Dynamic programming over subsets of the inputs for the
+  // cheapest binary tree (cost of a node: entries of its union plus entries
+  // written; intermediates at most one variable wider than the widest input
+  // or the output), then children whose union lies inside the parent's are
+  // merged back into it when that is cheaper.  Used when it beats the single
+  // product-sum by a clear margin.
+  auto contract_tree = [&](std::vector<int> inputs, const std::vector<int> &uni, int k) -> int {
+    const int n = (int)inputs.size(), U = (int)uni.size();
+    std::vector<int> summed(uni.begin(), uni.begin() + k);
+    if (!trees || n < 3 || n > MAXIN || U > 62) return contract(inputs, summed);
+    std::vector<uint64_t> vm(n);
+    int widest = 0;
+    for (int i = 0; i < n; ++i) {
+      for (int v : T[inputs[i]].vars) vm[i] |= 1ull << (std::find(uni.begin(), uni.end(), v) - uni.begin());
+      widest = std::max(widest, (int)T[inputs[i]].vars.size());
+    }
+    const uint64_t smask = (k >= 64) ? ~0ull : ((1ull << k) - 1);
+    const int full = (1 << n) - 1;
+    std::vector<uint64_t> all(full + 1, 0), res(full + 1, 0);
+    std::vector<char> bat(full + 1, 0);
+    for (int t = 1; t <= full; ++t) {
+      const int i = __builtin_ctz(t);
+      all[t] = all[t & (t - 1)] | vm[i];
+      bat[t] = bat[t & (t - 1)] | (T[inputs[i]].batched ? 1 : 0);
+    }
+    for (int t = 1; t <= full; ++t) res[t] = all[t] & ~(smask & ~all[full ^ t]);
+    const int limit = std::max(widest, __builtin_popcountll(res[full])) + 1;
+    auto ent = [&](uint64_t mask, bool b) { return std::ldexp(b ? (double)Bp : 1.0, __builtin_popcountll(mask)); };
+    const double step_over = 256.0;
+    std::vector<double> best(full + 1, 0.0);
+    std::vector<int> split_of(full + 1, 0);
+    for (int t = 1; t <= full; ++t) {
+      if (!(t & (t - 1))) continue;
+      best[t] = 1e300;
+      if (t != full && __builtin_popcountll(res[t]) > limit) continue;
+      const int low = t & -t, rest = t ^ low;
+      // t1 = low + any proper subset of the rest (t2 non-empty)
+      for (int sub = (rest - 1) & rest;; sub = (sub - 1) & rest) {
+        const int t1 = low | sub, t2 = t ^ t1;
+        if (best[t1] < 1e299 && best[t2] < 1e299) {
+          const double c = best[t1] + best[t2] + ent(res[t1] | res[t2], bat[t]) + ent(res[t], bat[t]) + step_over;
+          if (c < best[t]) {
+            best[t] = c;
+            split_of[t] = t1;
+          }
+        }
+        if (sub == 0) break;
+      }
+    }
+    const double fused = (n - 1) * ent(all[full], bat[full]) + ent(res[full], bat[full]) + step_over;
+    if (!(best[full] < 0.8 * fused)) return contract(inputs, summed);
+    // emit the tree: a leaf is an input, a node a subset of the inputs; a
+    // child is merged into its parent when the parent's union covers it and
+    // that is cheaper
+    std::function<int(int)> run = [&](int t) -> int {
+      if (!(t & (t - 1))) return inputs[__builtin_ctz(t)];
+      // flatten children whose contraction is better done inside this node
+      std::vector<int> kids = {split_of[t], t ^ split_of[t]};
+      const uint64_t u = res[split_of[t]] | res[t ^ split_of[t]];
+      bool changed = true;
+      while (changed) {
+        changed = false;
+        for (size_t q = 0; q < kids.size(); ++q) {
+          const int c = kids[q];
+          if (!(c & (c - 1))) continue;
+          const uint64_t uc = res[split_of[c]] | res[c ^ split_of[c]];
+          if (uc & ~u) continue;
+          const double sep = ent(uc, bat[c]) + ent(res[c], bat[c]) + step_over;
+          if (ent(u, bat[t]) <= sep) {
+            kids[q] = split_of[c];
+            kids.push_back(c ^ split_of[c]);
+            changed = true;
+            break;
+          }
+        }
+      }
+      std::vector<int> ins;
+      for (int c : kids) {
+        const int id = run(c);
+        ins.push_back((c & (c - 1)) ? hold(id) : id);
+      }
+      std::vector<int> sm;
+      uint64_t gone = 0;
+      for (int c : kids) gone |= res[c];
+      gone &= ~res[t];
+      for (int b = 0; b < U; ++b)
+        if ((gone >> b) & 1) sm.push_back(uni[b]);
+      return contract(ins, sm);
+    };
+    return run(full);
   };
   for (int pi = 0; pi < ne; ++pi) {
     if (bucket[pi].empty()) continue;
@@ -540,7 +695,7 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     std::vector<int> uni;
     for (int id : inputs)
       for (int v : T[id].vars) uni.push_back(v);
-    std::sort(uni.begin(), uni.end(), [&](int a, int b) { return pos[a] < pos[b]; });
+    std::sort(uni.begin(), uni.end(), by_pos);
     uni.erase(std::unique(uni.begin(), uni.end()), uni.end());
     int k = 1;
     // fuse the next variables of the union while every tensor holding them is
@@ -563,50 +718,7 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       ++k;
     }
     shrink(inputs);
-    // GEMM-shaped step: the two largest inputs hold every summed variable
-    // and every other input fits inside one of them (it is multiplied into
-    // that operand first, a product step with nothing summed)
-    bool gemm = false;
-    if (p->gemm_ok && k >= 4 && inputs.size() >= 2) {
-      std::vector<int> by = inputs;
-      std::stable_sort(by.begin(), by.end(), [&](int a, int b) { return T[a].vars.size() > T[b].vars.size(); });
-      const int A = by[0], Bt = by[1];
-      auto holds = [&](int id, int v) {
-        return std::find(T[id].vars.begin(), T[id].vars.end(), v) != T[id].vars.end();
-      };
-      bool ok = T[A].vars.size() >= 10 && T[Bt].vars.size() >= 10;
-      for (int a = 0; a < k && ok; ++a) ok = holds(A, uni[a]) && holds(Bt, uni[a]);
-      std::vector<int> toA = {A}, toB = {Bt};
-      for (size_t q = 2; q < by.size() && ok; ++q) {
-        bool inA = true, inB = true;
-        for (int v : T[by[q]].vars) {
-          inA = inA && holds(A, v);
-          inB = inB && holds(Bt, v);
-        }
-        if (T[by[q]].vars.size() > 8 || (!inA && !inB)) ok = false;
-        else if (inB && (!inA || T[Bt].entries < T[A].entries)) toB.push_back(by[q]);
-        else toA.push_back(by[q]);
-      }
-      int nm = 0, nn = 0;
-      for (size_t a = k; a < uni.size() && ok; ++a) {
-        const bool ha = holds(A, uni[a]), hb = holds(Bt, uni[a]);
-        if (!ha && !hb) ok = false;
-        nm += ha && !hb;
-        nn += hb && !ha;
-      }
-      if (ok && nm >= 6 && nn >= 6 && nm < GMAXB && nn < GMAXB) {
-        auto premul = [&](std::vector<int> &grp) {
-          if (grp.size() == 1) return grp[0];
-          int id = emit(grp, 0);
-          for (int v : T[id].vars) live[v]++;
-          return id;
-        };
-        const int a2 = premul(toA), b2 = premul(toB);
-        inputs = {a2, b2};
-        gemm = true;
-      }
-    }
-    int oid = emit(inputs, k, gemm);
+    const int oid = contract_tree(inputs, uni, k);
     place(oid);
   }
   // final product over the remaining tensors (scalars per batch entry, or
@@ -619,7 +731,7 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     R.final_tensor = fin[0];
   } else {
     shrink(fin);
-    int oid = emit(fin, 0);
+    int oid = emit(fin, {});
     R.final_tensor = oid;
   }
   R.final_tensors = finals;
@@ -890,6 +1002,8 @@ static void build_resident(qgm_plan *p) {
         }
         r.bytes = (int32_t)(offsetof(RStep, in) + d.m * sizeof(RIn));
         L.steps.push_back(r);
+        L.src_step.push_back(si);
+        L.level.push_back(lv);
       }
       pos = end;
     }
@@ -957,6 +1071,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   }
   const int max_fuse = o.max_fuse > 0 ? std::min(o.max_fuse, 16) : 8;
   p->gemm_ok = o.no_gemm == 0;
+  p->trees_ok = o.trees != 0;
   const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)64 << 30;
 
   reduce_factors(m, p->leaves, p->constant, p->half_pow_total);
@@ -1293,31 +1408,12 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
       in.off = it.off;
       in.meta = it.leaf < 0 ? it.meta : -1;
       in.batched = it.batched ? 1 : 0;
-      // union bit of var a is U-1-a; the input keeps its variables in order
-      int nr = 0, dst = 0;
-      int b = 0;
-      while (b < U) {
-        auto present = [&](int bit) {
-          int v = s.uni[U - 1 - bit];
-          return std::find(it.vars.begin(), it.vars.end(), v) != it.vars.end();
-        };
-        if (!present(b)) {
-          ++b;
-          continue;
-        }
-        int st = b;
-        while (b < U && present(b)) ++b;
-        if (nr >= MAXRUN) {
-          set_error("internal: index map with more than %d runs", MAXRUN);
-          return QGM_ERR_ARG;
-        }
-        in.src[nr] = (uint8_t)st;
-        in.len[nr] = (uint8_t)(b - st);
-        in.dst[nr] = (uint8_t)dst;
-        dst += b - st;
-        ++nr;
+      // union bit of var a is U-1-a; summed variables come first in the
+      // union, so an input's bits may land out of order (general runs)
+      if (!make_runs(s.uni, it.vars, in)) {
+        set_error("internal: index map with more than %d runs", MAXRUN);
+        return QGM_ERR_ARG;
       }
-      in.nruns = nr;
     }
     // register tile for large batched steps whose output has bits the
     // largest input lacks (those outputs reuse its loaded values)
@@ -1464,7 +1560,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     p->n_meta = next_meta;
     p->ws_bytes = goff + 256;
   }
-  if (o.executor < 0 || o.executor > 2) {
+  if (o.executor < 0 || o.executor > 3) {
     set_error("qgm_plan_order: bad executor %d", o.executor);
     return QGM_ERR_ARG;
   }

@@ -167,6 +167,7 @@ struct ResidentLayout {
   int n_levels = 0;
   int wlist_soff = 0;       // smem byte offset of the work lists
   int final_soff = -1, final_meta = -1;
+  std::vector<int> src_step, level;  // per entry of `steps`: plan step, dependency level
 };
 
 // Gradient of one parametrised gate (adjoint elimination): the adjoint of
@@ -272,9 +273,12 @@ struct qgm_plan {
   int64_t off_rsteps = 0;   // workspace region for the chosen layout's steps
   int executor_pref = 0;    // qgm_plan_opts.executor
   bool gemm_ok = true;      // GEMM-shaped steps run by the GEMM kernel
+  bool trees_ok = false;    // buckets of three or more inputs may run as contraction trees
   qgm_exec_state *exec = nullptr;
 };
 
 namespace qgm {
 int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p);
+// CUDA source of the resident kernel specialised to one layout (jit.cpp)
+std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const std::string &name, int minb);
 }

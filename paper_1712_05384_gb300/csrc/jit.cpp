@@ -1,0 +1,385 @@
+// Plan-specialised resident kernel (compiled at bind time with NVRTC).
+//
+// The resident executor runs the whole elimination of one chunk of
+// bitstrings inside one CTA (Sec. IV, App. A: every bucket's product-sum
+// with all tensors in shared memory).  Its generic form reads a descriptor
+// per step (index-map tables, warp schedule) and walks it at run time; for
+// the small steps that dominate low-depth circuits that bookkeeping costs
+// more than the arithmetic.  This file writes the same computation as CUDA
+// source with every plan constant in place (shared-memory offsets, index
+// maps, loop bounds, the warp schedule of each dependency level), so that
+// each step is only its loads, complex products and stores, and compiles it
+// for the device with NVRTC (loaded with dlopen; when it is missing, or the
+// compile fails, the generic resident kernel runs instead).
+//
+// Arithmetic is the generic kernel's: per-tensor power-of-two exponents
+// (the producer records max |re|,|im|; the consumer scales by 2^-e), one
+// combined scale per output entry when the inputs' exponents sum to a
+// representable power of two, per-load scaling otherwise.
+#include <cuda_runtime.h>
+#include <dlfcn.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "host.h"
+
+namespace qgm {
+
+namespace {
+
+// Value of union bit b in input i of step d, in float2 elements (0 when the
+// input does not hold that variable).
+std::vector<int64_t> union_values(const InDesc &in, int U, int64_t unit) {
+  std::vector<int64_t> v(U, 0);
+  for (int q = 0; q < in.nruns; ++q)
+    for (int l = 0; l < in.len[q]; ++l) v[in.src[q] + l] = ((int64_t)1 << (in.dst[q] + l)) * unit;
+  return v;
+}
+
+// C expression for sum_b bit_b(x) * val[lo + b], b < n, with val[] powers of
+// two or 0: runs of consecutive bits whose values double become one
+// shift-and-mask term.
+std::string bit_map_expr(const std::string &x, const std::vector<int64_t> &val, int lo, int n) {
+  std::string e;
+  int b = 0;
+  while (b < n) {
+    if (val[lo + b] == 0) {
+      ++b;
+      continue;
+    }
+    int l = 1;
+    while (b + l < n && val[lo + b + l] == val[lo + b] * ((int64_t)1 << l)) ++l;
+    const int s = __builtin_ctzll((unsigned long long)val[lo + b]);
+    std::ostringstream t;
+    t << "(((" << x << " >> " << b << ") & " << ((1 << l) - 1) << ") << " << s << ")";
+    e += (e.empty() ? "" : " + ") + t.str();
+    b += l;
+  }
+  return e.empty() ? "0" : e;
+}
+
+int64_t bit_map_value(int64_t x, const std::vector<int64_t> &val, int lo, int n) {
+  int64_t r = 0;
+  for (int b = 0; b < n; ++b)
+    if ((x >> b) & 1) r += val[lo + b];
+  return r;
+}
+
+const char *kPrelude = R"(
+typedef unsigned long long u64;
+struct Header { int status; int slice_id; int pad[62]; };
+struct Meta { unsigned maxbits; int exp; };
+struct RJob { int src; int dst; unsigned char n_out, q0, q1, batched; };
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float fmax_nan(float a, float b) { return (a > b || a != a) ? a : b; }
+__device__ __forceinline__ float absmax2(float2 a) { return fmax_nan(fabsf(a.x), fabsf(a.y)); }
+__device__ __forceinline__ void opscale(const Meta *meta, int slot, Header *hdr, float &s, int &e, int &esum) {
+  const unsigned bits = meta[slot].maxbits;
+  const int E = (int)((bits >> 23) & 0xff);
+  s = 1.f;
+  e = 0;
+  if (E == 0xff) atomicCAS(&hdr->status, 0, -5);
+  else if (E != 0) {
+    e = E - 126;
+    if (e > 126) e = 126;
+    s = __int_as_float((127 - e) << 23);
+  }
+  esum += e + meta[slot].exp;
+}
+)";
+
+constexpr int kUnroll = 16;  // terms per unrolled block
+
+// One step's body for the threads of its warps (gt = thread index in the
+// group).  fast: raw products, one combined scale per entry; else each
+// loaded value is scaled by its operand's factor.
+void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L, size_t q, bool fast) {
+  const RStep &r = L.steps[q];
+  const StepDesc &d = p->steps[L.src_step[q]];
+  const int logBc = __builtin_ctz(L.chunk);
+  const int m = d.m, k = d.k, w = d.w_out, U = w + k;
+  const int nw = (r.sched >> 4) & 15, lg = (r.sched >> 8) & 15;
+  const int lb = r.batched_out ? logBc : 0;
+  const int64_t items = ((int64_t)1 << w) << lb;
+  const int G = 32 * nw, tpi = 1 << lg, sit = G >> lg;
+  const int64_t n_iter = (items * tpi + G - 1) / G;
+  const bool always_live = (items * tpi) % G == 0 && items * tpi >= G;
+  const int tpt_log = k - lg;  // terms per thread per item: 2^tpt_log
+  const int unr_log = std::min(tpt_log, __builtin_ctz(kUnroll));
+  std::vector<std::vector<int64_t>> v(m);
+  for (int i = 0; i < m; ++i) v[i] = union_values(d.in[i], U, r.in[i].batched ? L.chunk : 1);
+  o << "    float lmax = 0.f;\n";
+  if (lg) {
+    o << "    const int g = gt & " << (tpi - 1) << ";\n";
+    for (int i = 0; i < m; ++i) o << "    const int go" << i << " = " << bit_map_expr("g", v[i], w, lg) << ";\n";
+  }
+  o << "#pragma unroll 1\n    for (int j = 0; j < " << n_iter << "; ++j) {\n";
+  o << "      const int it = (gt >> " << lg << ") + j * " << sit << ";\n";
+  o << "      float2 acc = make_float2(0.f, 0.f);\n";
+  o << "      if (" << (always_live ? "true" : "it < " + std::to_string(items)) << ") {\n";
+  if (w) o << "        const int row = it >> " << lb << ";\n";
+  if (lb) o << "        const int beta = it & " << ((1 << lb) - 1) << ";\n";
+  for (int i = 0; i < m; ++i) {
+    o << "        const int b" << i << " = " << (r.in[i].soff / 8);
+    if (r.in[i].batched && lb) o << " + beta";
+    o << " + " << bit_map_expr("row", v[i], 0, w);
+    if (lg) o << " + go" << i;
+    o << ";\n";
+  }
+  auto load = [&](int i, const std::string &idx) {
+    std::ostringstream t;
+    if (fast || r.in[i].meta < 0) t << "F[" << idx << "]";
+    else t << "sc(F[" << idx << "], s" << i << ")";
+    return t.str();
+  };
+  if (fast) {
+    // unrolled blocks of 2^unr_log terms: block offsets at run time, term
+    // offsets inside a block as constants
+    const int blk_log = tpt_log - unr_log;
+    o << "        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);\n";
+    o << "#pragma unroll 1\n        for (int blk = 0; blk < " << (1 << blk_log) << "; ++blk) {\n";
+    for (int i = 0; i < m; ++i) {
+      // term index e = (blk << (unr_log + lg)) | (u << lg) | g
+      std::string e = blk_log ? bit_map_expr("blk", v[i], w + lg + unr_log, blk_log) : std::string("0");
+      o << "          const int c" << i << " = b" << i << " + " << e << ";\n";
+    }
+    for (int u = 0; u < (1 << unr_log); ++u) {
+      o << "          { float2 p = " << load(0, "c0 + " + std::to_string(bit_map_value((int64_t)u << lg, v[0], w, k))) << ";\n";
+      for (int i = 1; i < m; ++i)
+        o << "            p = cmul(p, " << load(i, "c" + std::to_string(i) + " + " +
+                                              std::to_string(bit_map_value((int64_t)u << lg, v[i], w, k)))
+          << ");\n";
+      o << "            a" << (u & 1) << ".x += p.x; a" << (u & 1) << ".y += p.y; }\n";
+    }
+    o << "        }\n";
+    o << "        acc = make_float2((a0.x + a1.x) * comb, (a0.y + a1.y) * comb);\n";
+  } else {
+    o << "#pragma unroll 1\n        for (int t = 0; t < " << (1 << tpt_log) << "; ++t) {\n";
+    for (int i = 0; i < m; ++i)
+      o << "          const int c" << i << " = b" << i << " + "
+        << (tpt_log ? bit_map_expr("t", v[i], w + lg, tpt_log) : std::string("0")) << ";\n";
+    o << "          float2 p = " << load(0, "c0") << ";\n";
+    for (int i = 1; i < m; ++i) o << "          p = cmul(p, " << load(i, "c" + std::to_string(i)) << ");\n";
+    o << "          acc.x += p.x; acc.y += p.y;\n        }\n";
+  }
+  o << "      }\n";
+  for (int s = 1; s < tpi; s <<= 1)
+    o << "      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, " << s << "); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, "
+      << s << ");\n";
+  o << "      if (" << (always_live ? "true" : "it < " + std::to_string(items)) << (lg ? " && g == 0" : "") << ") {\n";
+  o << "        F[" << (r.out_soff / 8) << " + it] = acc;\n";
+  o << "        lmax = fmax_nan(lmax, absmax2(acc));\n      }\n";
+  o << "    }\n";
+}
+
+}  // namespace
+
+// CUDA source of the resident kernel specialised to layout L of plan p.
+std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const std::string &name, int minb) {
+  std::ostringstream o;
+  o << kPrelude;
+  o << "__device__ __forceinline__ float2 sc(float2 v, float s) { return make_float2(v.x * s, v.y * s); }\n";
+  const int logBc = __builtin_ctz(L.chunk);
+  o << "extern \"C\" __global__ void __launch_bounds__(256, " << minb << ") " << name
+    << "(const char *ws, const RJob *jobs, int n_jobs, const u64 *bits, long long B, double c_re, double c_im, "
+       "double2 *out, Header *hdr) {\n";
+  o << "  extern __shared__ __align__(16) char sm[];\n";
+  o << "  float2 *F = reinterpret_cast<float2 *>(sm);\n";
+  o << "  Meta *meta = reinterpret_cast<Meta *>(sm);\n";
+  o << "  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;\n";
+  o << "  const long long b0 = (long long)blockIdx.x * " << L.chunk << ";\n";
+  o << "  for (int i = tid; i < " << p->n_meta_fwd << "; i += 256) { meta[i].maxbits = 0u; meta[i].exp = 0; }\n";
+  // leaves: one job per leaf row (batched rows select the base entry from
+  // the output bits of x_beta)
+  o << "  const float2 *wsf = reinterpret_cast<const float2 *>(ws);\n";
+  o << "  for (int t = tid; t < (n_jobs << " << logBc << "); t += 256) {\n";
+  o << "    const int b = t & " << (L.chunk - 1) << ";\n";
+  o << "    const RJob jb = jobs[t >> " << logBc << "];\n";
+  o << "    if (!jb.batched && b) continue;\n";
+  o << "    int ob = 0;\n";
+  o << "    if (jb.n_out) {\n";
+  o << "      const u64 x = (b0 + b < B) ? bits[b0 + b] : 0ull;\n";
+  o << "      ob = jb.n_out == 1 ? (int)((x >> jb.q0) & 1ull) : (int)((((x >> jb.q0) & 1ull) << 1) | ((x >> jb.q1) & 1ull));\n";
+  o << "    }\n";
+  o << "    reinterpret_cast<float2 *>(sm + jb.dst)[jb.batched ? b : 0] = __ldg(wsf + jb.src + ob);\n";
+  o << "  }\n  __syncthreads();\n";
+  int cur_level = 0;
+  for (size_t q = 0; q < L.steps.size(); ++q) {
+    if (L.level[q] != cur_level) {
+      o << "  __syncthreads();\n";
+      cur_level = L.level[q];
+    }
+    const RStep &r = L.steps[q];
+    const StepDesc &d = p->steps[L.src_step[q]];
+    const int w0 = r.sched & 15, nw = (r.sched >> 4) & 15;
+    o << "  // step " << L.src_step[q] << ": " << d.m << " inputs, " << d.k << " summed, " << d.w_out
+      << " kept (level " << L.level[q] << ")\n";
+    o << "  if (wid >= " << w0 << " && wid < " << (w0 + nw) << ") {\n";
+    o << "    const int gt = tid - " << (32 * w0) << ";\n";
+    o << "    int es = 0, esum = 0;\n";
+    for (int i = 0; i < d.m; ++i) {
+      if (r.in[i].meta >= 0) {
+        o << "    float s" << i << "; { int e; opscale(meta, " << r.in[i].meta << ", hdr, s" << i
+          << ", e, esum); es += e; }\n";
+      }
+    }
+    o << "    float lm;\n";
+    bool any_meta = false;
+    for (int i = 0; i < d.m; ++i) any_meta |= r.in[i].meta >= 0;
+    if (!any_meta) {  // leaves only: no scale
+      o << "    const float comb = 1.f;\n";
+      std::ostringstream b;
+      emit_body(b, p, L, q, true);
+      o << "    {\n" << b.str() << "    lm = lmax; }\n";
+    } else {
+    o << "    if (es >= -120 && es <= 120) {\n";
+    o << "      const float comb = __int_as_float((127 - es) << 23);\n";
+    {
+      std::ostringstream b;
+      emit_body(b, p, L, q, true);
+      o << "    {\n" << b.str() << "    lm = lmax; }\n";
+    }
+    o << "    } else {\n";
+    {
+      std::ostringstream b;
+      emit_body(b, p, L, q, false);
+      o << "    {\n" << b.str() << "    lm = lmax; }\n";
+    }
+    o << "    }\n";
+    }
+    o << "    for (int s = 16; s > 0; s >>= 1) lm = fmax_nan(lm, __shfl_xor_sync(0xffffffffu, lm, s));\n";
+    o << "    if (lane == 0) {\n";
+    o << "      if (lm > 0.f || lm != lm) atomicMax(&meta[" << r.out_meta << "].maxbits, __float_as_uint(lm));\n";
+    o << "      if (wid == " << w0 << ") meta[" << r.out_meta << "].exp = esum;\n";
+    o << "    }\n  }\n";
+  }
+  o << "  __syncthreads();\n";
+  o << "  if (tid == 0 && ((meta[" << L.final_meta << "].maxbits >> 23) & 0xff) == 0xff) atomicCAS(&hdr->status, 0, -5);\n";
+  o << "  if (tid < " << L.chunk << " && b0 + tid < B) {\n";
+  o << "    const float2 v = F[" << (L.final_soff / 8) << (p->final_batched ? " + tid" : "") << "];\n";
+  o << "    const double scl = ldexp(1.0, meta[" << L.final_meta << "].exp);\n";
+  o << "    const double re = (double)v.x * scl, im = (double)v.y * scl;\n";
+  o << "    out[b0 + tid] = make_double2(re * c_re - im * c_im, re * c_im + im * c_re);\n";
+  o << "  }\n}\n";
+  return o.str();
+}
+
+}  // namespace qgm
+
+// ---------------------------------------------------------------- NVRTC
+namespace qgm {
+
+namespace {
+
+struct Nvrtc {
+  bool ok = false;
+  int (*create)(void **, const char *, const char *, int, const char *const *, const char *const *) = nullptr;
+  int (*compile)(void *, int, const char *const *) = nullptr;
+  int (*log_size)(void *, size_t *) = nullptr;
+  int (*log)(void *, char *) = nullptr;
+  int (*cubin_size)(void *, size_t *) = nullptr;
+  int (*cubin)(void *, char *) = nullptr;
+  int (*destroy)(void **) = nullptr;
+};
+
+Nvrtc &nvrtc() {
+  static Nvrtc n;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *h = nullptr;
+    for (const char *name : {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13"})
+      if ((h = dlopen(name, RTLD_NOW | RTLD_LOCAL))) break;
+    if (!h) return;
+    n.create = reinterpret_cast<decltype(n.create)>(dlsym(h, "nvrtcCreateProgram"));
+    n.compile = reinterpret_cast<decltype(n.compile)>(dlsym(h, "nvrtcCompileProgram"));
+    n.log_size = reinterpret_cast<decltype(n.log_size)>(dlsym(h, "nvrtcGetProgramLogSize"));
+    n.log = reinterpret_cast<decltype(n.log)>(dlsym(h, "nvrtcGetProgramLog"));
+    n.cubin_size = reinterpret_cast<decltype(n.cubin_size)>(dlsym(h, "nvrtcGetCUBINSize"));
+    n.cubin = reinterpret_cast<decltype(n.cubin)>(dlsym(h, "nvrtcGetCUBIN"));
+    n.destroy = reinterpret_cast<decltype(n.destroy)>(dlsym(h, "nvrtcDestroyProgram"));
+    n.ok = n.create && n.compile && n.log_size && n.log && n.cubin_size && n.cubin && n.destroy;
+  });
+  return n;
+}
+
+struct CacheKey {
+  int device;
+  size_t hash, len;
+  bool operator<(const CacheKey &o) const {
+    return device != o.device ? device < o.device : hash != o.hash ? hash < o.hash : len < o.len;
+  }
+};
+
+std::mutex g_cache_mu;
+std::map<CacheKey, cudaKernel_t> g_cache;
+
+}  // namespace
+
+// Compile `src` for the current device (sm_103a) and return kernel `name`.
+// Kernels are cached per device and source for the life of the process.
+// Returns false (with a message in *err) when NVRTC is unavailable or the
+// compile or load fails.
+bool jit_kernel(const std::string &src, const std::string &name, int device, cudaKernel_t *out,
+                std::string *err) {
+  const CacheKey key{device, std::hash<std::string>()(src), src.size()};
+  {
+    std::lock_guard<std::mutex> lk(g_cache_mu);
+    auto it = g_cache.find(key);
+    if (it != g_cache.end()) {
+      *out = it->second;
+      return true;
+    }
+  }
+  Nvrtc &n = nvrtc();
+  if (!n.ok) {
+    *err = "NVRTC library not found";
+    return false;
+  }
+  void *prog = nullptr;
+  if (n.create(&prog, src.c_str(), "qgm_resident.cu", 0, nullptr, nullptr) != 0) {
+    *err = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const char *opts[] = {"--gpu-architecture=sm_103a", "-std=c++17", "-default-device"};
+  const int rc = n.compile(prog, 3, opts);
+  if (rc != 0) {
+    size_t ls = 0;
+    n.log_size(prog, &ls);
+    std::string log(ls, '\0');
+    if (ls) n.log(prog, &log[0]);
+    *err = "NVRTC compile failed: " + log.substr(0, 2000);
+    n.destroy(&prog);
+    return false;
+  }
+  size_t cs = 0;
+  n.cubin_size(prog, &cs);
+  std::vector<char> cubin(cs);
+  n.cubin(prog, cubin.data());
+  n.destroy(&prog);
+  cudaLibrary_t lib;
+  cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
+    return false;
+  }
+  cudaKernel_t k;
+  e = cudaLibraryGetKernel(&k, lib, name.c_str());
+  if (e != cudaSuccess) {
+    *err = std::string("cudaLibraryGetKernel: ") + cudaGetErrorString(e);
+    return false;
+  }
+  std::lock_guard<std::mutex> lk(g_cache_mu);
+  g_cache[key] = k;
+  *out = k;
+  return true;
+}
+
+}  // namespace qgm

@@ -22,7 +22,7 @@ from oracle import ve
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-EXECS = [1, 2]   # stepwise, resident
+EXECS = [1, 2, 3]   # stepwise, resident, compiled resident
 REL_TOL = 1e-5
 ABS_TOL = 1e-5   # on |a - a_ref| * 2^{n/2}
 
@@ -48,7 +48,7 @@ def errors(a, ref, n):
     return rel, np.max(np.abs(a - ref)) * 2.0 ** (n / 2)
 
 
-def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0, executor=0):
+def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0, executor=0, trees=False):
     q = Q()
     if circuit_py.rows:
         c = q.Circuit.grid(circuit_py.rows, circuit_py.cols, circuit_py.depth, circuit_py.seed,
@@ -56,7 +56,7 @@ def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0, exec
     else:
         c = q.Circuit.from_gates(circuit_py.n, circuit_py.gates)
     p = q.Plan(q.Model(c), order_kind=order_kind, batch=B, mem_budget_bytes=budget,
-               max_fuse=max_fuse, executor=executor).bind()
+               max_fuse=max_fuse, executor=executor, trees=trees).bind()
     if executor:
         assert p.executor()[0] == executor
     if bits is None:
@@ -160,7 +160,7 @@ def test_grid5x5_d20_b1024_sampled(executor):
     c = qi.grid_circuit(5, 5, 20, 0)
     a, bits, p = run_batch(c, 1024, executor=executor)
     if executor == 0:
-        assert p.executor()[0] == 2
+        assert p.executor()[0] == 3
     idx = np.linspace(0, 1023, 64).astype(int)
     ref = ve.amplitudes(c, bits[idx])
     rel, ab = errors(a[idx], ref, c.n)
@@ -227,16 +227,17 @@ def test_errors_are_reported():
                executor=2)
 
 
+@pytest.mark.parametrize("executor", [2, 3])
 @pytest.mark.parametrize("chunk", [1, 2, 4, 8])
-def test_resident_chunks_agree(chunk):
+def test_resident_chunks_agree(chunk, executor):
     # bitstrings per CTA 1..8, batch 77 leaves a ragged last chunk
     q = Q()
     c = qi.grid_circuit(4, 4, 16, 6)
     bits = qi.bitstrings(16, 77, 6)
     ref = sv.amplitudes(c, bits)
-    p = q.Plan(q.Model(q.Circuit.grid(4, 4, 16, 6)), batch=77, executor=2,
+    p = q.Plan(q.Model(q.Circuit.grid(4, 4, 16, 6)), batch=77, executor=executor,
                resident_chunk=chunk).bind()
-    assert p.executor()[:2] == (2, chunk)
+    assert p.executor()[:2] == (executor, chunk)
     a = p.amplitudes_host(bits)
     rel, ab = errors(a, ref, c.n)
     assert rel < REL_TOL and ab < ABS_TOL
@@ -316,4 +317,23 @@ def test_register_tiled_steps_vs_state_vector():
     assert p.info.n_tile_steps > 0
     a = p.bind().amplitudes_host(bits)
     rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+@pytest.mark.parametrize("executor", EXECS)
+@pytest.mark.parametrize("rows,cols,depth,B", [(4, 4, 14, 40), (3, 5, 20, 17)])
+def test_contraction_trees_vs_state_vector(rows, cols, depth, B, executor):
+    # buckets run as contraction trees (pairs first, each variable summed as
+    # soon as no other factor holds it): same amplitudes, fewer products
+    c = qi.grid_circuit(rows, cols, depth, seed=7)
+    a, bits, p = run_batch(c, B, executor=executor, trees=True)
+    rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+def test_contraction_trees_grid5x5_d20_sampled():
+    c = qi.grid_circuit(5, 5, 20, 0)
+    a, bits, p = run_batch(c, 1024, trees=True)
+    idx = np.linspace(0, 1023, 24).astype(int)
+    rel, ab = errors(a[idx], ve.amplitudes(c, bits[idx]), c.n)
     assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)

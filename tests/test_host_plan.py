@@ -150,3 +150,18 @@ def test_partially_open_outputs_plan():
         Q.Plan(m, batch=8, open_mask=1 << 16)          # no qubit 16 on a 4x4 grid
     with pytest.raises(Q.QgmError):
         Q.Plan(m, batch=8, open_mask=mask, gradients=True)
+
+
+def test_contraction_trees_need_fewer_products():
+    # 5x5 depth 20: buckets of three or more large inputs multiplied pairwise
+    # (each variable summed once no other factor holds it) need well under
+    # the products of the single product-sum per bucket; same variables
+    m = Q.Model(Q.Circuit.grid(5, 5, 20, 0))
+    plain = Q.Plan(m, batch=64)
+    tree = Q.Plan(m, batch=64, trees=True)
+    assert tree.info.n_free == plain.info.n_free
+    assert tree.info.max_clique == plain.info.max_clique
+    f_plain, f_tree = plain.step_costs()[1].sum(), tree.step_costs()[1].sum()
+    assert f_tree < 0.6 * f_plain
+    st = tree.steps()
+    assert st["k"].sum() == tree.info.n_free
