@@ -1200,7 +1200,7 @@ static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, doub
     Header *hdr = reinterpret_cast<Header *>(x->ws + p->off_header);
     void *args[] = {&ws_c, &jobs, &n_jobs, &d_bits, &Bl, &cr, &ci, &d_out, &hdr};
     cudaLaunchKernel(reinterpret_cast<const void *>(x->jit), dim3((unsigned)G), dim3(RES_THREADS), args,
-                     (size_t)L.smem_bytes, st);
+                     (size_t)(L.smem_bytes - worklist_bytes(L)), st);
     return;
   }
   k_resident<<<(unsigned)G, RES_THREADS, (size_t)L.smem_bytes, st>>>(
@@ -1306,63 +1306,103 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
     CK(cudaMemcpyAsync(x->ws + p->off_gparams, p->gparams.data(), p->gparams.size() * sizeof(GradParam),
                        cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
-  // executor: resident when a layout fits; chunk size by fewest waves x chunk
+  // executor: compiled resident, else resident, when a layout fits; the
+  // chunk size by fewest waves x chunk
   x->kind = QGM_EXEC_STEPWISE;
   x->layout = -1;
-  if (p->executor_pref != QGM_EXEC_STEPWISE && !p->resident.empty()) {
-    int optin = 0;
-    CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, x->device));
+  if (p->executor_pref == QGM_EXEC_STEPWISE || p->resident.empty()) {
+    if (p->executor_pref == QGM_EXEC_RESIDENT || p->executor_pref == QGM_EXEC_COMPILED) {
+      set_error("qgm_plan_bind: this plan has no resident layout (one slice, batch outputs only)");
+      return QGM_ERR_ARG;
+    }
+    return QGM_OK;
+  }
+  int optin = 0, sm_smem = 0, reserved = 0;
+  CK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, x->device));
+  CK(cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, x->device));
+  CK(cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, x->device));
+  auto waves_x_chunk = [&](const ResidentLayout &L, int cps) {
+    const int64_t G = (p->batch + L.chunk - 1) / L.chunk;
+    return (double)((G + (int64_t)x->sms * cps - 1) / ((int64_t)x->sms * cps)) * L.chunk;
+  };
+  auto upload = [&](const ResidentLayout &L) -> int {
+    CK(cudaMemcpyAsync(x->ws + p->off_rsteps, L.steps.data(), L.steps.size() * sizeof(RStep),
+                       cudaMemcpyHostToDevice, st));
+    char *rs = x->ws + p->off_rsteps;
+    const size_t jo = L.steps.size() * sizeof(RStep), wo = jo + L.jobs.size() * sizeof(RJob);
+    if (!L.jobs.empty())
+      CK(cudaMemcpyAsync(rs + jo, L.jobs.data(), L.jobs.size() * sizeof(RJob), cudaMemcpyHostToDevice, st));
+    if (!L.wlist.empty())
+      CK(cudaMemcpyAsync(rs + wo, L.wlist.data(), L.wlist.size() * 4, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(rs + wo + L.wlist.size() * 4, L.wstart, sizeof(L.wstart), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return QGM_OK;
+  };
+  if (p->executor_pref == QGM_EXEC_AUTO || p->executor_pref == QGM_EXEC_COMPILED) {
+    // the pass as a kernel generated for this plan: as many CTAs per SM as
+    // shared memory allows (at most 8), registers bounded to match
+    int best_li = -1, best_cps = 0;
     double best = -1;
     for (size_t li = 0; li < p->resident.size(); ++li) {
       const ResidentLayout &L = p->resident[li];
       if (p->opts.resident_chunk > 0 && L.chunk != p->opts.resident_chunk) continue;
-      if (L.smem_bytes + (int64_t)sizeof(RStep) + 64 > optin) continue;
-      CK(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
-      int cps = 0;
-      CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_resident, RES_THREADS, (size_t)L.smem_bytes));
+      const int64_t smem = L.smem_bytes - worklist_bytes(L);
+      if (smem > optin) continue;
+      const int cps = (int)std::min<int64_t>(8, sm_smem / (smem + reserved));
       if (cps < 1) continue;
-      const int64_t G = (p->batch + L.chunk - 1) / L.chunk;
-      const int64_t waves = (G + (int64_t)x->sms * cps - 1) / ((int64_t)x->sms * cps);
-      const double cost = (double)waves * L.chunk;
+      const double cost = waves_x_chunk(L, cps);
       if (best < 0 || cost < best) {
         best = cost;
-        x->layout = (int)li;
+        best_li = (int)li;
+        best_cps = cps;
       }
     }
-    if (x->layout >= 0) {
-      const ResidentLayout &L = p->resident[x->layout];
-      CK(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
-      CK(cudaMemcpyAsync(x->ws + p->off_rsteps, L.steps.data(), L.steps.size() * sizeof(RStep),
-                         cudaMemcpyHostToDevice, st));
-      char *rs = x->ws + p->off_rsteps;
-      const size_t jo = L.steps.size() * sizeof(RStep), wo = jo + L.jobs.size() * sizeof(RJob);
-      if (!L.jobs.empty())
-        CK(cudaMemcpyAsync(rs + jo, L.jobs.data(), L.jobs.size() * sizeof(RJob), cudaMemcpyHostToDevice, st));
-      if (!L.wlist.empty())
-        CK(cudaMemcpyAsync(rs + wo, L.wlist.data(), L.wlist.size() * 4, cudaMemcpyHostToDevice, st));
-      CK(cudaMemcpyAsync(rs + wo + L.wlist.size() * 4, L.wstart, sizeof(L.wstart), cudaMemcpyHostToDevice, st));
-      CK(cudaStreamSynchronize(st));
-      x->kind = QGM_EXEC_RESIDENT;
-      if (p->executor_pref == QGM_EXEC_AUTO || p->executor_pref == QGM_EXEC_COMPILED) {
-        // the same pass as a kernel generated for this plan: as many CTAs per
-        // SM as shared memory allows (at most 6, keeping 42 registers a thread)
-        const int minb = (int)std::max<int64_t>(1, std::min<int64_t>(6, (228 * 1024) / (L.smem_bytes + 1024)));
-        const std::string src = resident_source(p, L, "qgm_resident_plan", minb);
-        cudaKernel_t k = nullptr;
-        if (jit_kernel(src, "qgm_resident_plan", x->device, &k, &x->jit_error)) {
-          CK(cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes,
-                                             x->device));
-          x->jit = k;
-          x->kind = QGM_EXEC_COMPILED;
-        } else if (p->executor_pref == QGM_EXEC_COMPILED) {
-          set_error("qgm_plan_bind: compiled resident kernel unavailable: %s", x->jit_error.c_str());
-          return QGM_ERR_ARG;
-        }
+    if (best_li >= 0) {
+      const ResidentLayout &L = p->resident[best_li];
+      const std::string src = resident_source(p, L, "qgm_resident_plan", best_cps);
+      cudaKernel_t k = nullptr;
+      if (jit_kernel(src, "qgm_resident_plan", x->device, &k, &x->jit_error)) {
+        CK(cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)(L.smem_bytes - worklist_bytes(L)), x->device));
+        int rc = upload(L);
+        if (rc) return rc;
+        x->jit = k;
+        x->layout = best_li;
+        x->kind = QGM_EXEC_COMPILED;
+        return QGM_OK;
       }
-    } else if (p->executor_pref == QGM_EXEC_RESIDENT || p->executor_pref == QGM_EXEC_COMPILED) {
-      set_error("qgm_plan_bind: no resident layout fits this device's shared memory");
+    } else {
+      x->jit_error = "no layout fits the device's shared memory";
+    }
+    if (p->executor_pref == QGM_EXEC_COMPILED) {
+      set_error("qgm_plan_bind: compiled resident kernel unavailable: %s", x->jit_error.c_str());
       return QGM_ERR_ARG;
     }
+  }
+  double best = -1;
+  for (size_t li = 0; li < p->resident.size(); ++li) {
+    const ResidentLayout &L = p->resident[li];
+    if (p->opts.resident_chunk > 0 && L.chunk != p->opts.resident_chunk) continue;
+    if (L.smem_bytes + (int64_t)sizeof(RStep) + 64 > optin) continue;
+    CK(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+    int cps = 0;
+    CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&cps, k_resident, RES_THREADS, (size_t)L.smem_bytes));
+    if (cps < 1) continue;
+    const double cost = waves_x_chunk(L, cps);
+    if (best < 0 || cost < best) {
+      best = cost;
+      x->layout = (int)li;
+    }
+  }
+  if (x->layout >= 0) {
+    const ResidentLayout &L = p->resident[x->layout];
+    CK(cudaFuncSetAttribute(k_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes));
+    int rc = upload(L);
+    if (rc) return rc;
+    x->kind = QGM_EXEC_RESIDENT;
+  } else if (p->executor_pref == QGM_EXEC_RESIDENT) {
+    set_error("qgm_plan_bind: no resident layout fits this device's shared memory");
+    return QGM_ERR_ARG;
   }
   return QGM_OK;
 }
@@ -1376,7 +1416,10 @@ int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int6
   if (kind) *kind = x->kind;
   const bool res = x->kind == QGM_EXEC_RESIDENT || x->kind == QGM_EXEC_COMPILED;
   if (chunk) *chunk = res ? p->resident[x->layout].chunk : (int32_t)p->Bp;
-  if (smem_bytes) *smem_bytes = res ? p->resident[x->layout].smem_bytes : 0;
+  if (smem_bytes)
+    *smem_bytes = !res ? 0
+                       : p->resident[x->layout].smem_bytes -
+                             (x->kind == QGM_EXEC_COMPILED ? worklist_bytes(p->resident[x->layout]) : 0);
   return QGM_OK;
 }
 

@@ -170,6 +170,10 @@ struct ResidentLayout {
   std::vector<int> src_step, level;  // per entry of `steps`: plan step, dependency level
 };
 
+// Shared-memory bytes of the work lists, which sit between the metadata and
+// the tensors (the compiled kernel has no work lists and drops them).
+inline int64_t worklist_bytes(const ResidentLayout &L) { return ((int64_t)L.wlist.size() * 4 + 15) & ~int64_t(15); }
+
 // Gradient of one parametrised gate (adjoint elimination): the adjoint of
 // the leaf holding the gate, and the leaf's derivative tables with respect to
 // theta and phi in the leaf's base-table layout.

@@ -99,9 +99,10 @@ __device__ __forceinline__ void opscale(const Meta *meta, int slot, Header *hdr,
 constexpr int kUnroll = 16;  // terms per unrolled block
 
 // One step's body for the threads of its warps (gt = thread index in the
-// group).  fast: raw products, one combined scale per entry; else each
-// loaded value is scaled by its operand's factor.
-void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L, size_t q, bool fast) {
+// group): every item's product-sum with raw operand values, times `comb`
+// (2^-es, the inputs' combined scale) per entry.  Shared-memory offsets are
+// the layout's minus `shift` (the generic kernel's work lists are not kept).
+void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L, size_t q, int64_t shift) {
   const RStep &r = L.steps[q];
   const StepDesc &d = p->steps[L.src_step[q]];
   const int logBc = __builtin_ctz(L.chunk);
@@ -114,8 +115,10 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
   const bool always_live = (items * tpi) % G == 0 && items * tpi >= G;
   const int tpt_log = k - lg;  // terms per thread per item: 2^tpt_log
   const int unr_log = std::min(tpt_log, __builtin_ctz(kUnroll));
+  const int blk_log = tpt_log - unr_log;
   std::vector<std::vector<int64_t>> v(m);
   for (int i = 0; i < m; ++i) v[i] = union_values(d.in[i], U, r.in[i].batched ? L.chunk : 1);
+  const std::string live = always_live ? "true" : "it < " + std::to_string(items);
   o << "    float lmax = 0.f;\n";
   if (lg) {
     o << "    const int g = gt & " << (tpi - 1) << ";\n";
@@ -124,58 +127,39 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
   o << "#pragma unroll 1\n    for (int j = 0; j < " << n_iter << "; ++j) {\n";
   o << "      const int it = (gt >> " << lg << ") + j * " << sit << ";\n";
   o << "      float2 acc = make_float2(0.f, 0.f);\n";
-  o << "      if (" << (always_live ? "true" : "it < " + std::to_string(items)) << ") {\n";
+  o << "      if (" << live << ") {\n";
   if (w) o << "        const int row = it >> " << lb << ";\n";
   if (lb) o << "        const int beta = it & " << ((1 << lb) - 1) << ";\n";
   for (int i = 0; i < m; ++i) {
-    o << "        const int b" << i << " = " << (r.in[i].soff / 8);
+    o << "        const int b" << i << " = " << ((r.in[i].soff - shift) / 8);
     if (r.in[i].batched && lb) o << " + beta";
     o << " + " << bit_map_expr("row", v[i], 0, w);
     if (lg) o << " + go" << i;
     o << ";\n";
   }
-  auto load = [&](int i, const std::string &idx) {
-    std::ostringstream t;
-    if (fast || r.in[i].meta < 0) t << "F[" << idx << "]";
-    else t << "sc(F[" << idx << "], s" << i << ")";
-    return t.str();
-  };
-  if (fast) {
-    // unrolled blocks of 2^unr_log terms: block offsets at run time, term
-    // offsets inside a block as constants
-    const int blk_log = tpt_log - unr_log;
-    o << "        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);\n";
-    o << "#pragma unroll 1\n        for (int blk = 0; blk < " << (1 << blk_log) << "; ++blk) {\n";
-    for (int i = 0; i < m; ++i) {
-      // term index e = (blk << (unr_log + lg)) | (u << lg) | g
-      std::string e = blk_log ? bit_map_expr("blk", v[i], w + lg + unr_log, blk_log) : std::string("0");
-      o << "          const int c" << i << " = b" << i << " + " << e << ";\n";
-    }
-    for (int u = 0; u < (1 << unr_log); ++u) {
-      o << "          { float2 p = " << load(0, "c0 + " + std::to_string(bit_map_value((int64_t)u << lg, v[0], w, k))) << ";\n";
-      for (int i = 1; i < m; ++i)
-        o << "            p = cmul(p, " << load(i, "c" + std::to_string(i) + " + " +
-                                              std::to_string(bit_map_value((int64_t)u << lg, v[i], w, k)))
-          << ");\n";
-      o << "            a" << (u & 1) << ".x += p.x; a" << (u & 1) << ".y += p.y; }\n";
-    }
-    o << "        }\n";
-    o << "        acc = make_float2((a0.x + a1.x) * comb, (a0.y + a1.y) * comb);\n";
-  } else {
-    o << "#pragma unroll 1\n        for (int t = 0; t < " << (1 << tpt_log) << "; ++t) {\n";
-    for (int i = 0; i < m; ++i)
-      o << "          const int c" << i << " = b" << i << " + "
-        << (tpt_log ? bit_map_expr("t", v[i], w + lg, tpt_log) : std::string("0")) << ";\n";
-    o << "          float2 p = " << load(0, "c0") << ";\n";
-    for (int i = 1; i < m; ++i) o << "          p = cmul(p, " << load(i, "c" + std::to_string(i)) << ");\n";
-    o << "          acc.x += p.x; acc.y += p.y;\n        }\n";
+  // unrolled blocks of 2^unr_log terms: the block's offsets at run time,
+  // the term offsets inside a block as constants; term index
+  // e = (blk << (unr_log + lg)) | (u << lg) | g
+  o << "        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);\n";
+  o << "#pragma unroll 1\n        for (int blk = 0; blk < " << (1 << blk_log) << "; ++blk) {\n";
+  for (int i = 0; i < m; ++i) {
+    const std::string e = blk_log ? bit_map_expr("blk", v[i], w + lg + unr_log, blk_log) : std::string("0");
+    o << "          const int c" << i << " = b" << i << " + " << e << ";\n";
   }
+  for (int u = 0; u < (1 << unr_log); ++u) {
+    o << "          { float2 p = F[c0 + " << bit_map_value((int64_t)u << lg, v[0], w, k) << "];\n";
+    for (int i = 1; i < m; ++i)
+      o << "            p = cmul(p, F[c" << i << " + " << bit_map_value((int64_t)u << lg, v[i], w, k) << "]);\n";
+    o << "            a" << (u & 1) << ".x += p.x; a" << (u & 1) << ".y += p.y; }\n";
+  }
+  o << "        }\n";
+  o << "        acc = make_float2((a0.x + a1.x) * comb, (a0.y + a1.y) * comb);\n";
   o << "      }\n";
-  for (int s = 1; s < tpi; s <<= 1)
-    o << "      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, " << s << "); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, "
-      << s << ");\n";
-  o << "      if (" << (always_live ? "true" : "it < " + std::to_string(items)) << (lg ? " && g == 0" : "") << ") {\n";
-  o << "        F[" << (r.out_soff / 8) << " + it] = acc;\n";
+  for (int s2 = 1; s2 < tpi; s2 <<= 1)
+    o << "      acc.x += __shfl_xor_sync(0xffffffffu, acc.x, " << s2
+      << "); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, " << s2 << ");\n";
+  o << "      if (" << live << (lg ? " && g == 0" : "") << ") {\n";
+  o << "        F[" << ((r.out_soff - shift) / 8) << " + it] = acc;\n";
   o << "        lmax = fmax_nan(lmax, absmax2(acc));\n      }\n";
   o << "    }\n";
 }
@@ -188,6 +172,7 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
   o << kPrelude;
   o << "__device__ __forceinline__ float2 sc(float2 v, float s) { return make_float2(v.x * s, v.y * s); }\n";
   const int logBc = __builtin_ctz(L.chunk);
+  const int64_t shift = worklist_bytes(L);
   o << "extern \"C\" __global__ void __launch_bounds__(256, " << minb << ") " << name
     << "(const char *ws, const RJob *jobs, int n_jobs, const u64 *bits, long long B, double c_re, double c_im, "
        "double2 *out, Header *hdr) {\n";
@@ -209,7 +194,7 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
   o << "      const u64 x = (b0 + b < B) ? bits[b0 + b] : 0ull;\n";
   o << "      ob = jb.n_out == 1 ? (int)((x >> jb.q0) & 1ull) : (int)((((x >> jb.q0) & 1ull) << 1) | ((x >> jb.q1) & 1ull));\n";
   o << "    }\n";
-  o << "    reinterpret_cast<float2 *>(sm + jb.dst)[jb.batched ? b : 0] = __ldg(wsf + jb.src + ob);\n";
+  o << "    reinterpret_cast<float2 *>(sm + jb.dst - " << shift << ")[jb.batched ? b : 0] = __ldg(wsf + jb.src + ob);\n";
   o << "  }\n  __syncthreads();\n";
   int cur_level = 0;
   for (size_t q = 0; q < L.steps.size(); ++q) {
@@ -231,29 +216,30 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
           << ", e, esum); es += e; }\n";
       }
     }
-    o << "    float lm;\n";
+    // scales: one combined factor per entry when the inputs' exponents sum
+    // to a representable power of two; otherwise the intermediate inputs are
+    // rescaled in place first (each feeds this step only) and the factor is 1
     bool any_meta = false;
     for (int i = 0; i < d.m; ++i) any_meta |= r.in[i].meta >= 0;
-    if (!any_meta) {  // leaves only: no scale
-      o << "    const float comb = 1.f;\n";
-      std::ostringstream b;
-      emit_body(b, p, L, q, true);
-      o << "    {\n" << b.str() << "    lm = lmax; }\n";
-    } else {
-    o << "    if (es >= -120 && es <= 120) {\n";
-    o << "      const float comb = __int_as_float((127 - es) << 23);\n";
+    o << "    float comb = 1.f;\n";
+    if (any_meta) {
+      o << "    if (es >= -120 && es <= 120) comb = __int_as_float((127 - es) << 23);\n";
+      o << "    else {\n";
+      for (int i = 0; i < d.m; ++i) {
+        if (r.in[i].meta < 0) continue;
+        const SymTensor &t = p->sim.tensors[p->sim.steps[L.src_step[q]].inputs[i]];
+        const int64_t n = ((int64_t)1 << t.vars.size()) * (t.batched ? L.chunk : 1);
+        o << "      for (int x = gt; x < " << n << "; x += " << 32 * nw << ") { float2 &y = F["
+          << ((r.in[i].soff - shift) / 8) << " + x]; y.x *= s" << i << "; y.y *= s" << i << "; }\n";
+      }
+      if (nw > 1) o << "      asm volatile(\"bar.sync %0, %1;\" :: \"r\"(" << (1 + w0) << "), \"r\"(" << 32 * nw << "));\n";
+      else o << "      __syncwarp();\n";
+      o << "    }\n";
+    }
     {
       std::ostringstream b;
-      emit_body(b, p, L, q, true);
-      o << "    {\n" << b.str() << "    lm = lmax; }\n";
-    }
-    o << "    } else {\n";
-    {
-      std::ostringstream b;
-      emit_body(b, p, L, q, false);
-      o << "    {\n" << b.str() << "    lm = lmax; }\n";
-    }
-    o << "    }\n";
+      emit_body(b, p, L, q, shift);
+      o << "    float lm;\n    {\n" << b.str() << "    lm = lmax; }\n";
     }
     o << "    for (int s = 16; s > 0; s >>= 1) lm = fmax_nan(lm, __shfl_xor_sync(0xffffffffu, lm, s));\n";
     o << "    if (lane == 0) {\n";
@@ -264,7 +250,7 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
   o << "  __syncthreads();\n";
   o << "  if (tid == 0 && ((meta[" << L.final_meta << "].maxbits >> 23) & 0xff) == 0xff) atomicCAS(&hdr->status, 0, -5);\n";
   o << "  if (tid < " << L.chunk << " && b0 + tid < B) {\n";
-  o << "    const float2 v = F[" << (L.final_soff / 8) << (p->final_batched ? " + tid" : "") << "];\n";
+  o << "    const float2 v = F[" << ((L.final_soff - shift) / 8) << (p->final_batched ? " + tid" : "") << "];\n";
   o << "    const double scl = ldexp(1.0, meta[" << L.final_meta << "].exp);\n";
   o << "    const double re = (double)v.x * scl, im = (double)v.y * scl;\n";
   o << "    out[b0 + tid] = make_double2(re * c_re - im * c_im, re * c_im + im * c_re);\n";
