@@ -1074,6 +1074,7 @@ struct qgm_exec_state {
   int kind = QGM_EXEC_STEPWISE;
   int layout = -1;  // index into qgm_plan::resident
   cudaKernel_t jit = nullptr;  // compiled resident kernel (QGM_EXEC_COMPILED)
+  cudaKernel_t jit_pre = nullptr;  // its bitstring-independent part, when split off
   std::string jit_error;       // why the compiled kernel is not used, if so
 };
 
@@ -1199,8 +1200,25 @@ static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, doub
     double cr = c.real(), ci = c.imag();
     Header *hdr = reinterpret_cast<Header *>(x->ws + p->off_header);
     void *args[] = {&ws_c, &jobs, &n_jobs, &d_bits, &Bl, &cr, &ci, &d_out, &hdr};
-    cudaLaunchKernel(reinterpret_cast<const void *>(x->jit), dim3((unsigned)G), dim3(RES_THREADS), args,
-                     (size_t)(L.smem_bytes - worklist_bytes(L)), st);
+    const size_t smem = (size_t)(L.smem_bytes - worklist_bytes(L));
+    if (!x->jit_pre) {
+      cudaLaunchKernel(reinterpret_cast<const void *>(x->jit), dim3((unsigned)G), dim3(RES_THREADS), args, smem, st);
+      return;
+    }
+    // the bitstring-independent part once (one CTA), then the batched part;
+    // the latter may start early and waits for the former's outputs
+    cudaLaunchKernel(reinterpret_cast<const void *>(x->jit_pre), dim3(1), dim3(RES_THREADS), args, smem, st);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)G);
+    cfg.blockDim = dim3(RES_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelExC(&cfg, reinterpret_cast<const void *>(x->jit), args);
     return;
   }
   k_resident<<<(unsigned)G, RES_THREADS, (size_t)L.smem_bytes, st>>>(
@@ -1359,14 +1377,24 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
     }
     if (best_li >= 0) {
       const ResidentLayout &L = p->resident[best_li];
-      const std::string src = resident_source(p, L, "qgm_resident_plan", best_cps);
-      cudaKernel_t k = nullptr;
-      if (jit_kernel(src, "qgm_resident_plan", x->device, &k, &x->jit_error)) {
-        CK(cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)(L.smem_bytes - worklist_bytes(L)), x->device));
+      const int smem = (int)(L.smem_bytes - worklist_bytes(L));
+      // the bitstring-independent steps run once per call in a kernel of
+      // their own when the batch takes two or more waves of CTAs (in one
+      // wave that kernel's latency outweighs what each CTA saves)
+      const bool split = L.split_pre && waves_x_chunk(L, best_cps) >= 2.0 * L.chunk;
+      cudaKernel_t k = nullptr, kp = nullptr;
+      bool ok = jit_kernel(resident_source(p, L, "qgm_resident_plan", best_cps, split ? RES_MAIN : RES_WHOLE),
+                           "qgm_resident_plan", x->device, &k, &x->jit_error);
+      if (ok && split)
+        ok = jit_kernel(resident_source(p, L, "qgm_resident_pre", 1, RES_PRE), "qgm_resident_pre", x->device, &kp,
+                        &x->jit_error);
+      if (ok) {
+        CK(cudaKernelSetAttributeForDevice(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem, x->device));
+        if (kp) CK(cudaKernelSetAttributeForDevice(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem, x->device));
         int rc = upload(L);
         if (rc) return rc;
         x->jit = k;
+        x->jit_pre = kp;
         x->layout = best_li;
         x->kind = QGM_EXEC_COMPILED;
         return QGM_OK;

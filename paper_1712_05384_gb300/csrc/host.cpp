@@ -647,7 +647,10 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       }
     }
     const double fused = (n - 1) * ent(all[full], bat[full]) + ent(res[full], bat[full]) + step_over;
-    if (!(best[full] < 0.8 * fused)) return contract(inputs, summed);
+    // only where it saves a clear share and a sizeable amount of work: small
+    // buckets stay one step (each extra step has a fixed cost)
+    if (!(best[full] < 0.8 * fused) || fused - best[full] < ent(0xfffull, bat[full]))
+      return contract(inputs, summed);
     // emit the tree: a leaf is an input, a node a subset of the inputs; a
     // child is merged into its parent when the parent's union covers it and
     // that is cheaper
@@ -878,6 +881,11 @@ static void build_resident(qgm_plan *p) {
     born[S.steps[si].out] = level[si];
     for (int id : S.steps[si].inputs) dies[id] = level[si];
   }
+  // an output without a batch axis read by a batched step may be staged
+  // before the first level (from the once-per-call part): live from the start
+  for (int si = 0; si < ns; ++si)
+    for (int id : S.steps[si].inputs)
+      if (S.steps[si].batched && id >= nl && !S.tensors[id].batched) born[id] = -1;
   for (int Bc : {1, 2, 4, 8}) {
     ResidentLayout L;
     L.chunk = Bc;
@@ -1042,6 +1050,34 @@ static void build_resident(qgm_plan *p) {
     if (!ok) break;
     if (L.smem_bytes > 200 * 1024) break;  // larger chunks only grow
     p->resident.push_back(L);
+  }
+  // bitstring-independent outputs read by batched steps (the same tensors and
+  // pre-region places in every layout)
+  std::vector<int> consumer(S.tensors.size(), -1);
+  for (int si = 0; si < ns; ++si)
+    for (int id : S.steps[si].inputs) consumer[id] = si;
+  const bool final_batched = S.tensors[S.final_tensor].batched;
+  for (ResidentLayout &L : p->resident) {
+    int64_t goff = 0;
+    for (size_t q = 0; q < L.steps.size(); ++q) {
+      const StepRec &st = S.steps[L.src_step[q]];
+      if (st.batched) continue;
+      const int c = consumer[st.out];
+      if (c < 0 || !S.steps[c].batched) continue;
+      const int64_t n = pow2((int)S.tensors[st.out].vars.size());
+      L.pre.push_back({L.steps[q].out_soff, L.steps[q].out_meta, (int32_t)n, (int32_t)goff});
+      goff += (n + 1) & ~int64_t(1);
+    }
+    L.split_pre = final_batched && !L.pre.empty();
+    if (L.split_pre) {
+      const int64_t meta_b = ((int64_t)L.pre.size() * 8 + 15) & ~int64_t(15);
+      p->pre_data = meta_b / 8;
+      const int64_t need = meta_b + goff * 8;
+      if (p->off_pre == 0) {
+        p->off_pre = p->ws_bytes - 256;
+        p->ws_bytes += (need + 255) & ~int64_t(255);
+      }
+    }
   }
 }
 

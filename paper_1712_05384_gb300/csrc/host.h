@@ -168,6 +168,17 @@ struct ResidentLayout {
   int wlist_soff = 0;       // smem byte offset of the work lists
   int final_soff = -1, final_meta = -1;
   std::vector<int> src_step, level;  // per entry of `steps`: plan step, dependency level
+  // The bitstring-independent part: steps without a batch axis, run once per
+  // call by a one-CTA kernel (compiled executor); `pre` lists their outputs
+  // read by batched steps, staged through the workspace's pre region.
+  struct PreT {
+    int32_t soff;     // smem byte offset in this layout
+    int32_t meta;     // metadata slot
+    int32_t entries;  // complex64 entries
+    int32_t goff;     // float2 index in the pre region's data
+  };
+  std::vector<PreT> pre;
+  bool split_pre = false;  // the compiled executor runs the pre kernel
 };
 
 // Shared-memory bytes of the work lists, which sit between the metadata and
@@ -275,6 +286,8 @@ struct qgm_plan {
   // resident executor layouts for Bc = 1, 2, 4, 8 (empty when infeasible)
   std::vector<qgm::ResidentLayout> resident;
   int64_t off_rsteps = 0;   // workspace region for the chosen layout's steps
+  int64_t off_pre = 0;      // pre region: per pre tensor (maxbits, exp), then the data (16-byte aligned)
+  int64_t pre_data = 0;     // float2 index of the data inside the pre region
   int executor_pref = 0;    // qgm_plan_opts.executor
   bool gemm_ok = true;      // GEMM-shaped steps run by the GEMM kernel
   bool trees_ok = false;    // buckets of three or more inputs may run as contraction trees
@@ -283,6 +296,9 @@ struct qgm_plan {
 
 namespace qgm {
 int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p);
-// CUDA source of the resident kernel specialised to one layout (jit.cpp)
-std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const std::string &name, int minb);
+// CUDA source of the resident kernel specialised to one layout (jit.cpp):
+// the whole pass, its batched part, or its bitstring-independent part
+enum { RES_WHOLE = 0, RES_MAIN = 1, RES_PRE = 2 };
+std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const std::string &name, int minb,
+                            int mode);
 }

@@ -79,8 +79,6 @@ struct RJob { int src; int dst; unsigned char n_out, q0, q1, batched; };
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float fmax_nan(float a, float b) { return (a > b || a != a) ? a : b; }
-__device__ __forceinline__ float absmax2(float2 a) { return fmax_nan(fabsf(a.x), fabsf(a.y)); }
 __device__ __forceinline__ void opscale(const Meta *meta, int slot, Header *hdr, float &s, int &e, int &esum) {
   const unsigned bits = meta[slot].maxbits;
   const int E = (int)((bits >> 23) & 0xff);
@@ -119,7 +117,7 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
   std::vector<std::vector<int64_t>> v(m);
   for (int i = 0; i < m; ++i) v[i] = union_values(d.in[i], U, r.in[i].batched ? L.chunk : 1);
   const std::string live = always_live ? "true" : "it < " + std::to_string(items);
-  o << "    float lmax = 0.f;\n";
+  o << "    unsigned lmax = 0u;\n";
   if (lg) {
     o << "    const int g = gt & " << (tpi - 1) << ";\n";
     for (int i = 0; i < m; ++i) o << "    const int go" << i << " = " << bit_map_expr("g", v[i], w, lg) << ";\n";
@@ -160,19 +158,25 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
       << "); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, " << s2 << ");\n";
   o << "      if (" << live << (lg ? " && g == 0" : "") << ") {\n";
   o << "        F[" << ((r.out_soff - shift) / 8) << " + it] = acc;\n";
-  o << "        lmax = fmax_nan(lmax, absmax2(acc));\n      }\n";
+  o << "        lmax = max(lmax, max(__float_as_uint(acc.x) & 0x7fffffffu, __float_as_uint(acc.y) & 0x7fffffffu));\n      }\n";
   o << "    }\n";
 }
 
 }  // namespace
 
 // CUDA source of the resident kernel specialised to layout L of plan p.
-std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const std::string &name, int minb) {
+// mode RES_WHOLE: the whole pass per CTA.  RES_MAIN: the steps with a batch
+// axis; the bitstring-independent tensors they read come from the pre
+// region, written by the RES_PRE kernel (one CTA running the steps without a
+// batch axis), which the main kernel may overlap up to the point where it
+// waits for them (programmatic dependent launch).
+std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const std::string &name, int minb,
+                            int mode) {
   std::ostringstream o;
   o << kPrelude;
-  o << "__device__ __forceinline__ float2 sc(float2 v, float s) { return make_float2(v.x * s, v.y * s); }\n";
   const int logBc = __builtin_ctz(L.chunk);
   const int64_t shift = worklist_bytes(L);
+  const bool pre = mode == RES_PRE, main_part = mode == RES_MAIN;
   o << "extern \"C\" __global__ void __launch_bounds__(256, " << minb << ") " << name
     << "(const char *ws, const RJob *jobs, int n_jobs, const u64 *bits, long long B, double c_re, double c_im, "
        "double2 *out, Header *hdr) {\n";
@@ -181,28 +185,49 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
   o << "  Meta *meta = reinterpret_cast<Meta *>(sm);\n";
   o << "  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;\n";
   o << "  const long long b0 = (long long)blockIdx.x * " << L.chunk << ";\n";
+  if (pre) o << "  asm volatile(\"griddepcontrol.launch_dependents;\");\n";
   o << "  for (int i = tid; i < " << p->n_meta_fwd << "; i += 256) { meta[i].maxbits = 0u; meta[i].exp = 0; }\n";
   // leaves: one job per leaf row (batched rows select the base entry from
-  // the output bits of x_beta)
+  // the output bits of x_beta); the pre kernel stages the unbatched ones only
   o << "  const float2 *wsf = reinterpret_cast<const float2 *>(ws);\n";
   o << "  for (int t = tid; t < (n_jobs << " << logBc << "); t += 256) {\n";
   o << "    const int b = t & " << (L.chunk - 1) << ";\n";
   o << "    const RJob jb = jobs[t >> " << logBc << "];\n";
-  o << "    if (!jb.batched && b) continue;\n";
+  o << "    if (" << (pre ? "jb.batched || b" : "!jb.batched && b") << ") continue;\n";
   o << "    int ob = 0;\n";
-  o << "    if (jb.n_out) {\n";
-  o << "      const u64 x = (b0 + b < B) ? bits[b0 + b] : 0ull;\n";
-  o << "      ob = jb.n_out == 1 ? (int)((x >> jb.q0) & 1ull) : (int)((((x >> jb.q0) & 1ull) << 1) | ((x >> jb.q1) & 1ull));\n";
-  o << "    }\n";
+  if (!pre) {
+    o << "    if (jb.n_out) {\n";
+    o << "      const u64 x = (b0 + b < B) ? bits[b0 + b] : 0ull;\n";
+    o << "      ob = jb.n_out == 1 ? (int)((x >> jb.q0) & 1ull) : (int)((((x >> jb.q0) & 1ull) << 1) | ((x >> jb.q1) & 1ull));\n";
+    o << "    }\n";
+  }
   o << "    reinterpret_cast<float2 *>(sm + jb.dst - " << shift << ")[jb.batched ? b : 0] = __ldg(wsf + jb.src + ob);\n";
-  o << "  }\n  __syncthreads();\n";
-  int cur_level = 0;
+  o << "  }\n";
+  if (main_part) {
+    // the pre kernel's outputs and their scales, once it has finished
+    o << "  __syncthreads();\n";
+    o << "  asm volatile(\"griddepcontrol.wait;\" ::: \"memory\");\n";
+    o << "  {\n    const float2 *pd = reinterpret_cast<const float2 *>(ws + " << p->off_pre << ") + " << p->pre_data
+      << ";\n";
+    o << "    const int2 *pm = reinterpret_cast<const int2 *>(ws + " << p->off_pre << ");\n";
+    for (size_t j = 0; j < L.pre.size(); ++j) {
+      const auto &t = L.pre[j];
+      o << "    for (int x = tid; x < " << t.entries << "; x += 256) F[" << ((t.soff - shift) / 8) << " + x] = pd["
+        << t.goff << " + x];\n";
+      o << "    if (tid == " << (j % 256) << ") { const int2 v = pm[" << j << "]; meta[" << t.meta
+        << "].maxbits = (unsigned)v.x; meta[" << t.meta << "].exp = v.y; }\n";
+    }
+    o << "  }\n";
+  }
+  o << "  __syncthreads();\n";
+  int cur_level = -1;
   for (size_t q = 0; q < L.steps.size(); ++q) {
+    const RStep &r = L.steps[q];
+    if ((pre && r.batched_out) || (main_part && !r.batched_out)) continue;
     if (L.level[q] != cur_level) {
-      o << "  __syncthreads();\n";
+      if (cur_level >= 0) o << "  __syncthreads();\n";
       cur_level = L.level[q];
     }
-    const RStep &r = L.steps[q];
     const StepDesc &d = p->steps[L.src_step[q]];
     const int w0 = r.sched & 15, nw = (r.sched >> 4) & 15;
     o << "  // step " << L.src_step[q] << ": " << d.m << " inputs, " << d.k << " summed, " << d.w_out
@@ -239,15 +264,32 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
     {
       std::ostringstream b;
       emit_body(b, p, L, q, shift);
-      o << "    float lm;\n    {\n" << b.str() << "    lm = lmax; }\n";
+      o << "    unsigned lm;\n    {\n" << b.str() << "    lm = lmax; }\n";
     }
-    o << "    for (int s = 16; s > 0; s >>= 1) lm = fmax_nan(lm, __shfl_xor_sync(0xffffffffu, lm, s));\n";
+    // max |re|,|im| over the step's entries: non-negative floats (and NaN,
+    // which must reach the maximum) order like their bit patterns
+    o << "    lm = __reduce_max_sync(0xffffffffu, lm);\n";
     o << "    if (lane == 0) {\n";
-    o << "      if (lm > 0.f || lm != lm) atomicMax(&meta[" << r.out_meta << "].maxbits, __float_as_uint(lm));\n";
+    o << "      if (lm) atomicMax(&meta[" << r.out_meta << "].maxbits, lm);\n";
     o << "      if (wid == " << w0 << ") meta[" << r.out_meta << "].exp = esum;\n";
     o << "    }\n  }\n";
   }
   o << "  __syncthreads();\n";
+  if (pre) {
+    // publish the outputs read by batched steps, with their scales
+    o << "  {\n    float2 *pd = reinterpret_cast<float2 *>(const_cast<char *>(ws) + " << p->off_pre << ") + "
+      << p->pre_data << ";\n";
+    o << "    int2 *pm = reinterpret_cast<int2 *>(const_cast<char *>(ws) + " << p->off_pre << ");\n";
+    for (size_t j = 0; j < L.pre.size(); ++j) {
+      const auto &t = L.pre[j];
+      o << "    for (int x = tid; x < " << t.entries << "; x += 256) pd[" << t.goff << " + x] = F["
+        << ((t.soff - shift) / 8) << " + x];\n";
+      o << "    if (tid == " << (j % 256) << ") pm[" << j << "] = make_int2((int)meta[" << t.meta << "].maxbits, meta["
+        << t.meta << "].exp);\n";
+    }
+    o << "  }\n}\n";
+    return o.str();
+  }
   o << "  if (tid == 0 && ((meta[" << L.final_meta << "].maxbits >> 23) & 0xff) == 0xff) atomicCAS(&hdr->status, 0, -5);\n";
   o << "  if (tid < " << L.chunk << " && b0 + tid < B) {\n";
   o << "    const float2 v = F[" << ((L.final_soff - shift) / 8) << (p->final_batched ? " + tid" : "") << "];\n";

@@ -337,3 +337,14 @@ def test_contraction_trees_grid5x5_d20_sampled():
     idx = np.linspace(0, 1023, 24).astype(int)
     rel, ab = errors(a[idx], ve.amplitudes(c, bits[idx]), c.n)
     assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+def test_compiled_many_waves_runs_shared_part_once():
+    # 4x4 depth 12 with 3000 bitstrings: several waves of one-bitstring CTAs,
+    # so the compiled executor runs the steps without a batch axis once per
+    # call in a kernel of their own, whose outputs every CTA reads
+    c = qi.grid_circuit(4, 4, 12, 8)
+    a, bits, p = run_batch(c, 3000, executor=3)
+    assert p.executor()[:2] == (3, 1)
+    rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
