@@ -189,6 +189,8 @@ typedef struct {
   double max_step_bytes;      /* algorithmic bytes of the largest step */
   int32_t n_gemm_steps;       /* steps run by the tiled GEMM kernel */
   int32_t n_tile_steps;       /* batched steps run with a register tile */
+  int32_t n_nested_steps;     /* steps whose compiled form sums some variables
+                                 in an inner loop over part of the inputs */
 } qgm_plan_info;
 
 /* Elimination order, slicing, step list and memory layout (Sec. IV, App. A).

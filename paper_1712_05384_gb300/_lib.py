@@ -54,7 +54,8 @@ class qgm_plan_info(C.Structure):
                 ("n_slices", C.c_int64), ("max_tensor_entries", C.c_int64),
                 ("workspace_bytes", C.c_int64), ("arena_bytes", C.c_int64),
                 ("bytes_per_slice", C.c_double), ("flops_per_slice", C.c_double),
-                ("max_step_bytes", C.c_double), ("n_gemm_steps", C.c_int32), ("n_tile_steps", C.c_int32)]
+                ("max_step_bytes", C.c_double), ("n_gemm_steps", C.c_int32), ("n_tile_steps", C.c_int32),
+                ("n_nested_steps", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -480,12 +480,14 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     place((int)T.size() - 1);
   }
   const bool trees = p->trees_ok;
+  const bool nest = p->nest_ok;
   int n_meta = 0;
   auto by_pos = [&](int a, int b) { return pos[a] < pos[b]; };
   // One step: out = sum over `summed` of the product of the inputs.  The
   // step's union lists the summed variables first, then the kept ones, each
   // in elimination order; the output keeps the kept ones in that order.
-  auto emit = [&](std::vector<int> inputs, std::vector<int> summed, bool gemm = false) -> int {
+  auto emit = [&](std::vector<int> inputs, std::vector<int> summed, bool gemm = false, int k_inner = 0,
+                  std::vector<char> inner = {}) -> int {
     std::vector<int> all;
     bool batched = false;
     for (int id : inputs) {
@@ -494,10 +496,13 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     }
     std::sort(all.begin(), all.end(), by_pos);
     all.erase(std::unique(all.begin(), all.end()), all.end());
-    std::sort(summed.begin(), summed.end(), by_pos);
+    // summed variables in elimination order; a nested step keeps its inner
+    // ones (the last k_inner) after the outer ones
+    std::sort(summed.begin(), summed.end() - k_inner, by_pos);
+    std::sort(summed.end() - k_inner, summed.end(), by_pos);
     std::vector<int> uni = summed;
     for (int v : all)
-      if (!std::binary_search(summed.begin(), summed.end(), v, by_pos)) uni.push_back(v);
+      if (std::find(summed.begin(), summed.end(), v) == summed.end()) uni.push_back(v);
     const int k = (int)summed.size();
     SymTensor out;
     out.vars.assign(uni.begin() + k, uni.end());
@@ -526,8 +531,14 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
     int oid = (int)T.size() - 1;
     s.out = oid;
     s.gemm = gemm;
-    if (want_steps) R.steps.push_back(s);
-    else R.steps.push_back(StepRec{{}, {}, k, oid, batched, s.bytes, s.flops, gemm});
+    s.k_inner = k_inner;
+    s.inner = inner;
+    if (!want_steps) {
+      s.inputs.clear();
+      s.uni.clear();
+      s.inner.clear();
+    }
+    R.steps.push_back(s);
     return oid;
   };
   // an intermediate consumed inside the same bucket holds its variables live
@@ -590,6 +601,89 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
         auto premul = [&](std::vector<int> &grp) { return grp.size() == 1 ? grp[0] : hold(emit(grp, {})); };
         const int a2 = premul(toA), b2 = premul(toB);
         return emit({a2, b2}, summed, true);
+      }
+    }
+    if (nest && inputs.size() >= 3 && k >= 2) {
+      // Nested product-sum: split the inputs into an inner group G2 and an
+      // outer group G1 so that the summed variables held by G2 only (K2) are
+      // summed in an inner loop: sum_K1 prod(G1) * sum_K2 prod(G2).  Inputs
+      // inside the largest member of their group are multiplied into it
+      // first.  Cost per output entry, in complex products:
+      // 2^|K1| (2^|K2| m2 + m1) against 2^|K| m for the flat product-sum.
+      const int n = (int)inputs.size();
+      int64_t out_vars = 0;
+      std::vector<int> allv;
+      for (int id : inputs)
+        for (int v : T[id].vars)
+          if (std::find(allv.begin(), allv.end(), v) == allv.end()) allv.push_back(v);
+      out_vars = (int64_t)allv.size() - k;
+      bool bat = false;
+      for (int id : inputs) bat |= T[id].batched;
+      const double bf = bat ? (double)Bp : 1.0;
+      auto group_plan = [&](const std::vector<int> &grp, std::vector<std::vector<int>> &parts) {
+        // members inside the group's largest member are multiplied into it
+        parts.clear();
+        if (grp.empty()) return 0.0;
+        int big = grp[0];
+        for (int id : grp)
+          if (T[id].vars.size() > T[big].vars.size()) big = id;
+        std::vector<int> into = {big};
+        for (int id : grp) {
+          if (id == big) continue;
+          bool inside = true;
+          for (int v : T[id].vars) inside = inside && holds(big, v);
+          if (inside) into.push_back(id);
+          else parts.push_back({id});
+        }
+        parts.insert(parts.begin(), into);
+        return into.size() > 1 ? std::ldexp(bf, (int)T[big].vars.size()) * (double)into.size() : 0.0;
+      };
+      const double flat = std::ldexp(bf, (int)(out_vars + k)) * n;
+      double best = 0.7 * flat;
+      int best_mask = 0;
+      for (int mask = 1; mask < (1 << n) - 1; ++mask) {
+        std::vector<int> g1, g2;
+        for (int i = 0; i < n; ++i) ((mask >> i) & 1 ? g2 : g1).push_back(inputs[i]);
+        int k2 = 0;
+        for (int v : summed) {
+          bool in1 = false, in2 = false;
+          for (int id : g1) in1 = in1 || holds(id, v);
+          for (int id : g2) in2 = in2 || holds(id, v);
+          k2 += in2 && !in1;
+        }
+        if (k2 == 0 || k2 == k) continue;
+        std::vector<std::vector<int>> p1, p2;
+        const double pre = group_plan(g1, p1) + group_plan(g2, p2);
+        const double cost =
+            std::ldexp(bf, (int)(out_vars + k - k2)) * ((double)((int64_t)1 << k2) * (double)p2.size() + (double)p1.size()) +
+            pre;
+        if (cost < best && flat - cost >= std::ldexp(bf, 12)) {
+          best = cost;
+          best_mask = mask;
+        }
+      }
+      if (best_mask) {
+        std::vector<int> g1, g2;
+        for (int i = 0; i < n; ++i) ((best_mask >> i) & 1 ? g2 : g1).push_back(inputs[i]);
+        std::vector<int> k1v, k2v;
+        for (int v : summed) {
+          bool in1 = false;
+          for (int id : g1) in1 = in1 || holds(id, v);
+          (in1 ? k1v : k2v).push_back(v);
+        }
+        std::vector<std::vector<int>> p1, p2;
+        group_plan(g1, p1);
+        group_plan(g2, p2);
+        std::vector<int> ins;
+        std::vector<char> inner;
+        for (int side = 0; side < 2; ++side)
+          for (auto &part : side ? p2 : p1) {
+            ins.push_back(part.size() == 1 ? part[0] : hold(emit(part, {})));
+            inner.push_back((char)side);
+          }
+        std::vector<int> sm = k1v;
+        sm.insert(sm.end(), k2v.begin(), k2v.end());
+        return emit(ins, sm, false, (int)k2v.size(), inner);
       }
     }
     return emit(inputs, summed);
@@ -1108,6 +1202,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   const int max_fuse = o.max_fuse > 0 ? std::min(o.max_fuse, 16) : 8;
   p->gemm_ok = o.no_gemm == 0;
   p->trees_ok = o.trees != 0;
+  p->nest_ok = true;
   const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)64 << 30;
 
   reduce_factors(m, p->leaves, p->constant, p->half_pow_total);
@@ -1770,6 +1865,8 @@ int qgm_plan_get_info(const qgm_plan *p, qgm_plan_info *info) {
   info->n_gemm_steps = (int32_t)p->gemms.size();
   info->n_tile_steps = 0;
   for (const StepDesc &d : p->steps) info->n_tile_steps += d.tile_t > 0;
+  info->n_nested_steps = 0;
+  for (const StepRec &st : p->sim.steps) info->n_nested_steps += st.k_inner > 0;
   return QGM_OK;
 }
 

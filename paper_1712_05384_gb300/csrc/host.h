@@ -214,6 +214,11 @@ struct StepRec {
   bool batched = false;
   double bytes = 0, flops = 0;
   bool gemm = false;        // two operands, run by the GEMM kernel
+  // nested evaluation (compiled resident kernel): the last k_inner summed
+  // variables occur only in the inputs flagged inner, so
+  // out = sum_outer prod(outer inputs) * sum_inner prod(inner inputs)
+  int k_inner = 0;
+  std::vector<char> inner;
 };
 
 struct LeafFactor {          // merged factor after fixing the inputs
@@ -291,6 +296,7 @@ struct qgm_plan {
   int executor_pref = 0;    // qgm_plan_opts.executor
   bool gemm_ok = true;      // GEMM-shaped steps run by the GEMM kernel
   bool trees_ok = false;    // buckets of three or more inputs may run as contraction trees
+  bool nest_ok = true;      // buckets may be marked for nested evaluation
   qgm_exec_state *exec = nullptr;
 };
 

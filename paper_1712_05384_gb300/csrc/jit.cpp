@@ -117,10 +117,16 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
   std::vector<std::vector<int64_t>> v(m);
   for (int i = 0; i < m; ++i) v[i] = union_values(d.in[i], U, r.in[i].batched ? L.chunk : 1);
   const std::string live = always_live ? "true" : "it < " + std::to_string(items);
+  // nested evaluation: the lanes of an entry split the outer terms, each
+  // lane runs all 2^k2 inner terms per outer term
+  const StepRec &st = p->sim.steps[L.src_step[q]];
+  const int k2 = st.k_inner, k1 = k - k2;
+  const bool nested = k2 > 0 && k2 <= 4 && lg <= k1 && (int)st.inner.size() == m;
+  const int glo = nested ? w + k2 : w;  // union bit of the lane index's bit 0
   o << "    unsigned lmax = 0u;\n";
   if (lg) {
     o << "    const int g = gt & " << (tpi - 1) << ";\n";
-    for (int i = 0; i < m; ++i) o << "    const int go" << i << " = " << bit_map_expr("g", v[i], w, lg) << ";\n";
+    for (int i = 0; i < m; ++i) o << "    const int go" << i << " = " << bit_map_expr("g", v[i], glo, lg) << ";\n";
   }
   o << "#pragma unroll 1\n    for (int j = 0; j < " << n_iter << "; ++j) {\n";
   o << "      const int it = (gt >> " << lg << ") + j * " << sit << ";\n";
@@ -135,6 +141,41 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
     if (lg) o << " + go" << i;
     o << ";\n";
   }
+  if (nested) {
+    // term index e = (e1 << k2) | e2 with e1 = (blk << (u1_log + lg)) | (u1 << lg) | g
+    const int u2n = 1 << k2;
+    const int u1_log = std::min(k1 - lg, std::max(0, 4 - k2));
+    const int blk_log1 = k1 - lg - u1_log;
+    o << "        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);\n";
+    o << "#pragma unroll 1\n        for (int blk = 0; blk < " << (1 << blk_log1) << "; ++blk) {\n";
+    for (int i = 0; i < m; ++i) {
+      const std::string e = blk_log1 ? bit_map_expr("blk", v[i], w + k2 + lg + u1_log, blk_log1) : std::string("0");
+      o << "          const int c" << i << " = b" << i << " + " << e << ";\n";
+    }
+    for (int u1 = 0; u1 < (1 << u1_log); ++u1) {
+      o << "          { float2 i0 = make_float2(0.f, 0.f), i1 = make_float2(0.f, 0.f);\n";
+      for (int u2 = 0; u2 < u2n; ++u2) {
+        const int64_t e = ((int64_t)u1 << (lg + k2)) | u2;
+        bool first = true;
+        o << "            { float2 p = ";
+        for (int i = 0; i < m; ++i) {
+          if (!st.inner[i]) continue;
+          const std::string ld = "F[c" + std::to_string(i) + " + " + std::to_string(bit_map_value(e, v[i], w, k)) + "]";
+          if (first) o << ld << ";\n";
+          else o << "              p = cmul(p, " << ld << ");\n";
+          first = false;
+        }
+        o << "              i" << (u2 & 1) << ".x += p.x; i" << (u2 & 1) << ".y += p.y; }\n";
+      }
+      o << "            float2 p = make_float2(i0.x + i1.x, i0.y + i1.y);\n";
+      const int64_t e = (int64_t)u1 << (lg + k2);
+      for (int i = 0; i < m; ++i)
+        if (!st.inner[i])
+          o << "            p = cmul(p, F[c" << i << " + " << bit_map_value(e, v[i], w, k) << "]);\n";
+      o << "            a" << (u1 & 1) << ".x += p.x; a" << (u1 & 1) << ".y += p.y; }\n";
+    }
+    o << "        }\n";
+  } else {
   // unrolled blocks of 2^unr_log terms: the block's offsets at run time,
   // the term offsets inside a block as constants; term index
   // e = (blk << (unr_log + lg)) | (u << lg) | g
@@ -151,6 +192,7 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
     o << "            a" << (u & 1) << ".x += p.x; a" << (u & 1) << ".y += p.y; }\n";
   }
   o << "        }\n";
+  }
   o << "        acc = make_float2((a0.x + a1.x) * comb, (a0.y + a1.y) * comb);\n";
   o << "      }\n";
   for (int s2 = 1; s2 < tpi; s2 <<= 1)
