@@ -19,6 +19,7 @@
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <map>
@@ -232,6 +233,8 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
   // leaves: one job per leaf row (batched rows select the base entry from
   // the output bits of x_beta); the pre kernel stages the unbatched ones only
   o << "  const float2 *wsf = reinterpret_cast<const float2 *>(ws);\n";
+  if (L.chunk == 1 && !pre) o << "  const u64 x1 = b0 < B ? __ldg(bits + b0) : 0ull;\n";
+  o << "#pragma unroll 4\n";
   o << "  for (int t = tid; t < (n_jobs << " << logBc << "); t += 256) {\n";
   o << "    const int b = t & " << (L.chunk - 1) << ";\n";
   o << "    const RJob jb = jobs[t >> " << logBc << "];\n";
@@ -239,7 +242,8 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
   o << "    int ob = 0;\n";
   if (!pre) {
     o << "    if (jb.n_out) {\n";
-    o << "      const u64 x = (b0 + b < B) ? bits[b0 + b] : 0ull;\n";
+    if (L.chunk == 1) o << "      const u64 x = x1;\n";
+    else o << "      const u64 x = (b0 + b < B) ? bits[b0 + b] : 0ull;\n";
     o << "      ob = jb.n_out == 1 ? (int)((x >> jb.q0) & 1ull) : (int)((((x >> jb.q0) & 1ull) << 1) | ((x >> jb.q1) & 1ull));\n";
     o << "    }\n";
   }
@@ -262,8 +266,16 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
     o << "  }\n";
   }
   o << "  __syncthreads();\n";
+  // steps in level order; inside a level grouped by first warp, so that
+  // each warp's code for the level is contiguous
+  std::vector<size_t> emit_order(L.steps.size());
+  for (size_t q = 0; q < emit_order.size(); ++q) emit_order[q] = q;
+  std::stable_sort(emit_order.begin(), emit_order.end(), [&](size_t a, size_t b) {
+    if (L.level[a] != L.level[b]) return L.level[a] < L.level[b];
+    return (L.steps[a].sched & 15) < (L.steps[b].sched & 15);
+  });
   int cur_level = -1;
-  for (size_t q = 0; q < L.steps.size(); ++q) {
+  for (size_t q : emit_order) {
     const RStep &r = L.steps[q];
     if ((pre && r.batched_out) || (main_part && !r.batched_out)) continue;
     if (L.level[q] != cur_level) {
