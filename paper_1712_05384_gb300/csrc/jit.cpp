@@ -80,6 +80,13 @@ struct RJob { int src; int dst; unsigned char n_out, q0, q1, batched; };
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+// a += x * y (complex), as four fused multiply-adds
+__device__ __forceinline__ void cmac(float2 &a, float2 x, float2 y) {
+  a.x = fmaf(x.x, y.x, a.x);
+  a.x = fmaf(-x.y, y.y, a.x);
+  a.y = fmaf(x.x, y.y, a.y);
+  a.y = fmaf(x.y, y.x, a.y);
+}
 __device__ __forceinline__ void opscale(const Meta *meta, int slot, Header *hdr, float &s, int &e, int &esum) {
   const unsigned bits = meta[slot].maxbits;
   const int E = (int)((bits >> 23) & 0xff);
@@ -96,6 +103,19 @@ __device__ __forceinline__ void opscale(const Meta *meta, int slot, Header *hdr,
 )";
 
 constexpr int kUnroll = 16;  // terms per unrolled block
+
+// "acc += f0 * f1 * ... " for the given operand expressions: products in a
+// chain, the last factor fused into the accumulation
+void emit_term(std::ostringstream &o, const std::vector<std::string> &f, const std::string &acc,
+               const std::string &ind) {
+  if (f.size() == 1) {
+    o << ind << "{ const float2 p = " << f[0] << "; " << acc << ".x += p.x; " << acc << ".y += p.y; }\n";
+    return;
+  }
+  o << ind << "{ float2 p = " << f[0] << ";\n";
+  for (size_t i = 1; i + 1 < f.size(); ++i) o << ind << "  p = cmul(p, " << f[i] << ");\n";
+  o << ind << "  cmac(" << acc << ", p, " << f.back() << "); }\n";
+}
 
 // One step's body for the threads of its warps (gt = thread index in the
 // group): every item's product-sum with raw operand values, times `comb`
@@ -157,23 +177,17 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
       o << "          { float2 i0 = make_float2(0.f, 0.f), i1 = make_float2(0.f, 0.f);\n";
       for (int u2 = 0; u2 < u2n; ++u2) {
         const int64_t e = ((int64_t)u1 << (lg + k2)) | u2;
-        bool first = true;
-        o << "            { float2 p = ";
-        for (int i = 0; i < m; ++i) {
-          if (!st.inner[i]) continue;
-          const std::string ld = "F[c" + std::to_string(i) + " + " + std::to_string(bit_map_value(e, v[i], w, k)) + "]";
-          if (first) o << ld << ";\n";
-          else o << "              p = cmul(p, " << ld << ");\n";
-          first = false;
-        }
-        o << "              i" << (u2 & 1) << ".x += p.x; i" << (u2 & 1) << ".y += p.y; }\n";
+        std::vector<std::string> f;
+        for (int i = 0; i < m; ++i)
+          if (st.inner[i]) f.push_back("F[c" + std::to_string(i) + " + " + std::to_string(bit_map_value(e, v[i], w, k)) + "]");
+        emit_term(o, f, "i" + std::to_string(u2 & 1), "            ");
       }
-      o << "            float2 p = make_float2(i0.x + i1.x, i0.y + i1.y);\n";
       const int64_t e = (int64_t)u1 << (lg + k2);
+      std::vector<std::string> f = {"make_float2(i0.x + i1.x, i0.y + i1.y)"};
       for (int i = 0; i < m; ++i)
-        if (!st.inner[i])
-          o << "            p = cmul(p, F[c" << i << " + " << bit_map_value(e, v[i], w, k) << "]);\n";
-      o << "            a" << (u1 & 1) << ".x += p.x; a" << (u1 & 1) << ".y += p.y; }\n";
+        if (!st.inner[i]) f.push_back("F[c" + std::to_string(i) + " + " + std::to_string(bit_map_value(e, v[i], w, k)) + "]");
+      emit_term(o, f, "a" + std::to_string(u1 & 1), "            ");
+      o << "          }\n";
     }
     o << "        }\n";
   } else {
@@ -187,10 +201,10 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
     o << "          const int c" << i << " = b" << i << " + " << e << ";\n";
   }
   for (int u = 0; u < (1 << unr_log); ++u) {
-    o << "          { float2 p = F[c0 + " << bit_map_value((int64_t)u << lg, v[0], w, k) << "];\n";
-    for (int i = 1; i < m; ++i)
-      o << "            p = cmul(p, F[c" << i << " + " << bit_map_value((int64_t)u << lg, v[i], w, k) << "]);\n";
-    o << "            a" << (u & 1) << ".x += p.x; a" << (u & 1) << ".y += p.y; }\n";
+    std::vector<std::string> f;
+    for (int i = 0; i < m; ++i)
+      f.push_back("F[c" + std::to_string(i) + " + " + std::to_string(bit_map_value((int64_t)u << lg, v[i], w, k)) + "]");
+    emit_term(o, f, "a" + std::to_string(u & 1), "          ");
   }
   o << "        }\n";
   }
