@@ -18,9 +18,15 @@ the caller.
   |Q(S-v, v)|) (Bodlaender, Fomin, Koster, Kratsch, Thilikos 2006); small
   graphs only, used to pin the heuristics from below.
 * ``line_graph``: App. E's construction.
-Parity: pinned (App. D example width 2, App. E line graph width 4, chains,
+* ``tensor_network``: App. E's tensor network of a circuit, one tensor per
+  gate, as its wire segments between two gates (the segments to the fixed
+  input and output vectors are fixed indices and drop out, as the boundary
+  variables do in ``graph``).
+Parity: pinned (App. D example width 2, App. E line graph width 4 -- from the
+printed graph and from the App. D circuit's tensor network --, chains,
 cycles, trees and cliques against their known treewidths, exact DP as a lower
-bound; tests/test_oracle_order.py).
+bound, the interaction graph a minor of the line graph so never wider;
+tests/test_oracle_order.py).
 """
 from itertools import combinations
 
@@ -162,3 +168,16 @@ def line_graph(edges):
             adj[i].add(j)
             adj[j].add(i)
     return adj
+
+
+def tensor_network(circuit):
+    """Wire segments between two gates as (producer, consumer) gate indices,
+    in the order their consumers close them (gate order, first qubit first)."""
+    last = {}
+    edges = []
+    for gi, g in enumerate(circuit.gates):
+        for q in ([g.q0] if g.q1 < 0 else [g.q0, g.q1]):
+            if q in last:
+                edges.append((last[q], gi))
+            last[q] = gi
+    return edges

@@ -102,3 +102,37 @@ def test_vertical_order_is_lexicographic():
     keys = [(rank[m.var_qubit[v]], m.var_k[v]) for v in order]
     assert keys == sorted(keys)
     assert O.qubit_rank(3, 3) == list(range(9))
+
+
+def test_app_d_tensor_network_line_graph_width_4(app_d):
+    # App. E: the App. D circuit as a tensor network; its line graph is the
+    # 4-clique of the CZ's segments (width 4, against 2 for the graphical model)
+    tn = O.tensor_network(app_d)
+    assert tn == [(0, 2), (1, 2), (2, 3), (2, 4)]
+    lg = O.line_graph(tn)
+    assert O.treewidth_exact(lg) + 1 == 4
+    assert O.min_fill(lg)[1] == 4
+
+
+def test_tensor_network_segments_and_chain():
+    # one qubit, k gates: k - 1 segments, a path (width 2); segment count is
+    # the sum over qubits of (gates on the qubit - 1)
+    G = qi.Gate
+    chain = qi.circuit_from_gates(1, [G(qi.GATE_H, t, 0) for t in range(6)])
+    lg = O.line_graph(O.tensor_network(chain))
+    assert len(lg) == 5 and O.treewidth_exact(lg) + 1 == 2
+    c = qi.grid_circuit(3, 3, 9, 1)
+    per_q = [sum(1 for g in c.gates if q in (g.q0, g.q1)) for q in range(c.n)]
+    assert len(O.tensor_network(c)) == sum(k - 1 for k in per_q)
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed", [(2, 2, 6, 0), (2, 3, 5, 1), (1, 4, 8, 2)])
+def test_graphical_model_never_wider_than_line_graph(rows, cols, depth, seed):
+    # the interaction graph is a minor of the line graph (segments joined by
+    # diagonal gates are one variable), so its treewidth is never larger
+    c = qi.grid_circuit(rows, cols, depth, seed)
+    ugm_g = O.graph(ugm.build(c))
+    lg = O.line_graph(O.tensor_network(c))
+    if len(lg) > 18:
+        pytest.skip("exact treewidth too slow")
+    assert O.treewidth_exact(ugm_g) <= O.treewidth_exact(lg)
