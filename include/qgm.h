@@ -91,6 +91,16 @@ int qgm_circuit_gates(const qgm_circuit *c, qgm_gate *gates, int64_t cap, int64_
  * parameter order of qgm_amplitude_grad (theta_p at 2p, phi_p at 2p+1). */
 int qgm_circuit_param_gates(const qgm_circuit *c, int32_t *idx, int64_t cap, int64_t *n);
 
+/* Ordering study (Sec. IV.B, App. E, Fig. 6): the line graph of the
+ * circuit's tensor network -- one vertex per wire segment between two gates
+ * (segments to the fixed input and output vectors are fixed indices and drop
+ * out), a clique per gate over its segments -- eliminated in min-fill order
+ * (ties: fewest neighbours, then lowest segment number; segments numbered in
+ * the order their consumer gates close them).  *max_clique: the largest
+ * clique along that order (treewidth bound = *max_clique - 1);
+ * *n_segments (may be NULL): vertices.  Errors: QGM_ERR_ARG. */
+int qgm_circuit_line_graph_width(const qgm_circuit *c, int32_t *n_segments, int32_t *max_clique);
+
 void qgm_circuit_free(qgm_circuit *c);
 
 /* ------------------------------------------------------------------ model */

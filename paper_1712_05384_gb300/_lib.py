@@ -71,6 +71,7 @@ _SIGS = {
     "qgm_circuit_from_gates": [C.c_int, C.POINTER(qgm_gate), C.c_int64, C.POINTER(_P)],
     "qgm_circuit_gates": [_P, C.POINTER(qgm_gate), C.c_int64, _I64P],
     "qgm_circuit_param_gates": [_P, _I32P, C.c_int64, _I64P],
+    "qgm_circuit_line_graph_width": [_P, _I32P, _I32P],
     "qgm_circuit_free": [_P],
     "qgm_build_model": [_P, C.POINTER(_P)],
     "qgm_model_get_info": [_P, C.POINTER(qgm_model_info)],
@@ -183,6 +184,13 @@ class Circuit:
         a = np.zeros(max(n.value, 1), dtype=np.int32)
         check(lib().qgm_circuit_param_gates(self._h, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
         return a[: n.value]
+
+    def line_graph_width(self):
+        """(segments, max clique) of the min-fill order on the line graph of
+        the circuit's tensor network (App. E)."""
+        ns, w = C.c_int32(), C.c_int32()
+        check(lib().qgm_circuit_line_graph_width(self._h, C.byref(ns), C.byref(w)))
+        return ns.value, w.value
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

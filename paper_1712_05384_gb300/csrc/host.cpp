@@ -1774,6 +1774,46 @@ int qgm_circuit_param_gates(const qgm_circuit *c, int32_t *idx, int64_t cap, int
   return QGM_OK;
 }
 
+// App. E: the circuit as a tensor network, one tensor per gate.  Its wire
+// segments between two gates are the vertices of the line graph, numbered in
+// the order their consumers close them (gate order, first qubit first);
+// segments sharing a gate are adjacent (a clique per gate).  Segments to the
+// fixed input and output vectors are fixed indices and drop out, as the
+// boundary variables do in the graphical model.
+int qgm_circuit_line_graph_width(const qgm_circuit *c, int32_t *n_segments, int32_t *max_clique) {
+  if (!c || !max_clique) {
+    set_error("qgm_circuit_line_graph_width: null argument");
+    return QGM_ERR_ARG;
+  }
+  const Circuit &C = c->c;
+  std::vector<int> last(C.n, -1);
+  std::vector<std::vector<int>> at_gate(C.gates.size());
+  int ns = 0;
+  for (size_t gi = 0; gi < C.gates.size(); ++gi) {
+    const qgm_gate &g = C.gates[gi];
+    for (int q : {g.q0, g.q1}) {
+      if (q < 0 || q >= C.n || (q == g.q1 && g.q1 == g.q0)) continue;
+      if (last[q] >= 0) {
+        at_gate[last[q]].push_back(ns);
+        at_gate[gi].push_back(ns);
+        ++ns;
+      }
+      last[q] = (int)gi;
+    }
+  }
+  Graph g(ns);
+  for (int v = 0; v < ns; ++v) g.alive[v] = 1;
+  for (const auto &segs : at_gate)
+    for (size_t a = 0; a < segs.size(); ++a)
+      for (size_t b = a + 1; b < segs.size(); ++b) g.add(segs[a], segs[b]);
+  const std::vector<int> order = order_minfill(g, std::vector<char>(ns, 0));
+  int w = 0;
+  for (int v : order) w = std::max(w, g.eliminate(v));
+  if (n_segments) *n_segments = ns;
+  *max_clique = w;
+  return QGM_OK;
+}
+
 void qgm_circuit_free(qgm_circuit *c) { delete c; }
 
 int qgm_build_model(const qgm_circuit *c, qgm_model **out) {

@@ -176,3 +176,29 @@ def test_nested_steps_keep_the_product_sum():
     assert p.info.n_nested_steps >= 2
     st = p.steps()
     assert st["k"].sum() == p.info.n_free
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed", [(3, 3, 8, 0), (4, 4, 12, 1), (3, 5, 16, 2),
+                                                  (2, 6, 10, 3)])
+def test_line_graph_width_bit_exact(rows, cols, depth, seed):
+    # App. E (ordering study, Fig. 6): the planner's line graph of the
+    # circuit's tensor network and its min-fill width equal the oracle's
+    c = qi.grid_circuit(rows, cols, depth, seed)
+    edges = O.tensor_network(c)
+    ref = O.min_fill(O.line_graph(edges))[1]
+    ns, w = Q.Circuit.grid(rows, cols, depth, seed).line_graph_width()
+    assert ns == len(edges) and w == ref
+
+
+def test_line_graph_width_app_d(app_d):
+    c = Q.Circuit.from_gates(2, app_d.gates)
+    assert c.line_graph_width() == (4, 4)
+
+
+def test_ordering_study_rows():
+    from paper_1712_05384_gb300 import study
+    r = study.widths(4, 4, 12)
+    m = Q.Model(Q.Circuit.grid(4, 4, 12, 0))
+    assert r["min_fill"] == Q.Plan(m, order_kind=Q.ORDER_MINFILL).info.max_clique - 1
+    assert r["line_graph"] + 1 == Q.Circuit.grid(4, 4, 12, 0).line_graph_width()[1]
+    assert r["line_graph"] >= r["min_fill"]
