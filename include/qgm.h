@@ -91,6 +91,22 @@ int qgm_circuit_gates(const qgm_circuit *c, qgm_gate *gates, int64_t cap, int64_
  * parameter order of qgm_amplitude_grad (theta_p at 2p, phi_p at 2p+1). */
 int qgm_circuit_param_gates(const qgm_circuit *c, int32_t *idx, int64_t cap, int64_t *n);
 
+/* Expectation value of a Pauli string (Sec. III): for O = pauli[0] (x) ...
+ * (character j, one of 'I', 'X', 'Y', 'Z', acts on qubit j), the gates of c
+ * outside O's backward light cone cancel against their inverses and
+ * <0|U^dagger O U|0> = phase * <0|W|0>, where W (written to *out, a new
+ * circuit to free with qgm_circuit_free) applies the light-cone gates V,
+ * then O, then V^dagger, on the qubits V touches, renumbered in increasing
+ * order (qubit_of[j]: new index of qubit j or -1; may be NULL).  O and the
+ * inverse gates are expressed exactly in the gate set (Z = T^4,
+ * X = i RXY(pi, 0), Y = i RXY(pi, pi/2), T^-1 = T^7, (X^1/2)^-1 =
+ * RXY(pi/2, pi), (Y^1/2)^-1 = RXY(pi/2, 3pi/2), RXY(t, f)^-1 = RXY(t, f + pi));
+ * phase (double[2], re and im) collects the factors i.  The amplitude of the
+ * all-zero bitstring of W then comes from any plan (qgm_plan_order, ...).
+ * For O = I: *out = NULL and phase = 1.  Errors: QGM_ERR_ARG. */
+int qgm_circuit_observable(const qgm_circuit *c, const char *pauli, qgm_circuit **out, double *phase,
+                           int32_t *qubit_of);
+
 /* Ordering study (Sec. IV.B, App. E, Fig. 6): the line graph of the
  * circuit's tensor network -- one vertex per wire segment between two gates
  * (segments to the fixed input and output vectors are fixed indices and drop

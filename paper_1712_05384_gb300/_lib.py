@@ -72,6 +72,7 @@ _SIGS = {
     "qgm_circuit_gates": [_P, C.POINTER(qgm_gate), C.c_int64, _I64P],
     "qgm_circuit_param_gates": [_P, _I32P, C.c_int64, _I64P],
     "qgm_circuit_line_graph_width": [_P, _I32P, _I32P],
+    "qgm_circuit_observable": [_P, C.c_char_p, C.POINTER(_P), C.POINTER(C.c_double), _I32P],
     "qgm_circuit_free": [_P],
     "qgm_build_model": [_P, C.POINTER(_P)],
     "qgm_model_get_info": [_P, C.POINTER(qgm_model_info)],
@@ -184,6 +185,16 @@ class Circuit:
         a = np.zeros(max(n.value, 1), dtype=np.int32)
         check(lib().qgm_circuit_param_gates(self._h, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
         return a[: n.value]
+
+    def observable(self, pauli: str):
+        """(circuit W or None, phase, qubit map) with <0|U^dagger P U|0> =
+        phase * <0|W|0> for the Pauli string P (Sec. III, light cone only)."""
+        h = _P()
+        ph = (C.c_double * 2)()
+        qmap = np.zeros(64, dtype=np.int32)
+        check(lib().qgm_circuit_observable(self._h, pauli.encode(), C.byref(h), ph,
+                                           qmap.ctypes.data_as(_I32P)))
+        return (Circuit(h) if h.value else None), complex(ph[0], ph[1]), qmap[: len(pauli)]
 
     def line_graph_width(self):
         """(segments, max clique) of the min-fill order on the line graph of

@@ -1774,6 +1774,113 @@ int qgm_circuit_param_gates(const qgm_circuit *c, int32_t *idx, int64_t cap, int
   return QGM_OK;
 }
 
+// Expectation value <0|U^dagger O U|0> of a Pauli string O (Sec. III): the
+// gates outside O's backward light cone meet their inverses and cancel;
+// what remains, V, gives <0|V^dagger O V|0>, an amplitude (of the all-zero
+// bitstring) of the circuit V, then O, then V^dagger, on the qubits V
+// touches.  Every gate is written with the existing gate set, exactly:
+// Z = T^4, X = i RXY(pi, 0), Y = i RXY(pi, pi/2), H^-1 = H, CZ^-1 = CZ,
+// T^-1 = T^7, (X^1/2)^-1 = RXY(pi/2, pi), (Y^1/2)^-1 = RXY(pi/2, 3pi/2),
+// RXY(theta, phi)^-1 = RXY(theta, phi + pi); the factors i go to *phase.
+int qgm_circuit_observable(const qgm_circuit *c, const char *pauli, qgm_circuit **out, double *phase,
+                           int32_t *qubit_of) {
+  if (!c || !pauli || !out || !phase) {
+    set_error("qgm_circuit_observable: null argument");
+    return QGM_ERR_ARG;
+  }
+  const Circuit &C = c->c;
+  if ((int)strlen(pauli) != C.n) {
+    set_error("qgm_circuit_observable: need one Pauli character per qubit (%d)", C.n);
+    return QGM_ERR_ARG;
+  }
+  std::vector<char> in_s(C.n, 0);
+  bool any = false;
+  for (int j = 0; j < C.n; ++j) {
+    const char ch = pauli[j];
+    if (ch != 'I' && ch != 'X' && ch != 'Y' && ch != 'Z') {
+      set_error("qgm_circuit_observable: character %d is not one of I, X, Y, Z", j);
+      return QGM_ERR_ARG;
+    }
+    in_s[j] = ch != 'I';
+    any |= in_s[j];
+  }
+  phase[0] = 1.0;
+  phase[1] = 0.0;
+  *out = nullptr;
+  if (!any) return QGM_OK;  // <I> = 1
+  std::vector<char> keep(C.gates.size(), 0);
+  for (int gi = (int)C.gates.size() - 1; gi >= 0; --gi) {
+    const qgm_gate &g = C.gates[gi];
+    const bool two = g.kind == QGM_GATE_CZ;
+    if (in_s[g.q0] || (two && in_s[g.q1])) {
+      keep[gi] = 1;
+      in_s[g.q0] = 1;
+      if (two) in_s[g.q1] = 1;
+    }
+  }
+  std::vector<int> map(C.n, -1);
+  int nq = 0;
+  for (int j = 0; j < C.n; ++j)
+    if (in_s[j]) map[j] = nq++;
+  if (qubit_of)
+    for (int j = 0; j < C.n; ++j) qubit_of[j] = map[j];
+  std::vector<qgm_gate> w;
+  auto push = [&](int kind, int cyc, int q0, int q1, double th, double ph) {
+    qgm_gate g{};
+    g.kind = kind;
+    g.cycle = cyc;
+    g.q0 = q0;
+    g.q1 = q1;
+    g.theta = th;
+    g.phi = ph;
+    w.push_back(g);
+  };
+  const int d = C.depth;
+  for (size_t gi = 0; gi < C.gates.size(); ++gi) {
+    if (!keep[gi]) continue;
+    const qgm_gate &g = C.gates[gi];
+    push(g.kind, g.cycle, map[g.q0], g.kind == QGM_GATE_CZ ? map[g.q1] : -1, g.theta, g.phi);
+  }
+  int n_i = 0;
+  for (int j = 0; j < C.n; ++j) {
+    switch (pauli[j]) {
+      case 'Z':
+        for (int r = 0; r < 4; ++r) push(QGM_GATE_T, d, map[j], -1, 0, 0);
+        break;
+      case 'X':
+        push(QGM_GATE_RXY, d, map[j], -1, M_PI, 0.0);
+        ++n_i;
+        break;
+      case 'Y':
+        push(QGM_GATE_RXY, d, map[j], -1, M_PI, M_PI / 2);
+        ++n_i;
+        break;
+      default:
+        break;
+    }
+  }
+  for (int gi = (int)C.gates.size() - 1; gi >= 0; --gi) {
+    if (!keep[gi]) continue;
+    const qgm_gate &g = C.gates[gi];
+    const int cyc = 2 * d - g.cycle, q0 = map[g.q0];
+    switch (g.kind) {
+      case QGM_GATE_H: push(QGM_GATE_H, cyc, q0, -1, 0, 0); break;
+      case QGM_GATE_CZ: push(QGM_GATE_CZ, cyc, q0, map[g.q1], 0, 0); break;
+      case QGM_GATE_T:
+        for (int r = 0; r < 7; ++r) push(QGM_GATE_T, cyc, q0, -1, 0, 0);
+        break;
+      case QGM_GATE_X12: push(QGM_GATE_RXY, cyc, q0, -1, M_PI / 2, M_PI); break;
+      case QGM_GATE_Y12: push(QGM_GATE_RXY, cyc, q0, -1, M_PI / 2, 1.5 * M_PI); break;
+      default: push(QGM_GATE_RXY, cyc, q0, -1, g.theta, g.phi + M_PI); break;
+    }
+  }
+  // i^n_i
+  static const double re[4] = {1, 0, -1, 0}, im[4] = {0, 1, 0, -1};
+  phase[0] = re[n_i & 3];
+  phase[1] = im[n_i & 3];
+  return qgm_circuit_from_gates(nq, w.data(), (int64_t)w.size(), out);
+}
+
 // App. E: the circuit as a tensor network, one tensor per gate.  Its wire
 // segments between two gates are the vertices of the line graph, numbered in
 // the order their consumers close them (gate order, first qubit first);

@@ -202,3 +202,28 @@ def test_ordering_study_rows():
     assert r["min_fill"] == Q.Plan(m, order_kind=Q.ORDER_MINFILL).info.max_clique - 1
     assert r["line_graph"] + 1 == Q.Circuit.grid(4, 4, 12, 0).line_graph_width()[1]
     assert r["line_graph"] >= r["min_fill"]
+
+
+@pytest.mark.parametrize("rows,cols,depth,seed,pauli", [(2, 3, 6, 0, "IZIIII"), (3, 3, 5, 1, "XIIIYIIIZ"),
+                                                        (2, 2, 8, 2, "YYXZ"), (3, 3, 3, 3, "IIIIXIIII"),
+                                                        (2, 3, 4, 4, "ZIIIIX")])
+def test_observable_circuit_reproduces_expectation(rows, cols, depth, seed, pauli):
+    # Sec. III: <0|U^dagger P U|0> = phase * <0|W|0> with W built on the host
+    # from the light cone; W's amplitude by the oracle's state vector, the
+    # expectation by the oracle's definition
+    from oracle import observable as OB
+    from oracle import statevector as sv
+    c = qi.grid_circuit(rows, cols, depth, seed)
+    w, phase, qmap = Q.Circuit.grid(rows, cols, depth, seed).observable(pauli)
+    keep, support = OB.light_cone(c, pauli)
+    assert sorted(np.nonzero(qmap >= 0)[0].tolist()) == support
+    gates = [qi.Gate(*g) for g in w.gates()]
+    # the light-cone gates come first, renumbered
+    for g, gi in zip(gates, keep):
+        o = c.gates[gi]
+        assert (g.kind, g.q0) == (o.kind, int(qmap[o.q0]))
+    wc = qi.circuit_from_gates(len(support), gates)
+    assert abs(phase * sv.state(wc)[0] - OB.expectation(c, pauli)) < 1e-12
+    assert Q.Circuit.grid(rows, cols, depth, seed).observable("I" * c.n)[0] is None
+    with pytest.raises(Q.QgmError):
+        Q.Circuit.grid(rows, cols, depth, seed).observable("Q" * c.n)
