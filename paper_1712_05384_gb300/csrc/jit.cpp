@@ -92,8 +92,9 @@ __device__ __forceinline__ void opscale(const Meta *meta, int slot, Header *hdr,
   const int E = (int)((bits >> 23) & 0xff);
   s = 1.f;
   e = 0;
-  if (E == 0xff) atomicCAS(&hdr->status, 0, -5);
-  else if (E != 0) {
+  // Inf or NaN (E = 0xff) stays unscaled: it reaches the final tensor,
+  // whose check sets the status
+  if (E != 0 && E != 0xff) {
     e = E - 126;
     if (e > 126) e = 126;
     s = __int_as_float((127 - e) << 23);
