@@ -1200,7 +1200,7 @@ static void launch_resident(qgm_plan *p, const uint64_t *d_bits, int64_t B, doub
     double cr = c.real(), ci = c.imag();
     Header *hdr = reinterpret_cast<Header *>(x->ws + p->off_header);
     void *args[] = {&ws_c, &jobs, &n_jobs, &d_bits, &Bl, &cr, &ci, &d_out, &hdr};
-    const size_t smem = (size_t)(L.smem_bytes - worklist_bytes(L));
+    const size_t smem = (size_t)compiled_smem(L);
     if (!x->jit_pre) {
       cudaLaunchKernel(reinterpret_cast<const void *>(x->jit), dim3((unsigned)G), dim3(RES_THREADS), args, smem, st);
       return;
@@ -1364,7 +1364,7 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
     for (size_t li = 0; li < p->resident.size(); ++li) {
       const ResidentLayout &L = p->resident[li];
       if (p->opts.resident_chunk > 0 && L.chunk != p->opts.resident_chunk) continue;
-      const int64_t smem = L.smem_bytes - worklist_bytes(L);
+      const int64_t smem = compiled_smem(L);
       if (smem > optin) continue;
       const int cps = (int)std::min<int64_t>(8, sm_smem / (smem + reserved));
       if (cps < 1) continue;
@@ -1377,7 +1377,7 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
     }
     if (best_li >= 0) {
       const ResidentLayout &L = p->resident[best_li];
-      const int smem = (int)(L.smem_bytes - worklist_bytes(L));
+      const int smem = (int)compiled_smem(L);
       // the bitstring-independent steps run once per call in a kernel of
       // their own when the batch takes two or more waves of CTAs (in one
       // wave that kernel's latency outweighs what each CTA saves)
@@ -1393,6 +1393,20 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
         if (kp) CK(cudaKernelSetAttributeForDevice(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem, x->device));
         int rc = upload(L);
         if (rc) return rc;
+        // initial shared memory: zeros (tensor metadata included) with the
+        // bitstring-independent leaf rows in place
+        {
+          const int64_t shift = worklist_bytes(L);
+          std::vector<float> img((size_t)smem / 4, 0.f);
+          for (const RJob &j : L.jobs) {
+            if (j.batched) continue;
+            const int64_t d = (j.dst - shift) / 4, s2 = 2 * (int64_t)j.src - p->off_base / 4;
+            img[d] = p->base_tables[s2];
+            img[d + 1] = p->base_tables[s2 + 1];
+          }
+          CK(cudaMemcpyAsync(x->ws + p->off_image, img.data(), img.size() * 4, cudaMemcpyHostToDevice, st));
+          CK(cudaStreamSynchronize(st));
+        }
         x->jit = k;
         x->jit_pre = kp;
         x->layout = best_li;
@@ -1446,8 +1460,8 @@ int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int6
   if (chunk) *chunk = res ? p->resident[x->layout].chunk : (int32_t)p->Bp;
   if (smem_bytes)
     *smem_bytes = !res ? 0
-                       : p->resident[x->layout].smem_bytes -
-                             (x->kind == QGM_EXEC_COMPILED ? worklist_bytes(p->resident[x->layout]) : 0);
+                       : x->kind == QGM_EXEC_COMPILED ? compiled_smem(p->resident[x->layout])
+                                                      : p->resident[x->layout].smem_bytes;
   return QGM_OK;
 }
 

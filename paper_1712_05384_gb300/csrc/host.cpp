@@ -1143,7 +1143,18 @@ static void build_resident(qgm_plan *p) {
     }
     if (!ok) break;
     if (L.smem_bytes > 200 * 1024) break;  // larger chunks only grow
+    // leaf rows read from the bitstrings first (the compiled kernel stages
+    // only those one by one; the others come with its shared-memory image)
+    std::stable_partition(L.jobs.begin(), L.jobs.end(), [](const RJob &j) { return j.batched != 0; });
     p->resident.push_back(L);
+  }
+  {
+    int64_t image = 0;
+    for (const ResidentLayout &L : p->resident) image = std::max(image, compiled_smem(L));
+    if (image > 0) {
+      p->off_image = p->ws_bytes - 256;
+      p->ws_bytes += (image + 255) & ~int64_t(255);
+    }
   }
   // bitstring-independent outputs read by batched steps (the same tensors and
   // pre-region places in every layout)

@@ -184,6 +184,8 @@ struct ResidentLayout {
 // Shared-memory bytes of the work lists, which sit between the metadata and
 // the tensors (the compiled kernel has no work lists and drops them).
 inline int64_t worklist_bytes(const ResidentLayout &L) { return ((int64_t)L.wlist.size() * 4 + 15) & ~int64_t(15); }
+// Dynamic shared memory of the compiled resident kernel (16-byte multiple).
+inline int64_t compiled_smem(const ResidentLayout &L) { return (L.smem_bytes - worklist_bytes(L) + 15) & ~int64_t(15); }
 
 // Gradient of one parametrised gate (adjoint elimination): the adjoint of
 // the leaf holding the gate, and the leaf's derivative tables with respect to
@@ -293,6 +295,7 @@ struct qgm_plan {
   int64_t off_rsteps = 0;   // workspace region for the chosen layout's steps
   int64_t off_pre = 0;      // pre region: per pre tensor (maxbits, exp), then the data (16-byte aligned)
   int64_t pre_data = 0;     // float2 index of the data inside the pre region
+  int64_t off_image = 0;    // compiled resident kernel: initial shared-memory image (bitstring-independent leaves)
   int executor_pref = 0;    // qgm_plan_opts.executor
   bool gemm_ok = true;      // GEMM-shaped steps run by the GEMM kernel
   bool trees_ok = false;    // buckets of three or more inputs may run as contraction trees

@@ -244,26 +244,31 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
   o << "  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;\n";
   o << "  const long long b0 = (long long)blockIdx.x * " << L.chunk << ";\n";
   if (pre) o << "  asm volatile(\"griddepcontrol.launch_dependents;\");\n";
-  o << "  for (int i = tid; i < " << p->n_meta_fwd << "; i += 256) { meta[i].maxbits = 0u; meta[i].exp = 0; }\n";
-  // leaves: one job per leaf row (batched rows select the base entry from
-  // the output bits of x_beta); the pre kernel stages the unbatched ones only
-  o << "  const float2 *wsf = reinterpret_cast<const float2 *>(ws);\n";
-  if (L.chunk == 1 && !pre) o << "  const u64 x1 = b0 < B ? __ldg(bits + b0) : 0ull;\n";
-  o << "#pragma unroll 4\n";
-  o << "  for (int t = tid; t < (n_jobs << " << logBc << "); t += 256) {\n";
-  o << "    const int b = t & " << (L.chunk - 1) << ";\n";
-  o << "    const RJob jb = jobs[t >> " << logBc << "];\n";
-  o << "    if (" << (pre ? "jb.batched || b" : "!jb.batched && b") << ") continue;\n";
-  o << "    int ob = 0;\n";
-  if (!pre) {
+  // shared memory starts as the plan's image: zeros (tensor metadata
+  // included) with the bitstring-independent leaf rows in place
+  const int64_t smem = compiled_smem(L);
+  o << "  {\n    const uint4 *img = reinterpret_cast<const uint4 *>(ws + " << p->off_image << ");\n";
+  o << "    uint4 *S = reinterpret_cast<uint4 *>(sm);\n";
+  o << "#pragma unroll 4\n    for (int i = tid; i < " << smem / 16 << "; i += 256) S[i] = __ldg(img + i);\n  }\n";
+  int n_batched = 0;
+  for (const RJob &j : L.jobs) n_batched += j.batched != 0;
+  if (!pre && n_batched) {
+    // leaf rows that depend on the output bits of x_beta (listed first)
+    o << "  __syncthreads();\n";
+    o << "  const float2 *wsf = reinterpret_cast<const float2 *>(ws);\n";
+    if (L.chunk == 1) o << "  const u64 x1 = b0 < B ? __ldg(bits + b0) : 0ull;\n";
+    o << "  for (int t = tid; t < " << (n_batched << logBc) << "; t += 256) {\n";
+    o << "    const int b = t & " << (L.chunk - 1) << ";\n";
+    o << "    const RJob jb = jobs[t >> " << logBc << "];\n";
+    o << "    int ob = 0;\n";
     o << "    if (jb.n_out) {\n";
     if (L.chunk == 1) o << "      const u64 x = x1;\n";
     else o << "      const u64 x = (b0 + b < B) ? bits[b0 + b] : 0ull;\n";
     o << "      ob = jb.n_out == 1 ? (int)((x >> jb.q0) & 1ull) : (int)((((x >> jb.q0) & 1ull) << 1) | ((x >> jb.q1) & 1ull));\n";
     o << "    }\n";
+    o << "    reinterpret_cast<float2 *>(sm + jb.dst - " << shift << ")[b] = __ldg(wsf + jb.src + ob);\n";
+    o << "  }\n";
   }
-  o << "    reinterpret_cast<float2 *>(sm + jb.dst - " << shift << ")[jb.batched ? b : 0] = __ldg(wsf + jb.src + ob);\n";
-  o << "  }\n";
   if (main_part) {
     // the pre kernel's outputs and their scales, once it has finished
     o << "  __syncthreads();\n";
