@@ -801,6 +801,11 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       int u = uni[k];
       int pu = pos[u];
       if (pu >= ne) break;
+      // a wide bucket keeps at least 2^9 output entries per bitstring: the
+      // resident kernels give each bitstring 256 threads, and an output
+      // smaller than that makes lanes split the summed terms and reduce
+      // across lanes (the rest is summed by the next, small, step)
+      if ((int)uni.size() > 10 && (int)uni.size() - (k + 1) < 9) break;
       int in_inputs = 0;
       for (int id : inputs)
         if (std::find(T[id].vars.begin(), T[id].vars.end(), u) != T[id].vars.end()) ++in_inputs;

@@ -162,7 +162,7 @@ def test_contraction_trees_need_fewer_products():
     assert tree.info.n_free == plain.info.n_free
     assert tree.info.max_clique == plain.info.max_clique
     f_plain, f_tree = plain.step_costs()[1].sum(), tree.step_costs()[1].sum()
-    assert f_tree < 0.7 * f_plain
+    assert f_tree < 0.8 * f_plain
     st = tree.steps()
     assert st["k"].sum() == tree.info.n_free
 
