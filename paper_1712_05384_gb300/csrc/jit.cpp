@@ -122,7 +122,8 @@ void emit_term(std::ostringstream &o, const std::vector<std::string> &f, const s
 // group): every item's product-sum with raw operand values, times `comb`
 // (2^-es, the inputs' combined scale) per entry.  Shared-memory offsets are
 // the layout's minus `shift` (the generic kernel's work lists are not kept).
-void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L, size_t q, int64_t shift) {
+void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L, size_t q, int64_t shift,
+               bool track_max) {
   const RStep &r = L.steps[q];
   const StepDesc &d = p->steps[L.src_step[q]];
   const int logBc = __builtin_ctz(L.chunk);
@@ -145,7 +146,7 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
   const int k2 = st.k_inner, k1 = k - k2;
   const bool nested = k2 > 0 && k2 <= 4 && lg <= k1 && (int)st.inner.size() == m;
   const int glo = nested ? w + k2 : w;  // union bit of the lane index's bit 0
-  o << "    unsigned lmax = 0u;\n";
+  if (track_max) o << "    unsigned lmax = 0u;\n";
   if (lg) {
     o << "    const int g = gt & " << (tpi - 1) << ";\n";
     for (int i = 0; i < m; ++i) o << "    const int go" << i << " = " << bit_map_expr("g", v[i], glo, lg) << ";\n";
@@ -216,7 +217,9 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
       << "); acc.y += __shfl_xor_sync(0xffffffffu, acc.y, " << s2 << ");\n";
   o << "      if (" << live << (lg ? " && g == 0" : "") << ") {\n";
   o << "        F[" << ((r.out_soff - shift) / 8) << " + it] = acc;\n";
-  o << "        lmax = max(lmax, max(__float_as_uint(acc.x) & 0x7fffffffu, __float_as_uint(acc.y) & 0x7fffffffu));\n      }\n";
+  if (track_max)
+    o << "        lmax = max(lmax, max(__float_as_uint(acc.x) & 0x7fffffffu, __float_as_uint(acc.y) & 0x7fffffffu));\n";
+  o << "      }\n";
   o << "    }\n";
 }
 
@@ -335,18 +338,23 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
       else o << "      __syncwarp();\n";
       o << "    }\n";
     }
+    const bool track = !static_max_step(r, L.final_meta);
     {
       std::ostringstream b;
-      emit_body(b, p, L, q, shift);
-      o << "    unsigned lm;\n    {\n" << b.str() << "    lm = lmax; }\n";
+      emit_body(b, p, L, q, shift, track);
+      if (track) o << "    unsigned lm;\n    {\n" << b.str() << "    lm = lmax; }\n";
+      else o << "    {\n" << b.str() << "    }\n";
     }
-    // max |re|,|im| over the step's entries: non-negative floats (and NaN,
-    // which must reach the maximum) order like their bit patterns
-    o << "    lm = __reduce_max_sync(0xffffffffu, lm);\n";
-    o << "    if (lane == 0) {\n";
-    o << "      if (lm) atomicMax(&meta[" << r.out_meta << "].maxbits, lm);\n";
-    o << "      if (wid == " << w0 << ") meta[" << r.out_meta << "].exp = esum;\n";
-    o << "    }\n  }\n";
+    if (track) {
+      // max |re|,|im| over the step's entries: non-negative floats (and NaN,
+      // which must reach the maximum) order like their bit patterns
+      o << "    lm = __reduce_max_sync(0xffffffffu, lm);\n";
+      o << "    if (lane == 0) {\n";
+      o << "      if (lm) atomicMax(&meta[" << r.out_meta << "].maxbits, lm);\n";
+      o << "      if (wid == " << w0 << ") meta[" << r.out_meta << "].exp = esum;\n";
+      o << "    }\n";
+    }
+    o << "  }\n";
   }
   o << "  __syncthreads();\n";
   if (pre) {
