@@ -289,6 +289,10 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
     o << "  }\n";
   }
   o << "  __syncthreads();\n";
+  // recorded maxima known before the run: steps with a static bound
+  std::map<int, int> static_k;  // metadata slot -> k of the bound 2^k
+  for (const RStep &r : L.steps)
+    if (static_max_step(r, L.final_meta)) static_k[r.out_meta] = r.k;
   // steps in level order; inside a level grouped by first warp, so that
   // each warp's code for the level is contiguous
   std::vector<size_t> emit_order(L.steps.size());
@@ -311,12 +315,25 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
       << " kept (level " << L.level[q] << ")\n";
     o << "  if (wid >= " << w0 << " && wid < " << (w0 + nw) << ") {\n";
     o << "    const int gt = tid - " << (32 * w0) << ";\n";
-    o << "    int es = 0, esum = 0;\n";
-    for (int i = 0; i < d.m; ++i) {
+    // inputs whose producer has a static bound 2^k' get the constant scale
+    // 2^-(k'+1) (exponent k'+1, recorded exponent 0); the others read theirs
+    int es_static = 0;
+    bool any_dynamic = false;
+    for (int i = 0; i < d.m; ++i)
       if (r.in[i].meta >= 0) {
+        auto it = static_k.find(r.in[i].meta);
+        if (it != static_k.end()) es_static += it->second + 1;
+        else any_dynamic = true;
+      }
+    o << "    int es = " << es_static << ", esum = " << es_static << ";\n";
+    for (int i = 0; i < d.m; ++i) {
+      if (r.in[i].meta < 0) continue;
+      auto it = static_k.find(r.in[i].meta);
+      if (it != static_k.end())
+        o << "    const float s" << i << " = __int_as_float(" << (126 - it->second) << " << 23);\n";
+      else
         o << "    float s" << i << "; { int e; opscale(meta, " << r.in[i].meta << ", hdr, s" << i
           << ", e, esum); es += e; }\n";
-      }
     }
     // scales: one combined factor per entry when the inputs' exponents sum
     // to a representable power of two; otherwise the intermediate inputs are
@@ -324,7 +341,9 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
     bool any_meta = false;
     for (int i = 0; i < d.m; ++i) any_meta |= r.in[i].meta >= 0;
     o << "    float comb = 1.f;\n";
-    if (any_meta) {
+    if (any_meta && !any_dynamic && es_static >= -120 && es_static <= 120) {
+      o << "    comb = __int_as_float(" << (127 - es_static) << " << 23);\n";
+    } else if (any_meta) {
       o << "    if (es >= -120 && es <= 120) comb = __int_as_float((127 - es) << 23);\n";
       o << "    else {\n";
       for (int i = 0; i < d.m; ++i) {
