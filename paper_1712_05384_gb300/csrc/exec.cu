@@ -1405,11 +1405,12 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
             img[d + 1] = p->base_tables[s2 + 1];
           }
           // recorded maxima of the steps with a static bound: 2^k, exponent 0
-          for (const RStep &r : L.steps)
-            if (static_max_step(r, L.final_meta)) {
-              const uint32_t bits = (uint32_t)(127 + r.k) << 23;
-              std::memcpy(&img[2 * (size_t)r.out_meta], &bits, 4);
-            }
+          for (const auto &sb : static_bounds(L)) {
+            const uint32_t bits = (uint32_t)(127 + sb.second.first) << 23;
+            const int32_t ex = sb.second.second;
+            std::memcpy(&img[2 * (size_t)sb.first], &bits, 4);
+            std::memcpy(&img[2 * (size_t)sb.first + 1], &ex, 4);
+          }
           CK(cudaMemcpyAsync(x->ws + p->off_image, img.data(), img.size() * 4, cudaMemcpyHostToDevice, st));
           CK(cudaStreamSynchronize(st));
         }

@@ -4,6 +4,7 @@
 
 #include <complex>
 #include <cstdint>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -184,18 +185,17 @@ struct ResidentLayout {
 // Shared-memory bytes of the work lists, which sit between the metadata and
 // the tensors (the compiled kernel has no work lists and drops them).
 inline int64_t worklist_bytes(const ResidentLayout &L) { return ((int64_t)L.wlist.size() * 4 + 15) & ~int64_t(15); }
-// A step of the compiled resident kernel whose inputs are all leaves (gate
-// tables, entries of modulus at most 1) and whose output is not the final
-// tensor: its output is bounded by 2^k (k summed variables), and that bound,
-// placed in the kernel's initial shared-memory image, serves as its recorded
-// maximum (no run-time reduction).  Non-finite values still reach the final
-// tensor, whose maximum is measured.
-inline bool static_max_step(const RStep &r, int final_meta) {
-  if (r.out_meta == final_meta) return false;
-  for (int i = 0; i < r.m; ++i)
-    if (r.in[i].meta >= 0) return false;
-  return true;
-}
+// Steps of the compiled resident kernel with a static bound on their output:
+// every input is a leaf (gate tables: entries of modulus at most 1) or the
+// output of such a step, scaled by the consumer to maxima at most 1/2, so
+// |out| <= 2^k for k summed variables.  That bound, placed in the kernel's
+// initial shared-memory image, serves as the recorded maximum (no run-time
+// reduction); chains of such steps stop after three levels, so that the
+// headroom a loose bound gives away stays far from FP32's range, and the
+// final tensor is always measured (non-finite values reach it and set the
+// status there).  Returns metadata slot -> (k, exponent), the exponent being
+// the sum of the inputs' exponents and scale exponents, as at run time.
+std::map<int, std::pair<int, int>> static_bounds(const ResidentLayout &L);
 // Dynamic shared memory of the compiled resident kernel (16-byte multiple).
 inline int64_t compiled_smem(const ResidentLayout &L) { return (L.smem_bytes - worklist_bytes(L) + 15) & ~int64_t(15); }
 

@@ -225,6 +225,30 @@ void emit_body(std::ostringstream &o, const qgm_plan *p, const ResidentLayout &L
 
 }  // namespace
 
+std::map<int, std::pair<int, int>> static_bounds(const ResidentLayout &L) {
+  std::map<int, std::pair<int, int>> bound;  // metadata slot -> (k, exponent)
+  std::map<int, int> depth;                  // chain depth
+  for (const RStep &r : L.steps) {
+    if (r.out_meta == L.final_meta) continue;
+    int dp = 1, ex = 0;
+    bool ok = true;
+    for (int i = 0; i < r.m && ok; ++i) {
+      if (r.in[i].meta < 0) continue;
+      auto it = bound.find(r.in[i].meta);
+      if (it == bound.end()) ok = false;
+      else {
+        dp = std::max(dp, depth[r.in[i].meta] + 1);
+        ex += it->second.first + 1 + it->second.second;  // scale exponent k+1, recorded exponent
+      }
+    }
+    if (ok && dp <= 3) {
+      bound[r.out_meta] = {r.k, ex};
+      depth[r.out_meta] = dp;
+    }
+  }
+  return bound;
+}
+
 // CUDA source of the resident kernel specialised to layout L of plan p.
 // mode RES_WHOLE: the whole pass per CTA.  RES_MAIN: the steps with a batch
 // axis; the bitstring-independent tensors they read come from the pre
@@ -290,9 +314,7 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
   }
   o << "  __syncthreads();\n";
   // recorded maxima known before the run: steps with a static bound
-  std::map<int, int> static_k;  // metadata slot -> k of the bound 2^k
-  for (const RStep &r : L.steps)
-    if (static_max_step(r, L.final_meta)) static_k[r.out_meta] = r.k;
+  const std::map<int, std::pair<int, int>> static_k = static_bounds(L);  // slot -> (k of 2^k, exponent)
   // steps in level order; inside a level grouped by first warp, so that
   // each warp's code for the level is contiguous
   std::vector<size_t> emit_order(L.steps.size());
@@ -317,20 +339,24 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
     o << "    const int gt = tid - " << (32 * w0) << ";\n";
     // inputs whose producer has a static bound 2^k' get the constant scale
     // 2^-(k'+1) (exponent k'+1, recorded exponent 0); the others read theirs
-    int es_static = 0;
+    int es_static = 0, esum_static = 0;
     bool any_dynamic = false;
     for (int i = 0; i < d.m; ++i)
       if (r.in[i].meta >= 0) {
         auto it = static_k.find(r.in[i].meta);
-        if (it != static_k.end()) es_static += it->second + 1;
-        else any_dynamic = true;
+        if (it != static_k.end()) {
+          es_static += it->second.first + 1;
+          esum_static += it->second.first + 1 + it->second.second;
+        } else {
+          any_dynamic = true;
+        }
       }
-    o << "    int es = " << es_static << ", esum = " << es_static << ";\n";
+    o << "    int es = " << es_static << ", esum = " << esum_static << ";\n";
     for (int i = 0; i < d.m; ++i) {
       if (r.in[i].meta < 0) continue;
       auto it = static_k.find(r.in[i].meta);
       if (it != static_k.end())
-        o << "    const float s" << i << " = __int_as_float(" << (126 - it->second) << " << 23);\n";
+        o << "    const float s" << i << " = __int_as_float(" << (126 - it->second.first) << " << 23);\n";
       else
         o << "    float s" << i << "; { int e; opscale(meta, " << r.in[i].meta << ", hdr, s" << i
           << ", e, esum); es += e; }\n";
@@ -357,7 +383,7 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
       else o << "      __syncwarp();\n";
       o << "    }\n";
     }
-    const bool track = !static_max_step(r, L.final_meta);
+    const bool track = static_k.count(r.out_meta) == 0;
     {
       std::ostringstream b;
       emit_body(b, p, L, q, shift, track);
