@@ -348,3 +348,18 @@ def test_compiled_many_waves_runs_shared_part_once():
     assert p.executor()[:2] == (3, 1)
     rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
     assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+def test_compiled_grid6x6_d20_param_sampled():
+    # the widest plan here that fits the resident executors (116 KB of shared
+    # memory per bitstring): compiled kernel against the oracle on sampled
+    # bitstrings, and against the stepwise executor on all 256
+    c = qi.grid_circuit(6, 6, 20, 0, param=True)
+    a3, bits, p3 = run_batch(c, 256, executor=3)
+    assert p3.executor()[0] == 3
+    a1, _, _ = run_batch(c, 256, executor=1)
+    rel, ab = errors(a3, a1, c.n)
+    assert rel < 2 * REL_TOL and ab < 2 * ABS_TOL, (rel, ab)
+    idx = np.linspace(0, 255, 6).astype(int)
+    rel, ab = errors(a3[idx], ve.amplitudes(c, bits[idx]), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
