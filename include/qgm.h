@@ -262,7 +262,10 @@ int qgm_amplitudes(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double 
                    void *stream);
 
 /* The same with HOST bitstrings and a HOST result: copies in, runs, copies
- * out and synchronises `stream`.  Uses the bound workspace for staging. */
+ * out and synchronises `stream`.  Uses the bound workspace for staging; with
+ * the resident executors and page-locked buffers the device can address
+ * (cudaHostAlloc, cudaHostRegister), the kernel reads and writes them in
+ * place instead. */
 int qgm_amplitudes_host(qgm_plan *p, const uint64_t *h_bitstrings, int64_t B,
                         double *h_out, void *stream);
 

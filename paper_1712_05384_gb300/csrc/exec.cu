@@ -1497,6 +1497,24 @@ int qgm_amplitudes_host(qgm_plan *p, const uint64_t *h_bitstrings, int64_t B, do
     return QGM_ERR_ARG;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // Page-locked host buffers the device can address (registered or pinned
+  // memory has a device pointer): the resident executors, which read each
+  // bitstring once and write each amplitude once, use them in place.
+  if ((p->exec->kind == QGM_EXEC_RESIDENT || p->exec->kind == QGM_EXEC_COMPILED) && p->open_in_batch == 0) {
+    cudaPointerAttributes ab{}, ao{};
+    const bool mapped = cudaPointerGetAttributes(&ab, h_bitstrings) == cudaSuccess &&
+                        ab.type == cudaMemoryTypeHost && ab.devicePointer != nullptr &&
+                        cudaPointerGetAttributes(&ao, h_out) == cudaSuccess && ao.type == cudaMemoryTypeHost &&
+                        ao.devicePointer != nullptr;
+    cudaGetLastError();  // a query on pageable memory may leave an error behind
+    if (mapped) {
+      rc = run(p, static_cast<const uint64_t *>(ab.devicePointer), B, static_cast<double2 *>(ao.devicePointer), B,
+               st);
+      if (rc) return rc;
+      CK(cudaStreamSynchronize(st));
+      return QGM_OK;
+    }
+  }
   uint64_t *d_bits = reinterpret_cast<uint64_t *>(p->exec->ws + p->off_bits);
   double2 *d_out = reinterpret_cast<double2 *>(p->exec->ws + p->off_outstage);
   CK(cudaMemcpyAsync(d_bits, h_bitstrings, B * sizeof(uint64_t), cudaMemcpyHostToDevice, st));

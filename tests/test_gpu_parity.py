@@ -363,3 +363,22 @@ def test_compiled_grid6x6_d20_param_sampled():
     idx = np.linspace(0, 255, 6).astype(int)
     rel, ab = errors(a3[idx], ve.amplitudes(c, bits[idx]), c.n)
     assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+@pytest.mark.parametrize("executor", [2, 3])
+def test_host_api_with_page_locked_buffers(executor):
+    # page-locked host buffers are read and written in place by the resident
+    # executors; pageable ones go through staging copies; same amplitudes
+    import ctypes as C
+    q = Q()
+    c = qi.grid_circuit(4, 4, 12, 3)
+    bits = qi.bitstrings(16, 50, 3)
+    a_dev, _, p = run_batch(c, 50, bits=bits, executor=executor)
+    hb = torch.from_numpy(bits.astype(np.int64)).pin_memory()
+    ho = torch.zeros(100, dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        ho.zero_()
+        q._lib.check(q.lib().qgm_amplitudes_host(p._h, hb.data_ptr(), 50, ho.data_ptr(), None))
+        o = ho.numpy()
+        assert np.array_equal(o[0::2] + 1j * o[1::2], a_dev)
+    assert np.array_equal(p.amplitudes_host(bits), a_dev)
