@@ -87,7 +87,7 @@ __device__ __forceinline__ void cmac(float2 &a, float2 x, float2 y) {
   a.y = fmaf(x.x, y.y, a.y);
   a.y = fmaf(x.y, y.x, a.y);
 }
-__device__ __forceinline__ void opscale(const Meta *meta, int slot, Header *hdr, float &s, int &e, int &esum) {
+__device__ __forceinline__ void opscale(const Meta *meta, int slot, float &s, int &e, int &esum) {
   const unsigned bits = meta[slot].maxbits;
   const int E = (int)((bits >> 23) & 0xff);
   s = 1.f;
@@ -358,7 +358,7 @@ std::string resident_source(const qgm_plan *p, const ResidentLayout &L, const st
       if (it != static_k.end())
         o << "    const float s" << i << " = __int_as_float(" << (126 - it->second.first) << " << 23);\n";
       else
-        o << "    float s" << i << "; { int e; opscale(meta, " << r.in[i].meta << ", hdr, s" << i
+        o << "    float s" << i << "; { int e; opscale(meta, " << r.in[i].meta << ", s" << i
           << ", e, esum); es += e; }\n";
     }
     // scales: one combined factor per entry when the inputs' exponents sum
