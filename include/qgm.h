@@ -285,6 +285,17 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
  * CTA (resident and compiled). */
 int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int64_t *smem_bytes);
 
+/* CUDA source of the compiled resident kernel (QGM_EXEC_COMPILED) for this
+ * plan, as qgm_plan_bind compiles it; needs no GPU.  chunk: bitstrings per
+ * CTA of the layout (1, 2, 4 or 8); part: 0 the whole pass, 1 its batched
+ * part, 2 its bitstring-independent part (the split used for batches of two
+ * or more waves); min_blocks: CTAs per SM for the launch bounds (0: as many
+ * as 228 KB of shared memory per SM hold, at most 8).  Copies up to cap - 1
+ * bytes and a NUL into buf (may be NULL) and the full length into *len.
+ * Errors: QGM_ERR_ARG (no such layout, bad part). */
+int qgm_plan_kernel_source(const qgm_plan *p, int32_t chunk, int32_t part, int32_t min_blocks, char *buf,
+                           int64_t cap, int64_t *len);
+
 /* No counterpart in the paper: an allocation-free variant of qgm_amplitudes
  * for callers that cannot allocate device memory when they need amplitudes
  * (a framework whose pool allocator owns all device memory, or a

@@ -72,6 +72,7 @@ _SIGS = {
     "qgm_circuit_gates": [_P, C.POINTER(qgm_gate), C.c_int64, _I64P],
     "qgm_circuit_param_gates": [_P, _I32P, C.c_int64, _I64P],
     "qgm_circuit_line_graph_width": [_P, _I32P, _I32P],
+    "qgm_plan_kernel_source": [_P, C.c_int32, C.c_int32, C.c_int32, C.c_char_p, C.c_int64, _I64P],
     "qgm_circuit_observable": [_P, C.c_char_p, C.POINTER(_P), C.POINTER(C.c_double), _I32P],
     "qgm_circuit_free": [_P],
     "qgm_build_model": [_P, C.POINTER(_P)],
@@ -343,6 +344,14 @@ class Plan:
         check(lib().qgm_plan_profile(self._h, _ptr(d_bits), B, _ptr(d_out),
                                      ms.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
         return ms
+
+    def kernel_source(self, chunk=1, part=0, min_blocks=0) -> str:
+        """CUDA source of the compiled resident kernel for this plan (no GPU needed)."""
+        n = C.c_int64()
+        check(lib().qgm_plan_kernel_source(self._h, chunk, part, min_blocks, None, 0, C.byref(n)))
+        buf = C.create_string_buffer(n.value + 1)
+        check(lib().qgm_plan_kernel_source(self._h, chunk, part, min_blocks, buf, n.value + 1, C.byref(n)))
+        return buf.value.decode()
 
     def executor(self):
         """(kind, chunk, smem_bytes) of the bound executor."""

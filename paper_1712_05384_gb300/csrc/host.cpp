@@ -2101,3 +2101,28 @@ void qgm_plan_free(qgm_plan *p) {
 }
 
 }  // extern "C"
+
+int qgm_plan_kernel_source(const qgm_plan *p, int32_t chunk, int32_t part, int32_t min_blocks, char *buf,
+                           int64_t cap, int64_t *len) {
+  if (!p || !len || part < RES_WHOLE || part > RES_PRE) {
+    set_error("qgm_plan_kernel_source: bad argument");
+    return QGM_ERR_ARG;
+  }
+  const ResidentLayout *L = nullptr;
+  for (const ResidentLayout &l : p->resident)
+    if (l.chunk == chunk) L = &l;
+  if (!L) {
+    set_error("qgm_plan_kernel_source: no resident layout with %d bitstrings per CTA", chunk);
+    return QGM_ERR_ARG;
+  }
+  const int mb = min_blocks > 0 ? min_blocks
+                                : (int)std::max<int64_t>(1, std::min<int64_t>(8, (228 * 1024) / (compiled_smem(*L) + 1024)));
+  const std::string src = resident_source(p, *L, part == RES_PRE ? "qgm_resident_pre" : "qgm_resident_plan", mb, part);
+  *len = (int64_t)src.size();
+  if (buf && cap > 0) {
+    const int64_t n = std::min<int64_t>(cap - 1, (int64_t)src.size());
+    std::memcpy(buf, src.data(), (size_t)n);
+    buf[n] = '\0';
+  }
+  return QGM_OK;
+}
