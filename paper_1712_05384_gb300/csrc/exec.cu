@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(256)
 // (grid x), K in chunks of 16 staged in shared memory, a 4 x 4 complex tile
 // per thread in registers.  Operand and output addresses come from the bit
 // positions of the m, n, k, s variables in each tensor's own index.
-constexpr int GT = 64, GK = 16;
+constexpr int GT = 64;
 
 __device__ __forceinline__ int64_t lin_bits(uint64_t x, const uint8_t *pos, int nb) {
   int64_t r = 0;
@@ -575,6 +575,9 @@ __device__ __forceinline__ int64_t lin_bits(uint64_t x, const uint8_t *pos, int 
   return r;
 }
 
+// GK: summed entries per shared-memory chunk (16, or 32 when K allows: half
+// the barriers per product)
+template <int GK>
 __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *meta, Header *hdr, int Bp) {
   __shared__ float2 As[GK][GT];
   __shared__ float2 Bs[GK][GT];
@@ -609,14 +612,14 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
   for (int r = 0; r < 4; ++r)
 #pragma unroll
     for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
-  const int nkc = 1 << (g.nk - 4);
+  const int nkc = (1 << g.nk) / GK;
   for (int kc = 0; kc < nkc; ++kc) {
     __syncthreads();  // the previous chunk's tiles and tables are consumed
     if (tid < GK) oAk[tid] = lin_bits((uint64_t)kc * GK + tid, g.kA, g.nk) * uA;
     else if (tid < 2 * GK) oBk[tid - GK] = lin_bits((uint64_t)kc * GK + tid - GK, g.kB, g.nk) * uB;
     __syncthreads();
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < GK * GT / 256; ++q) {
       const int e = tid + 256 * q, i = e & (GT - 1), j = e >> 6;
       const float2 va = __ldg(reinterpret_cast<const float2 *>(ws + baseA + oAm[i] + oAk[j]));
       const float2 vb = __ldg(reinterpret_cast<const float2 *>(ws + baseB + oBn[i] + oBk[j]));
@@ -1113,7 +1116,10 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
   if (d.gemm >= 0 && gemms) {
     const GemmDesc &g = gemms[d.gemm];
     const unsigned tiles = 1u << ((g.nm - 6) + (g.nn - 6));
-    k_gemm<<<dim3(tiles, g.o_bat ? Bp : 1, 1u << g.ns), 256, 0, st>>>(ws, g, meta, hdr, Bp);
+    if (g.nk >= 5)
+      k_gemm<32><<<dim3(tiles, g.o_bat ? Bp : 1, 1u << g.ns), 256, 0, st>>>(ws, g, meta, hdr, Bp);
+    else
+      k_gemm<16><<<dim3(tiles, g.o_bat ? Bp : 1, 1u << g.ns), 256, 0, st>>>(ws, g, meta, hdr, Bp);
     return;
   }
   auto pow2_floor = [](uint64_t v) {
