@@ -348,7 +348,9 @@ int qgm_status(qgm_plan *p, void *stream);
  * d_grad[i] = dL/dp_i = 2 Re sum_b conj(g_b) da_b/dp_i for the n_params
  * parameters (theta, phi of each RXY gate, see qgm_circuit_param_gates) into
  * device double[n_params], and the amplitudes into d_amp (device double[2B],
- * may be NULL).  Requires QGM_OUT_BATCH.  Errors as qgm_amplitudes. */
+ * may be NULL).  Requires QGM_OUT_BATCH.  Asynchronous on `stream`; the
+ * first call with a given set of pointers and B builds a CUDA graph of the
+ * pass, later calls launch it.  Errors as qgm_amplitudes. */
 int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B,
                        const double *d_dL_dconja, double *d_grad, double *d_amp,
                        void *stream);

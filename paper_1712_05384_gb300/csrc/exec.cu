@@ -1076,6 +1076,10 @@ struct qgm_exec_state {
   int sms = 148;
   int kind = QGM_EXEC_STEPWISE;
   int layout = -1;  // index into qgm_plan::resident
+  cudaGraphExec_t ggraph = nullptr;  // the adjoint pass, for one set of pointers
+  const void *gg_bits = nullptr, *gg_dl = nullptr;
+  void *gg_grad = nullptr, *gg_amp = nullptr;
+  int64_t gg_B = -1;
   cudaKernel_t jit = nullptr;  // compiled resident kernel (QGM_EXEC_COMPILED)
   cudaKernel_t jit_pre = nullptr;  // its bitstring-independent part, when split off
   std::string jit_error;       // why the compiled kernel is not used, if so
@@ -1095,6 +1099,7 @@ static int cuda_fail(cudaError_t e, const char *what) {
 extern "C" void qgm_exec_release(qgm_plan *p) {
   if (!p || !p->exec) return;
   if (p->exec->graph) cudaGraphExecDestroy(p->exec->graph);
+  if (p->exec->ggraph) cudaGraphExecDestroy(p->exec->ggraph);
   delete p->exec;
   p->exec = nullptr;
 }
@@ -1637,6 +1642,11 @@ int qgm_status(qgm_plan *p, void *stream) {
   return s;
 }
 
+}  // extern "C"
+static void enqueue_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, const double *d_dL_dconja,
+                         double *d_grad, double2 *amp, cudaStream_t st);
+extern "C" {
+
 int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, const double *d_dL_dconja,
                        double *d_grad, double *d_amp, void *stream) {
   int rc = check_bound(p, "qgm_amplitude_grad");
@@ -1651,10 +1661,48 @@ int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, con
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   qgm_exec_state *x = p->exec;
+  double2 *amp = d_amp ? reinterpret_cast<double2 *>(d_amp) : reinterpret_cast<double2 *>(x->ws + p->off_outstage);
+  // the pass (hundreds of short launches) runs as one CUDA graph, captured
+  // on the first call with this set of pointers
+  if (!x->ggraph || x->gg_bits != d_bitstrings || x->gg_dl != d_dL_dconja || x->gg_grad != d_grad ||
+      x->gg_amp != amp || x->gg_B != B) {
+    if (x->ggraph) {
+      cudaGraphExecDestroy(x->ggraph);
+      x->ggraph = nullptr;
+    }
+    cudaStream_t cs;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      enqueue_grad(p, d_bitstrings, B, d_dL_dconja, d_grad, amp, cs);
+      e = cudaStreamEndCapture(cs, &g);
+    }
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) return cuda_fail(e, "graph capture (adjoint)");
+    e = cudaGraphInstantiate(&x->ggraph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate (adjoint)");
+    x->gg_bits = d_bitstrings;
+    x->gg_dl = d_dL_dconja;
+    x->gg_grad = d_grad;
+    x->gg_amp = amp;
+    x->gg_B = B;
+  }
+  CK(cudaGraphLaunch(x->ggraph, st));
+  return QGM_OK;
+}
+
+}  // extern "C"
+
+// Forward elimination keeping every intermediate, FP64 amplitudes, the seed,
+// the backward steps and the per-gate reduction (qgm_amplitude_grad).
+static void enqueue_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, const double *d_dL_dconja,
+                         double *d_grad, double2 *amp, cudaStream_t st) {
+  qgm_exec_state *x = p->exec;
   char *ws = x->ws;
   Header *hdr = reinterpret_cast<Header *>(ws + p->off_header);
   Meta *meta = reinterpret_cast<Meta *>(ws + p->off_meta);
-  double2 *amp = d_amp ? reinterpret_cast<double2 *>(d_amp) : reinterpret_cast<double2 *>(ws + p->off_outstage);
   const int64_t iblocks = std::min<int64_t>((B + 255) / 256, (int64_t)x->sms * 4);
   k_init<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(amp, B, hdr);
   launch_leaves(p, d_bitstrings, B, st);
@@ -1671,11 +1719,7 @@ int qgm_amplitude_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, con
                                                d_bitstrings, B, p->Bp,
                                                reinterpret_cast<const double2 *>(d_dL_dconja), meta, c.real(),
                                                c.imag(), d_grad);
-  CK(cudaGetLastError());
-  return QGM_OK;
 }
-
-}  // extern "C"
 
 // ===========================================================================
 // Allocation-free entry point.
