@@ -12,10 +12,13 @@
 // for the device with NVRTC (loaded with dlopen; when it is missing, or the
 // compile fails, the generic resident kernel runs instead).
 //
-// Arithmetic is the generic kernel's: per-tensor power-of-two exponents
+// Arithmetic follows the generic kernel: per-tensor power-of-two exponents
 // (the producer records max |re|,|im|; the consumer scales by 2^-e), one
 // combined scale per output entry when the inputs' exponents sum to a
-// representable power of two, per-load scaling otherwise.
+// representable power of two, the inputs rescaled in place otherwise.  Two
+// additions: short chains of steps over gate tables take a static bound as
+// their recorded maximum (static_bounds), and shared memory starts from a
+// plan image built at bind.
 #include <cuda_runtime.h>
 #include <dlfcn.h>
 
