@@ -175,10 +175,12 @@ typedef struct {
                                  kernel instead of the tiled GEMM kernel */
   int32_t gradients;          /* 1: also lay out the adjoint elimination of
                                  qgm_amplitude_grad (more workspace) */
-  int32_t trees;              /* 1: buckets of three or more inputs may run as
-                                 contraction trees (pairs multiplied first, each
-                                 variable summed once no other factor holds it)
-                                 when that needs clearly fewer products */
+  int32_t trees;              /* buckets of three or more inputs as contraction
+                                 trees (pairs multiplied first, each variable
+                                 summed once no other factor holds it) where that
+                                 needs clearly fewer products: 1 on, -1 off,
+                                 0 automatic (on for batch plans that no resident
+                                 layout fits, when it saves 10% of the products) */
   uint64_t open_mask;         /* QGM_OUT_BATCH: qubits whose outputs stay open
                                  (Eq. psi_x without their deltas): each bitstring
                                  then yields 2^popcount(open_mask) amplitudes */

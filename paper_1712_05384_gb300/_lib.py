@@ -241,7 +241,7 @@ class Model:
 class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
-                 resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=False):
+                 resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=None):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -254,7 +254,7 @@ class Plan:
         o.gradients = int(gradients)
         o.no_gemm = 0 if gemm else 1
         o.open_mask = open_mask
-        o.trees = int(trees)
+        o.trees = 0 if trees is None else (1 if trees else -1)
         # amplitudes per bitstring: its open qubits run over all 2^k values
         self.n_open = bin(open_mask).count("1") if output_mode == OUT_BATCH else 0
         self._order_buf = None

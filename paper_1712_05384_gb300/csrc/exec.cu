@@ -576,14 +576,16 @@ __device__ __forceinline__ int64_t lin_bits(uint64_t x, const uint8_t *pos, int 
 }
 
 // GK: summed entries per shared-memory chunk (16, or 32 when K allows: half
-// the barriers per product)
-template <int GK>
+// the barriers per product); NT: tile columns (64, or 32 when B has five
+// private kept variables), NT / 16 per thread
+template <int GK, int NT>
 __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *meta, Header *hdr, int Bp) {
+  constexpr int TC = NT / 16;
   __shared__ float2 As[GK][GT];
-  __shared__ float2 Bs[GK][GT];
-  __shared__ int64_t oAm[GT], oBn[GT], oOm[GT], oOn[GT], oAk[GK], oBk[GK];
+  __shared__ float2 Bs[GK][NT];
+  __shared__ int64_t oAm[GT], oBn[NT], oOm[GT], oOn[NT], oAk[GK], oBk[GK];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int lnt = g.nn - 6;
+  const int lnt = g.nn - (NT == 64 ? 6 : 5);
   const uint64_t tm = (uint64_t)blockIdx.x >> lnt, tn = (uint64_t)blockIdx.x & ((1ull << lnt) - 1);
   const int beta = blockIdx.y;
   const uint64_t sidx = blockIdx.z;
@@ -595,10 +597,10 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
   if (tid < GT) {
     oAm[tid] = lin_bits(tm * GT + tid, g.mA, g.nm) * uA;
     oOm[tid] = lin_bits(tm * GT + tid, g.mO, g.nm) * uO;
-  } else if (tid < 2 * GT) {
+  } else if (tid < GT + NT) {
     const int j = tid - GT;
-    oBn[j] = lin_bits(tn * GT + j, g.nB, g.nn) * uB;
-    oOn[j] = lin_bits(tn * GT + j, g.nO, g.nn) * uO;
+    oBn[j] = lin_bits(tn * NT + j, g.nB, g.nn) * uB;
+    oOn[j] = lin_bits(tn * NT + j, g.nO, g.nn) * uO;
   }
   float sa, sb;
   int ea, eb;
@@ -607,37 +609,53 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
   if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
     meta[g.o_meta].exp = ea + eb + (g.a_meta >= 0 ? meta[g.a_meta].exp : 0) +
                          (g.b_meta >= 0 ? meta[g.b_meta].exp : 0);
-  float2 acc[4][4];
+  float2 acc[4][TC];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = make_float2(0.f, 0.f);
+    for (int c = 0; c < TC; ++c) acc[r][c] = make_float2(0.f, 0.f);
   const int nkc = (1 << g.nk) / GK;
   for (int kc = 0; kc < nkc; ++kc) {
     __syncthreads();  // the previous chunk's tiles and tables are consumed
     if (tid < GK) oAk[tid] = lin_bits((uint64_t)kc * GK + tid, g.kA, g.nk) * uA;
     else if (tid < 2 * GK) oBk[tid - GK] = lin_bits((uint64_t)kc * GK + tid - GK, g.kB, g.nk) * uB;
     __syncthreads();
+    if constexpr (NT == GT) {
+      // both tiles in one loop: two loads in flight per iteration
 #pragma unroll
-    for (int q = 0; q < GK * GT / 256; ++q) {
-      const int e = tid + 256 * q, i = e & (GT - 1), j = e >> 6;
-      const float2 va = __ldg(reinterpret_cast<const float2 *>(ws + baseA + oAm[i] + oAk[j]));
-      const float2 vb = __ldg(reinterpret_cast<const float2 *>(ws + baseB + oBn[i] + oBk[j]));
-      As[j][i] = make_float2(va.x * sa, va.y * sa);
-      Bs[j][i] = make_float2(vb.x * sb, vb.y * sb);
+      for (int q = 0; q < GK * GT / 256; ++q) {
+        const int e = tid + 256 * q, i = e & (GT - 1), j = e >> 6;
+        const float2 va = __ldg(reinterpret_cast<const float2 *>(ws + baseA + oAm[i] + oAk[j]));
+        const float2 vb = __ldg(reinterpret_cast<const float2 *>(ws + baseB + oBn[i] + oBk[j]));
+        As[j][i] = make_float2(va.x * sa, va.y * sa);
+        Bs[j][i] = make_float2(vb.x * sb, vb.y * sb);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < GK * GT / 256; ++q) {
+        const int e = tid + 256 * q, i = e & (GT - 1), j = e >> 6;
+        const float2 va = __ldg(reinterpret_cast<const float2 *>(ws + baseA + oAm[i] + oAk[j]));
+        As[j][i] = make_float2(va.x * sa, va.y * sa);
+      }
+#pragma unroll
+      for (int q = 0; q < GK * NT / 256; ++q) {
+        const int e = tid + 256 * q, i = e & (NT - 1), j = e / NT;
+        const float2 vb = __ldg(reinterpret_cast<const float2 *>(ws + baseB + oBn[i] + oBk[j]));
+        Bs[j][i] = make_float2(vb.x * sb, vb.y * sb);
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GK; ++kk) {
-      float2 a[4], b[4];
+      float2 a[4], b[TC];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+      for (int c = 0; c < TC; ++c) b[c] = Bs[kk][tx * TC + c];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < TC; ++c) {
           acc[r][c].x = fmaf(a[r].x, b[c].x, fmaf(-a[r].y, b[c].y, acc[r][c].x));
           acc[r][c].y = fmaf(a[r].x, b[c].y, fmaf(a[r].y, b[c].x, acc[r][c].y));
         }
@@ -647,8 +665,8 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      *reinterpret_cast<float2 *>(ws + baseO + oOm[ty * 4 + r] + oOn[tx * 4 + c]) = acc[r][c];
+    for (int c = 0; c < TC; ++c) {
+      *reinterpret_cast<float2 *>(ws + baseO + oOm[ty * 4 + r] + oOn[tx * TC + c]) = acc[r][c];
       lmax = fmax_nan(lmax, absmax2(acc[r][c]));
     }
   record_max(lmax, meta, g.o_meta);
@@ -1120,11 +1138,14 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
   const uint64_t rows = 1ull << d.w_out;
   if (d.gemm >= 0 && gemms) {
     const GemmDesc &g = gemms[d.gemm];
-    const unsigned tiles = 1u << ((g.nm - 6) + (g.nn - 6));
-    if (g.nk >= 5)
-      k_gemm<32><<<dim3(tiles, g.o_bat ? Bp : 1, 1u << g.ns), 256, 0, st>>>(ws, g, meta, hdr, Bp);
-    else
-      k_gemm<16><<<dim3(tiles, g.o_bat ? Bp : 1, 1u << g.ns), 256, 0, st>>>(ws, g, meta, hdr, Bp);
+    const dim3 grid(1u << ((g.nm - 6) + (g.nn - (g.nn >= 6 ? 6 : 5))), g.o_bat ? Bp : 1, 1u << g.ns);
+    if (g.nn >= 6) {
+      if (g.nk >= 5) k_gemm<32, 64><<<grid, 256, 0, st>>>(ws, g, meta, hdr, Bp);
+      else k_gemm<16, 64><<<grid, 256, 0, st>>>(ws, g, meta, hdr, Bp);
+    } else {
+      if (g.nk >= 5) k_gemm<32, 32><<<grid, 256, 0, st>>>(ws, g, meta, hdr, Bp);
+      else k_gemm<16, 32><<<grid, 256, 0, st>>>(ws, g, meta, hdr, Bp);
+    }
     return;
   }
   auto pow2_floor = [](uint64_t v) {

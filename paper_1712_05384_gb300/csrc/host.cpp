@@ -597,10 +597,14 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
         nm += ha && !hb;
         nn += hb && !ha;
       }
-      if (ok && nm >= 6 && nn >= 6 && nm < GMAXB && nn < GMAXB) {
+      // tiles of 64 x 64 or, with a wide batch (many GEMMs per launch), 64 x
+      // 32 outputs: the operand with six or more private kept variables
+      // goes first
+      const int min_side = Bp >= 64 ? 5 : 6;
+      if (ok && std::max(nm, nn) >= 6 && std::min(nm, nn) >= min_side && nm < GMAXB && nn < GMAXB) {
         auto premul = [&](std::vector<int> &grp) { return grp.size() == 1 ? grp[0] : hold(emit(grp, {})); };
         const int a2 = premul(toA), b2 = premul(toB);
-        return emit({a2, b2}, summed, true);
+        return nm >= 6 ? emit({a2, b2}, summed, true) : emit({b2, a2}, summed, true);
       }
     }
     if (nest && inputs.size() >= 3 && k >= 2) {
@@ -1217,7 +1221,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   }
   const int max_fuse = o.max_fuse > 0 ? std::min(o.max_fuse, 16) : 8;
   p->gemm_ok = o.no_gemm == 0;
-  p->trees_ok = o.trees != 0;
+  p->trees_ok = o.trees > 0;
   p->nest_ok = true;
   const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)64 << 30;
 
@@ -2002,6 +2006,21 @@ int qgm_plan_order(const qgm_model *m, const qgm_plan_opts *opts, qgm_plan **out
   if (rc != QGM_OK) {
     delete p;
     return rc;
+  }
+  // trees = 0 (automatic): a batch plan that no resident layout fits runs
+  // stepwise, out of device memory, where contraction trees pay when they
+  // save a clear share of the products
+  if (opts->trees == 0 && opts->output_mode == QGM_OUT_BATCH && p->resident.empty() && !p->grad) {
+    qgm_plan_opts o2 = *opts;
+    o2.trees = 1;
+    qgm_plan *t = new qgm_plan;
+    if (build_plan(m->m, o2, t) == QGM_OK && t->sim.flops < 0.9 * p->sim.flops &&
+        t->ws_bytes <= std::max<int64_t>(2 * p->ws_bytes, p->ws_bytes + ((int64_t)4 << 30))) {
+      delete p;
+      p = t;
+    } else {
+      delete t;
+    }
   }
   *out = p;
   return QGM_OK;
