@@ -382,3 +382,21 @@ def test_host_api_with_page_locked_buffers(executor):
         o = ho.numpy()
         assert np.array_equal(o[0::2] + 1j * o[1::2], a_dev)
     assert np.array_equal(p.amplitudes_host(bits), a_dev)
+
+
+def test_narrow_gemm_tiles_with_wide_batch():
+    # 4x6 depth 30, 64 bitstrings, contraction trees: one GEMM-shaped step has
+    # five private variables on one side and runs with 64 x 32 tiles; the
+    # amplitudes equal the product-sum kernels' (no GEMM) and the oracle's
+    q = Q()
+    c = qi.grid_circuit(4, 6, 30, 0)
+    bits = qi.bitstrings(c.n, 64, 0)
+    m = q.Model(q.Circuit.grid(4, 6, 30, 0))
+    p = q.Plan(m, batch=64, trees=True, executor=1)
+    assert p.info.n_gemm_steps > q.Plan(m, batch=8, trees=True, executor=1).info.n_gemm_steps
+    a = p.bind().amplitudes_host(bits)
+    b = q.Plan(m, batch=64, trees=True, executor=1, gemm=False).bind().amplitudes_host(bits)
+    rel, ab = errors(a, b, c.n)
+    assert rel < 2 * REL_TOL and ab < 2 * ABS_TOL, (rel, ab)
+    rel, ab = errors(a[:4], ve.amplitudes(c, bits[:4]), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
