@@ -187,6 +187,14 @@ typedef struct {
   int32_t resident_chunk;     /* bitstrings per CTA of the resident executor:
                                  1, 2, 4 or 8; 0 = chosen at bind (fewest
                                  waves x chunk on the bound device) */
+  int32_t gemm_split_bf16;    /* 0 (default) or 1: GEMM-shaped steps with at
+                                 least 2^7 rows on one side, 2^5 on the other
+                                 and 2^4 summed entries run on the tensor cores
+                                 (tcgen05) as split-BF16 products: each FP32
+                                 operand value becomes three BF16 terms, the six
+                                 term products above 2^-24 of the product are
+                                 kept and accumulated in FP32; -1: every GEMM
+                                 step on the FP32 cores */
 } qgm_plan_opts;
 
 enum {
@@ -219,6 +227,8 @@ typedef struct {
   int32_t n_tile_steps;       /* batched steps run with a register tile */
   int32_t n_nested_steps;     /* steps whose compiled form sums some variables
                                  in an inner loop over part of the inputs */
+  int32_t n_gemm_tc_steps;    /* of the GEMM steps, those run on the tensor
+                                 cores (qgm_plan_opts.gemm_split_bf16) */
 } qgm_plan_info;
 
 /* Elimination order, slicing, step list and memory layout (Sec. IV, App. A).

@@ -40,7 +40,7 @@ class qgm_plan_opts(C.Structure):
                 ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
                 ("no_gemm", C.c_int32), ("gradients", C.c_int32), ("trees", C.c_int32),
                 ("open_mask", C.c_uint64),
-                ("resident_chunk", C.c_int32)]
+                ("resident_chunk", C.c_int32), ("gemm_split_bf16", C.c_int32)]
 
 
 class qgm_xeb_result(C.Structure):
@@ -55,7 +55,7 @@ class qgm_plan_info(C.Structure):
                 ("workspace_bytes", C.c_int64), ("arena_bytes", C.c_int64),
                 ("bytes_per_slice", C.c_double), ("flops_per_slice", C.c_double),
                 ("max_step_bytes", C.c_double), ("n_gemm_steps", C.c_int32), ("n_tile_steps", C.c_int32),
-                ("n_nested_steps", C.c_int32)]
+                ("n_nested_steps", C.c_int32), ("n_gemm_tc_steps", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -241,7 +241,8 @@ class Model:
 class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
-                 resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=None):
+                 resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=None,
+                 split_bf16=None):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -255,6 +256,9 @@ class Plan:
         o.no_gemm = 0 if gemm else 1
         o.open_mask = open_mask
         o.trees = 0 if trees is None else (1 if trees else -1)
+        # GEMM steps on the tensor cores (split BF16): None or True where
+        # eligible (the default), False: FP32 cores
+        o.gemm_split_bf16 = 0 if split_bf16 is None else (1 if split_bf16 else -1)
         # amplitudes per bitstring: its open qubits run over all 2^k values
         self.n_open = bin(open_mask).count("1") if output_mode == OUT_BATCH else 0
         self._order_buf = None

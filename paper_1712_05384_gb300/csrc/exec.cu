@@ -22,6 +22,7 @@
 // kernel scales that operand by 2^{-e} (exact) with e = floor(log2 max) + 1
 // and adds e to the exponent it passes on.  Partial amplitudes of the slices
 // are summed in FP64 with their exponents applied.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -672,6 +673,270 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
   record_max(lmax, meta, g.o_meta);
 }
 
+// ---------------------------------------------------------------------------
+// GEMM-shaped step on the tensor cores (tcgen05.mma kind::f16, FP32
+// accumulation in tensor memory), split BF16.  Each scaled FP32 operand value
+// x becomes x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0) and
+// x2 = bf16(x - x0 - x1) (the differences are exact in FP32); a real product
+// keeps the six term products x_i y_j with i + j <= 2 (the dropped ones are
+// below 2^-24 |x y|), and the complex product takes four real products: one
+// chunk of 16 summed entries is 24 MMAs of 128 x NT x 16.
+//
+// One CTA of 128 threads forms a 128 x NT output tile of one (s, batch
+// entry): D_re in tensor-memory columns [0, NT), D_im in [NT, 2 NT), tile row
+// r in lane r.  Per chunk, thread r gathers row r of A (and of B, r < NT)
+// through the bit maps, splits it and stores it in shared memory in the
+// K-major layout without swizzle: core matrices of 8 rows x 16 bytes, the two
+// 8-entry halves of a row 128 bytes apart, 8-row groups 256 bytes apart.
+// Thread 0 then issues the chunk's MMAs and commits them to an mbarrier, and
+// the threads gather the next chunk into registers while the tensor cores
+// run.  A plane holds one of the three terms of the real part, the
+// imaginary part or the negated imaginary part (A) of a 16-entry chunk.
+constexpr int TC_M = 128;
+constexpr int TC_PLANE_A = TC_M * 32;  // bytes of one 128 x 16 BF16 plane
+
+__host__ __device__ constexpr int tc_smem_bytes(int nt) {
+  // nine A planes and six B planes; 128-column tiles ask for 80 KB so that
+  // at most two CTAs (2 x 256 tensor-memory columns) share an SM
+  return nt == 128 ? 80 * 1024 : 9 * TC_PLANE_A + 6 * nt * 32;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor: start address, leading byte offset (the
+// next 16 bytes along K: 128), stride byte offset (the next 8-row group: 256),
+// descriptor version 1, no swizzle.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
+         (1ull << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+// Wait (about one second at most) for the completion of the mbarrier phase
+// of the given parity; false when the limit ran out.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+  uint64_t t0, t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
+  }
+}
+
+// 16 consecutive FP32 columns of this warp's 32 lanes, waited for
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Two values -> their three BF16 terms, each as a pair (first value in the
+// low half: the lower address)
+__device__ __forceinline__ void split3(float a, float b, uint32_t &t0, uint32_t &t1, uint32_t &t2) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  const float2 hf = __bfloat1622float2(h);
+  const float ra = a - hf.x, rb = b - hf.y;
+  const __nv_bfloat162 m = __floats2bfloat162_rn(ra, rb);
+  const float2 mf = __bfloat1622float2(m);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(ra - mf.x, rb - mf.y);
+  t0 = *reinterpret_cast<const uint32_t *>(&h);
+  t1 = *reinterpret_cast<const uint32_t *>(&m);
+  t2 = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+template <int NT>
+__global__ void __launch_bounds__(128, 1)
+    k_gemm_tc(char *ws, const __grid_constant__ GemmDesc g, Meta *meta, Header *hdr, int Bp) {
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t tbase;
+  __shared__ int64_t kloA[16], kloB[16], oOn[NT];
+  constexpr int PB = NT * 32;                  // bytes of one NT x 16 BF16 plane
+  constexpr uint32_t COLS = 2 * NT < 32 ? 32 : 2 * NT;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  // the batch entries of one tile are neighbours in the grid (they write
+  // the same output sectors, which then merge in L2)
+  const int nb = g.o_bat ? Bp : 1;
+  const uint64_t tile = blockIdx.x / nb;
+  const int beta = (int)(blockIdx.x - tile * nb);
+  const int lnt = g.nn - (NT == 128 ? 7 : NT == 64 ? 6 : 5);
+  const uint64_t tm = tile >> lnt, tn = tile & ((1ull << lnt) - 1);
+  const uint64_t sidx = blockIdx.y;
+  const int64_t uA = g.a_bat ? (int64_t)Bp * 8 : 8, uB = g.b_bat ? (int64_t)Bp * 8 : 8,
+                uO = g.o_bat ? (int64_t)Bp * 8 : 8;
+  const int64_t baseA = g.a_off + lin_bits(sidx, g.sA, g.ns) * uA + (g.a_bat ? beta * 8 : 0);
+  const int64_t baseB = g.b_off + lin_bits(sidx, g.sB, g.ns) * uB + (g.b_bat ? beta * 8 : 0);
+  const int64_t baseO = g.o_off + lin_bits(sidx, g.sO, g.ns) * uO + (g.o_bat ? beta * 8 : 0);
+  const int64_t rowA = lin_bits(tm * TC_M + tid, g.mA, g.nm) * uA;
+  const int64_t rowO = lin_bits(tm * TC_M + tid, g.mO, g.nm) * uO;
+  const int64_t rowB = tid < NT ? lin_bits(tn * NT + tid, g.nB, g.nn) * uB : 0;
+  if (tid < NT) oOn[tid] = lin_bits(tn * NT + tid, g.nO, g.nn) * uO;
+  if (tid < 16) kloA[tid] = lin_bits((uint64_t)tid, g.kA, 4) * uA;
+  else if (tid < 32) kloB[tid - 16] = lin_bits((uint64_t)(tid - 16), g.kB, 4) * uB;
+  float sa, sb;
+  int ea, eb;
+  operand_scale(meta, g.a_meta, hdr, &sa, &ea);
+  operand_scale(meta, g.b_meta, hdr, &sb, &eb);
+  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
+    meta[g.o_meta].exp = ea + eb + (g.a_meta >= 0 ? meta[g.a_meta].exp : 0) +
+                         (g.b_meta >= 0 ? meta[g.b_meta].exp : 0);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                 "r"(COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  const uint32_t bar_a = smem_u32(&bar);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tbase;
+  const uint32_t sA = smem_u32(tsm), sB = sA + 9 * TC_PLANE_A;
+  const uint32_t rowoff = (uint32_t)((tid >> 3) * 256 + (tid & 7) * 16);
+  float2 ra[16], rb[16];
+  auto gather = [&](int kc) {
+    const int64_t hA = baseA + rowA + lin_bits((uint64_t)kc, g.kA + 4, g.nk - 4) * uA;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) ra[k] = __ldg(reinterpret_cast<const float2 *>(ws + hA + kloA[k]));
+    if (tid < NT) {
+      const int64_t hB = baseB + rowB + lin_bits((uint64_t)kc, g.kB + 4, g.nk - 4) * uB;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) rb[k] = __ldg(reinterpret_cast<const float2 *>(ws + hB + kloB[k]));
+    }
+  };
+  auto put = [&]() {
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      uint32_t re[3][4], im[3][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float2 x = ra[half * 8 + 2 * q], y = ra[half * 8 + 2 * q + 1];
+        split3(x.x * sa, y.x * sa, re[0][q], re[1][q], re[2][q]);
+        split3(x.y * sa, y.y * sa, im[0][q], im[1][q], im[2][q]);
+      }
+      uint8_t *base = tsm + half * 128 + rowoff;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        *reinterpret_cast<uint4 *>(base + t * TC_PLANE_A) = make_uint4(re[t][0], re[t][1], re[t][2], re[t][3]);
+        *reinterpret_cast<uint4 *>(base + (3 + t) * TC_PLANE_A) = make_uint4(im[t][0], im[t][1], im[t][2], im[t][3]);
+        // the negated imaginary part: sign bits flipped (exact)
+        *reinterpret_cast<uint4 *>(base + (6 + t) * TC_PLANE_A) =
+            make_uint4(im[t][0] ^ 0x80008000u, im[t][1] ^ 0x80008000u, im[t][2] ^ 0x80008000u,
+                       im[t][3] ^ 0x80008000u);
+      }
+    }
+    if (tid < NT) {
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        uint32_t re[3][4], im[3][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const float2 x = rb[half * 8 + 2 * q], y = rb[half * 8 + 2 * q + 1];
+          split3(x.x * sb, y.x * sb, re[0][q], re[1][q], re[2][q]);
+          split3(x.y * sb, y.y * sb, im[0][q], im[1][q], im[2][q]);
+        }
+        uint8_t *base = tsm + 9 * TC_PLANE_A + half * 128 + rowoff;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+          *reinterpret_cast<uint4 *>(base + t * PB) = make_uint4(re[t][0], re[t][1], re[t][2], re[t][3]);
+          *reinterpret_cast<uint4 *>(base + (3 + t) * PB) = make_uint4(im[t][0], im[t][1], im[t][2], im[t][3]);
+        }
+      }
+    }
+  };
+  // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major,
+  // N >> 3 at bit 17, M >> 4 at bit 24
+  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+                             ((uint32_t)(TC_M >> 4) << 24);
+  auto issue = [&](int kc) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    uint32_t acc = kc > 0 ? 1u : 0u;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      const int i = t == 2 || t == 4 ? 1 : t == 5 ? 2 : 0;  // term pairs (i, j), i + j <= 2
+      const int j = t == 1 || t == 4 ? 1 : t == 3 ? 2 : 0;
+      const uint64_t ar = tc_desc(sA + i * TC_PLANE_A), ai = tc_desc(sA + (3 + i) * TC_PLANE_A),
+                     an = tc_desc(sA + (6 + i) * TC_PLANE_A);
+      const uint64_t br = tc_desc(sB + j * PB), bi = tc_desc(sB + (3 + j) * PB);
+      tc_mma(tmem, ar, br, idesc, acc);       // re += Ar Br
+      tc_mma(tmem, an, bi, idesc, 1u);        // re -= Ai Bi
+      tc_mma(tmem + NT, ar, bi, idesc, acc);  // im += Ar Bi
+      tc_mma(tmem + NT, ai, br, idesc, 1u);   // im += Ai Br
+      acc = 1u;
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
+                 : "memory");
+  };
+  const int nkc = 1 << (g.nk - 4);
+  bool ok = true;
+  int issued = -1;  // last chunk whose MMAs were issued
+  gather(0);
+  for (int kc = 0; kc < nkc; ++kc) {
+    if (kc > 0) {
+      // the previous chunk's MMAs have read the planes
+      ok = !__syncthreads_or(!tc_wait(bar_a, (uint32_t)(kc - 1) & 1u));
+      if (!ok) break;
+    }
+    put();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) issue(kc);
+    issued = kc;
+    if (kc + 1 < nkc) gather(kc + 1);
+  }
+  if (ok) ok = !__syncthreads_or(!tc_wait(bar_a, (uint32_t)issued & 1u));
+  float lmax = 0.f;
+  if (ok) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+    char *orow = ws + baseO + rowO;
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+      uint32_t re[16], im[16];
+      tc_ld16(tl + c0, re);
+      tc_ld16(tl + NT + c0, im);
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float2 v = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+        *reinterpret_cast<float2 *>(orow + oOn[c0 + j]) = v;
+        lmax = fmax_nan(lmax, absmax2(v));
+      }
+    }
+  } else {
+    // the status says the tile is missing; wait once more (bounded) for the
+    // MMAs in flight before the tensor memory is released
+    if (tid == 0 && hdr) atomicCAS(&hdr->status, 0, QGM_ERR_TIMEOUT);
+    tc_wait(bar_a, (uint32_t)issued & 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
+  record_max(lmax, meta, g.o_meta);
+}
+
 // out[x] += F[x] * 2^exp * c in FP64 (one slice's partial amplitudes), then
 // advance the slice counter.
 __global__ void k_accumulate(const char *ws, int64_t final_off, int final_meta, int final_batched,
@@ -1134,8 +1399,31 @@ static void launch_leaves(qgm_plan *p, const uint64_t *d_bits, int64_t B, cudaSt
 // Grid of one product-sum step: row strides are powers of two so that the
 // kernels can walk rows by table increments.
 static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const GemmDesc *gemms, Meta *meta,
-                           Header *hdr, cudaStream_t st) {
+                           Header *hdr, cudaStream_t st, bool tc = false) {
   const uint64_t rows = 1ull << d.w_out;
+  if (d.gemm >= 0 && gemms && tc && gemm_tc_eligible(gemms[d.gemm])) {
+    // the wider side takes the MMA's 128 rows: out[s, n, m] = sum_k B A is
+    // the same product with the roles exchanged
+    GemmDesc g = gemms[d.gemm];
+    if (g.nm < 7) {
+      std::swap(g.a_off, g.b_off);
+      std::swap(g.a_meta, g.b_meta);
+      std::swap(g.a_bat, g.b_bat);
+      std::swap(g.nm, g.nn);
+      for (int b = 0; b < GMAXB; ++b) {
+        std::swap(g.mA[b], g.nB[b]);
+        std::swap(g.mO[b], g.nO[b]);
+        std::swap(g.kA[b], g.kB[b]);
+        std::swap(g.sA[b], g.sB[b]);
+      }
+    }
+    const int lnt = g.nn >= 7 ? 7 : g.nn;
+    const dim3 grid((1u << ((g.nm - 7) + (g.nn - lnt))) * (g.o_bat ? Bp : 1), 1u << g.ns);
+    if (lnt == 7) k_gemm_tc<128><<<grid, 128, tc_smem_bytes(128), st>>>(ws, g, meta, hdr, Bp);
+    else if (lnt == 6) k_gemm_tc<64><<<grid, 128, tc_smem_bytes(64), st>>>(ws, g, meta, hdr, Bp);
+    else k_gemm_tc<32><<<grid, 128, tc_smem_bytes(32), st>>>(ws, g, meta, hdr, Bp);
+    return;
+  }
   if (d.gemm >= 0 && gemms) {
     const GemmDesc &g = gemms[d.gemm];
     const dim3 grid(1u << ((g.nm - 6) + (g.nn - (g.nn >= 6 ? 6 : 5))), g.o_bat ? Bp : 1, 1u << g.ns);
@@ -1188,7 +1476,7 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
 static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st) {
   char *ws = p->exec->ws;
   launch_step_ws(ws, p->exec->sms, p->Bp, d, p->gemms.data(), reinterpret_cast<Meta *>(ws + p->off_meta),
-                 reinterpret_cast<Header *>(ws + p->off_header), st);
+                 reinterpret_cast<Header *>(ws + p->off_header), st, p->gemm_tc);
 }
 
 static void launch_accumulate(qgm_plan *p, double2 *d_out, int64_t n_out, cudaStream_t st) {
@@ -1343,6 +1631,11 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
   CK(cudaGetDevice(&x->device));
   CK(cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, x->device));
   x->ws = static_cast<char *>(d_workspace);
+  if (p->gemm_tc && !p->gemms.empty()) {
+    CK(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(128)));
+    CK(cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(64)));
+    CK(cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(32)));
+  }
   x->ws_bytes = ws_bytes;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(x->ws + p->off_header, 0, 256, st));

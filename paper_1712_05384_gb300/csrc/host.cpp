@@ -1221,6 +1221,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   }
   const int max_fuse = o.max_fuse > 0 ? std::min(o.max_fuse, 16) : 8;
   p->gemm_ok = o.no_gemm == 0;
+  p->gemm_tc = o.gemm_split_bf16 >= 0;
   p->trees_ok = o.trees > 0;
   p->nest_ok = true;
   const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)64 << 30;
@@ -2049,6 +2050,9 @@ int qgm_plan_get_info(const qgm_plan *p, qgm_plan_info *info) {
   for (const StepDesc &d : p->steps) info->n_tile_steps += d.tile_t > 0;
   info->n_nested_steps = 0;
   for (const StepRec &st : p->sim.steps) info->n_nested_steps += st.k_inner > 0;
+  info->n_gemm_tc_steps = 0;
+  if (p->gemm_tc)
+    for (const GemmDesc &g : p->gemms) info->n_gemm_tc_steps += gemm_tc_eligible(g);
   return QGM_OK;
 }
 

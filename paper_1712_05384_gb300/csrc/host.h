@@ -93,6 +93,14 @@ struct GemmDesc {
   uint8_t kA[GMAXB], kB[GMAXB], sA[GMAXB], sB[GMAXB], sO[GMAXB];
 };
 
+// A GEMM step runs on the tensor cores (split BF16) when one side has at
+// least 2^7 rows (the MMA's M = 128), the other at least 2^5 (N = 32, 64 or
+// 128) and the summed entries come in whole chunks of 16 (one MMA's K).
+inline bool gemm_tc_eligible(const GemmDesc &g) {
+  const int hi = g.nm > g.nn ? g.nm : g.nn, lo = g.nm > g.nn ? g.nn : g.nm;
+  return g.nk >= 4 && hi >= 7 && lo >= 5;
+}
+
 // Leaf factor built on the device per slice: base table over
 // (internal vars | slice vars | output vars), MSB first.
 struct LeafDesc {
@@ -310,6 +318,7 @@ struct qgm_plan {
   int64_t off_image = 0;    // compiled resident kernel: initial shared-memory image (bitstring-independent leaves)
   int executor_pref = 0;    // qgm_plan_opts.executor
   bool gemm_ok = true;      // GEMM-shaped steps run by the GEMM kernel
+  bool gemm_tc = false;     // eligible GEMM steps run on the tensor cores (split BF16)
   bool trees_ok = false;    // buckets of three or more inputs may run as contraction trees
   bool nest_ok = true;      // buckets may be marked for nested evaluation
   qgm_exec_state *exec = nullptr;

@@ -252,13 +252,16 @@ def test_gemm_steps_vs_state_vector(rows, cols, depth, B):
     c = qi.grid_circuit(rows, cols, depth, 0)
     bits = qi.bitstrings(c.n, B, 0)
     ref = sv.amplitudes(c, bits)
-    for gemm in (True, False):
+    # GEMM steps on the tensor cores (split BF16, the default), on the FP32
+    # cores, and no GEMM steps (product-sum kernels)
+    for gemm, split in ((True, None), (True, False), (False, None)):
         p = q.Plan(q.Model(q.Circuit.grid(rows, cols, depth, 0)), order_kind=1, batch=B,
-                   executor=1, gemm=gemm)
+                   executor=1, gemm=gemm, split_bf16=split)
         assert (p.info.n_gemm_steps > 0) == gemm
+        assert (p.info.n_gemm_tc_steps > 0) == (gemm and split is None)
         a = p.bind().amplitudes_host(bits)
         rel, ab = errors(a, ref, c.n)
-        assert rel < REL_TOL and ab < ABS_TOL, (gemm, rel, ab)
+        assert rel < REL_TOL and ab < ABS_TOL, (gemm, split, rel, ab)
 
 
 def test_grid5x9_d40_two_plans_and_porter_thomas():
@@ -385,15 +388,17 @@ def test_host_api_with_page_locked_buffers(executor):
 
 
 def test_narrow_gemm_tiles_with_wide_batch():
-    # 4x6 depth 30, 64 bitstrings, contraction trees: one GEMM-shaped step has
-    # five private variables on one side and runs with 64 x 32 tiles; the
+    # 4x6 depth 30, 64 bitstrings, contraction trees, FP32-core GEMM: one
+    # GEMM-shaped step has five private variables on one side and runs with
+    # 64 x 32 tiles; the
     # amplitudes equal the product-sum kernels' (no GEMM) and the oracle's
     q = Q()
     c = qi.grid_circuit(4, 6, 30, 0)
     bits = qi.bitstrings(c.n, 64, 0)
     m = q.Model(q.Circuit.grid(4, 6, 30, 0))
-    p = q.Plan(m, batch=64, trees=True, executor=1)
+    p = q.Plan(m, batch=64, trees=True, executor=1, split_bf16=False)
     assert p.info.n_gemm_steps > q.Plan(m, batch=8, trees=True, executor=1).info.n_gemm_steps
+    assert p.info.n_gemm_tc_steps == 0
     a = p.bind().amplitudes_host(bits)
     b = q.Plan(m, batch=64, trees=True, executor=1, gemm=False).bind().amplitudes_host(bits)
     rel, ab = errors(a, b, c.n)

@@ -167,6 +167,23 @@ def test_contraction_trees_need_fewer_products():
     assert st["k"].sum() == tree.info.n_free
 
 
+@pytest.mark.parametrize("rows,cols,depth,B,n_gemm,n_tc", [(4, 5, 30, 16, 1, 1), (4, 6, 34, 6, 3, 2),
+                                                         (4, 8, 40, 4, 3, 3)])
+def test_tensor_core_gemm_steps(rows, cols, depth, B, n_gemm, n_tc):
+    # GEMM steps (min-fill) and their (m, n, k) variable counts:
+    # 4x5 d30 (7, 6, 6); 4x6 d34 (8, 6, 8), (9, 6, 4), (6, 6, 8); 4x8 d40
+    # (8, 8, 8), (11, 7, 8), (11, 9, 8).  A step goes to the tensor cores when
+    # one side has >= 7 variables (the MMA's 128 rows), the other >= 5 and
+    # k >= 4 (16 summed entries per MMA): all but (6, 6, 8)
+    m = Q.Model(Q.Circuit.grid(rows, cols, depth, 0))
+    p = Q.Plan(m, order_kind=1, batch=B)
+    assert (p.info.n_gemm_steps, p.info.n_gemm_tc_steps) == (n_gemm, n_tc)
+    assert Q.Plan(m, order_kind=1, batch=B, split_bf16=True).info.n_gemm_tc_steps == n_tc
+    off = Q.Plan(m, order_kind=1, batch=B, split_bf16=False)
+    assert (off.info.n_gemm_steps, off.info.n_gemm_tc_steps) == (n_gemm, 0)
+    assert Q.Plan(m, order_kind=1, batch=B, gemm=False).info.n_gemm_tc_steps == 0
+
+
 def test_nested_steps_keep_the_product_sum():
     # 5x5 depth 20: the two widest buckets sum part of their variables in an
     # inner loop over the inputs that alone hold them; the steps still list
