@@ -33,8 +33,9 @@ UNIT = "amplitudes/s"
 L2_BYTES = 129 * 2 ** 20
 
 # DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
-# the sha1 of the kernel source it was taken on (null once the source changed).
-NCU_TRAFFIC = {"a901ede19ea7": 141824.0}   # qgm_resident_plan, profiles/qgm_resident_plan_grid5x5_d20_b1024.md
+# the sha1 of the kernel source it was taken on (null once the source changed):
+# for the compiled resident executor, the CUDA source generated for the plan.
+NCU_TRAFFIC = {"e03135235b82": 141824.0}   # qgm_resident_plan, profiles/qgm_resident_plan_grid5x5_d20_b1024.md
 
 
 def parse():
@@ -67,10 +68,15 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_hash():
+def kernel_hash(plan=None, chunk=1):
+    """sha1 (12 hex digits) of the dominant kernel's source: the CUDA source
+    generated for the plan when the compiled resident executor runs it, else
+    exec.cu (the other executors' kernels)."""
     h = hashlib.sha1()
-    for name in ("exec.cu", "jit.cpp"):
-        with open(os.path.join(ROOT, "paper_1712_05384_gb300", "csrc", name), "rb") as f:
+    if plan is not None:
+        h.update(plan.kernel_source(chunk, 0).encode())
+    else:
+        with open(os.path.join(ROOT, "paper_1712_05384_gb300", "csrc", "exec.cu"), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
 
@@ -279,7 +285,7 @@ def main():
         flush.fill_(1.0)
         ms += plan.profile(d_bits, d_out, B=B, stream=stream)
     ms /= reps
-    traffic = NCU_TRAFFIC.get(kernel_hash())
+    traffic = NCU_TRAFFIC.get(kernel_hash(plan if ex_kind == q.EXEC_COMPILED else None, ex_chunk))
     if ex_kind in (q.EXEC_RESIDENT, q.EXEC_COMPILED):
         # all intermediates live in shared memory: bound by the SM's FP32/ALU
         # issue, peak = 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
