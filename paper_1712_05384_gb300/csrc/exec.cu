@@ -677,10 +677,11 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
 // GEMM-shaped step on the tensor cores (tcgen05.mma kind::f16, FP32
 // accumulation in tensor memory), split BF16.  Each scaled FP32 operand value
 // x becomes x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0) and
-// x2 = bf16(x - x0 - x1) (the differences are exact in FP32); a real product
-// keeps the six term products x_i y_j with i + j <= 2 (the dropped ones are
-// below 2^-24 |x y|), and the complex product takes four real products: one
-// chunk of 16 summed entries is 24 MMAs of 128 x NT x 16.
+// x2 = bf16(x - x0 - x1) (the differences are exact in FP32, and the three
+// 8-bit terms hold x exactly); a real product keeps the six term products
+// x_i y_j with i + j <= 2 (each dropped one is at most about 2^-24 |x y|), and
+// the complex product takes four real products: one chunk of 16 summed
+// entries is 24 MMAs of 128 x NT x 16.
 //
 // One CTA of 128 threads forms a 128 x NT output tile of one (s, batch
 // entry): D_re in tensor-memory columns [0, NT), D_im in [NT, 2 NT), tile row
