@@ -315,7 +315,8 @@ int qgm_plan_kernel_source(const qgm_plan *p, int32_t chunk, int32_t part, int32
  * device).  Runs the plan with the stepwise kernels, their scratch being one
  * static device array of QGM_STATIC_SCRATCH_BYTES that every GPU loading this
  * library holds until exit; no qgm_plan_bind is needed and nothing is
- * allocated.  d_bitstrings: device uint64[B]; d_out: device double[2B].
+ * allocated.  GEMM-shaped steps run on the FP32 cores here (the tensor-core
+ * kernel's shared-memory limit is raised at bind).  d_bitstrings: device uint64[B]; d_out: device double[2B].
  * The first call on a device (that device current) looks the array's device
  * address up with cudaGetSymbolAddress; make that first call before any
  * stream capture.  Calls share the array: each reloads the plan's tables and
