@@ -322,6 +322,7 @@ def main():
                    "max_clique": info.max_clique, "steps_per_pass": info.n_steps,
                    "slices": info.n_slices, "parallelism": f"replicas{world}",
                    "executor": {1: "stepwise", 2: "resident", 3: "compiled resident"}.get(ex_kind), "chunk": ex_chunk,
+                   "gemm_steps": info.n_gemm_steps, "gemm_steps_split_bf16": info.n_gemm_tc_steps,
                    "l2": "flushed between timed steps (264 MB write, untimed)"},
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * B,
                 "d2h_bytes_per_step": 16 * B},
