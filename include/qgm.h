@@ -251,6 +251,13 @@ int qgm_plan_get_step_kernels(const qgm_plan *p, int32_t *kind, int64_t cap);
 /* Algorithmic cost of step s: bytes[s] (inputs read once + output written,
  * complex64) and flops[s] (real flops of the products and sums). */
 int qgm_plan_get_step_cost(const qgm_plan *p, double *bytes, double *flops, int64_t cap);
+/* Shapes of the GEMM-shaped steps (Sec. IV, Eq. par_sum with two large
+ * operands sharing every summed variable): for the c-th such step, c < cap,
+ * rec[9c .. 9c+8] = step index, nm, nn, nk, ns (variables private to A, to B,
+ * summed, shared and kept), A batched, B batched, output batched, and 1 when
+ * the step runs on the tensor cores.  *n = the number of GEMM steps; rec may
+ * be NULL to query it.  Host only. */
+int qgm_plan_get_gemm(const qgm_plan *p, int32_t *rec, int64_t cap, int64_t *n);
 void qgm_plan_free(qgm_plan *p);
 
 /* ------------------------------------------------------------- execution */

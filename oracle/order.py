@@ -17,6 +17,11 @@ the caller.
 * ``treewidth_exact``: subset dynamic programme TW(S) = min_v max(TW(S-v),
   |Q(S-v, v)|) (Bodlaender, Fomin, Koster, Kratsch, Thilikos 2006); small
   graphs only, used to pin the heuristics from below.
+* ``cliques`` and ``slice_greedy``: the cliques an order makes, and slicing
+  (conditioning on variables, Sec. IV's remark that fixing a variable splits
+  the sum into independent parts) chosen greedily: repeatedly fix the
+  variable that lies in the most cliques of the largest size (ties: smallest
+  id), removing it from the graph before the cliques are recounted.
 * ``line_graph``: App. E's construction.
 * ``tensor_network``: App. E's tensor network of a circuit, one tensor per
   gate, as its wire segments between two gates (the segments to the fixed
@@ -93,6 +98,46 @@ def min_fill(adj, keep=()):
         _eliminate(g, v)
         order.append(v)
     return order, w
+
+
+def cliques(adj, order, removed=()):
+    """Cliques (vertex + remaining neighbours) along ``order`` on the graph
+    without the vertices in ``removed``; vertices of ``removed`` are skipped."""
+    removed = set(removed)
+    g = {v: set(n) - removed for v, n in adj.items() if v not in removed}
+    out = []
+    for v in order:
+        if v in removed:
+            continue
+        out.append({v} | g[v])
+        _eliminate(g, v)
+    return out
+
+
+def slice_greedy(adj, order, n_slices=None, max_clique=None, allowed=None):
+    """Greedy slicing: fix, one at a time, the variable (from ``allowed``,
+    default the vertices of ``order``) in the most cliques of the largest
+    size along ``order``, ties to the smallest id; stop after ``n_slices``
+    variables or once the largest clique is at most ``max_clique``."""
+    allowed = set(order if allowed is None else allowed)
+    chosen = []
+    while True:
+        cl = cliques(adj, order, chosen)
+        mx = max((len(c) for c in cl), default=0)
+        if n_slices is not None and len(chosen) >= n_slices:
+            break
+        if max_clique is not None and mx <= max_clique:
+            break
+        count = {}
+        for c in cl:
+            if len(c) == mx:
+                for v in c:
+                    if v in allowed:
+                        count[v] = count.get(v, 0) + 1
+        if not count:
+            break
+        chosen.append(min(count, key=lambda v: (-count[v], v)))
+    return chosen
 
 
 def qubit_rank(rows, cols, transpose=False):

@@ -87,6 +87,7 @@ _SIGS = {
     "qgm_plan_get_steps": [_P, _I32P, _I32P, _I32P, _I32P, C.c_int64],
     "qgm_plan_get_step_kernels": [_P, _I32P, C.c_int64],
     "qgm_plan_get_step_cost": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64],
+    "qgm_plan_get_gemm": [_P, _I32P, C.c_int64, _I64P],
     "qgm_plan_profile": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), _P],
     "qgm_plan_free": [_P],
     "qgm_plan_bind": [_P, _P, C.c_size_t, _P],
@@ -309,6 +310,17 @@ class Plan:
         check(lib().qgm_plan_get_step_cost(self._h, b.ctypes.data_as(C.POINTER(C.c_double)),
                                            f.ctypes.data_as(C.POINTER(C.c_double)), n))
         return b[:n], f[:n]
+
+    def gemm_shapes(self):
+        """GEMM-shaped steps: list of dicts (step, nm, nn, nk, ns, a_bat,
+        b_bat, o_bat, tc) -- 2^nm x 2^nn outputs, 2^nk summed entries, for
+        each of the 2^ns shared indices (and batch entry when batched)."""
+        n = C.c_int64()
+        check(lib().qgm_plan_get_gemm(self._h, None, 0, C.byref(n)))
+        a = np.zeros(9 * max(n.value, 1), dtype=np.int32)
+        check(lib().qgm_plan_get_gemm(self._h, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
+        keys = ("step", "nm", "nn", "nk", "ns", "a_bat", "b_bat", "o_bat", "tc")
+        return [dict(zip(keys, map(int, a[9 * c: 9 * c + 9]))) for c in range(n.value)]
 
     # ------------------------------------------------------------ device
     def bind(self, workspace=None, stream=None):

@@ -1300,11 +1300,27 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     std::vector<int> svars;
     SimResult r = simulate(p, c.second, sliced, max_fuse, false);
     while (r.arena_peak > budget && svars.size() < 40) {
-      // the variable held by the most tensors of the largest size
+      // the variable in the most cliques of the largest size along the
+      // order, on the graph without the variables sliced so far (ties:
+      // smallest id)
+      std::vector<char> ig = in_graph;
+      for (int v = 0; v < m.n_vars; ++v)
+        if (sliced[v]) ig[v] = 0;
+      Graph gs = make_graph(p, ig);
+      std::vector<std::vector<int>> cl;
+      size_t mx = 0;
+      for (int v : c.second) {
+        if (sliced[v]) continue;
+        std::vector<int> q = gs.nbrs(v);
+        q.push_back(v);
+        mx = std::max(mx, q.size());
+        cl.push_back(std::move(q));
+        gs.eliminate(v);
+      }
       std::vector<int> cnt(m.n_vars, 0);
-      for (const SymTensor &t : r.tensors)
-        if (t.leaf < 0 && t.entries == r.max_entries)
-          for (int v : t.vars)
+      for (const auto &q : cl)
+        if (q.size() == mx)
+          for (int v : q)
             if (p->var_role[v] == 0) cnt[v]++;
       int bv = -1;
       for (int v = 0; v < m.n_vars; ++v)
@@ -2102,6 +2118,34 @@ int qgm_plan_get_step_kernels(const qgm_plan *p, int32_t *kind, int64_t cap) {
     const StepDesc &d = p->steps[s];
     kind[s] = d.gemm >= 0 ? 3 : (d.tile_t > 0 ? 2 : (d.batched_out ? 1 : 0));
   }
+  return QGM_OK;
+}
+
+int qgm_plan_get_gemm(const qgm_plan *p, int32_t *rec, int64_t cap, int64_t *n) {
+  if (!p || !n) {
+    set_error("qgm_plan_get_gemm: null argument");
+    return QGM_ERR_ARG;
+  }
+  int64_t c = 0;
+  for (size_t s = 0; s < p->steps.size(); ++s) {
+    const StepDesc &d = p->steps[s];
+    if (d.gemm < 0) continue;
+    if (rec && c < cap) {
+      const GemmDesc &g = p->gemms[d.gemm];
+      int32_t *r = rec + 9 * c;
+      r[0] = (int32_t)s;
+      r[1] = g.nm;
+      r[2] = g.nn;
+      r[3] = g.nk;
+      r[4] = g.ns;
+      r[5] = g.a_bat;
+      r[6] = g.b_bat;
+      r[7] = g.o_bat;
+      r[8] = p->gemm_tc && gemm_tc_eligible(g) ? 1 : 0;
+    }
+    ++c;
+  }
+  *n = c;
   return QGM_OK;
 }
 

@@ -119,7 +119,10 @@ def test_slicing_respects_budget():
     assert p.info.n_slices > 1 and p.info.arena_bytes <= budget
     sv = p.slice_vars()
     assert len(sv) == p.info.n_slice_vars and len(set(sv)) == len(sv)
-    assert not set(sv) & set(p.order()) or True
+    # sliced variables are free variables of the order (they are skipped
+    # there), and slicing narrows the order's cliques
+    assert set(sv) <= set(p.order()) and p.info.n_free == len(p.order())
+    assert p.info.max_clique < full.info.max_clique
     with pytest.raises(Q.QgmError):
         Q.Plan(m, order_kind=Q.ORDER_MINFILL, batch=64, mem_budget_bytes=1024)
 
@@ -244,3 +247,24 @@ def test_observable_circuit_reproduces_expectation(rows, cols, depth, seed, paul
     assert Q.Circuit.grid(rows, cols, depth, seed).observable("I" * c.n)[0] is None
     with pytest.raises(Q.QgmError):
         Q.Circuit.grid(rows, cols, depth, seed).observable("Q" * c.n)
+
+
+@pytest.mark.parametrize("rows,cols,depth,batch,div", [
+    (5, 5, 20, 64, 3), (5, 5, 20, 64, 20), (6, 6, 25, 8, 4), (4, 5, 30, 16, 10), (5, 9, 40, 1, 64)])
+def test_slicer_bit_exact(rows, cols, depth, batch, div):
+    # Slicing conditions on variables (Sec. IV); the choice is the greedy
+    # rule restated independently in oracle.order.slice_greedy: the variable
+    # in the most largest-size cliques along the order, ties to the smallest
+    # id.  The library stops when its live set fits the budget; the oracle is
+    # asked for the same number of variables and must pick the same ones.
+    m = Q.Model(Q.Circuit.grid(rows, cols, depth, 0))
+    full = Q.Plan(m, order_kind=Q.ORDER_MINFILL, batch=batch)
+    p = Q.Plan(m, order_kind=Q.ORDER_MINFILL, batch=batch, mem_budget_bytes=full.info.arena_bytes // div)
+    sv = [int(v) for v in p.slice_vars()]
+    assert len(sv) >= 1
+    om = ugm.build(qi.grid_circuit(rows, cols, depth, 0))
+    adj = O.graph(om)
+    order = [int(v) for v in p.order()]
+    assert O.slice_greedy(adj, order, n_slices=len(sv)) == sv
+    # the reported width is the order's largest clique without those variables
+    assert p.info.max_clique == max(len(c) for c in O.cliques(adj, order, sv))

@@ -80,3 +80,25 @@ def test_bitstrings_uniform_and_seeded():
     assert (a == b).all() and a.max() < (1 << 25)
     bits = ((a[:, None] >> np.arange(25, dtype=np.uint64)) & np.uint64(1)).astype(float)
     assert np.all(np.abs(bits.mean(0) - 0.5) < 0.05)
+
+
+def test_seed0_circuits_match_golden():
+    # tests/golden/circuits_seed0.json (written by tests/golden/make_golden.py
+    # from qgm_inputs): the sha256 of each workload's canonical seed-0 gate
+    # list and its gate counts; the C++ generator is checked against this
+    # generator gate by gate in tests/test_host_plan.py
+    import hashlib
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "circuits_seed0.json")) as f:
+        gold = json.load(f)["circuits"]
+    assert set(gold) == set(qi.WORKLOADS)
+    for name, (rows, cols, depth, _, param) in qi.WORKLOADS.items():
+        c = qi.grid_circuit(rows, cols, depth, 0, param=param)
+        gl = [(int(g.kind), int(g.cycle), int(g.q0), int(g.q1), f"{float(g.theta):.17g}", f"{float(g.phi):.17g}")
+              for g in c.gates]
+        assert hashlib.sha256(json.dumps(gl).encode()).hexdigest() == gold[name]["sha256"], name
+        assert len(gl) == gold[name]["n_gates"]
+        # every qubit starts with H and gets T as its first later one-qubit
+        # gate, so H and T each number n
+        assert gold[name]["by_kind"]["0"] == rows * cols and gold[name]["by_kind"]["3"] == rows * cols
