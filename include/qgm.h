@@ -187,14 +187,21 @@ typedef struct {
   int32_t resident_chunk;     /* bitstrings per CTA of the resident executor:
                                  1, 2, 4 or 8; 0 = chosen at bind (fewest
                                  waves x chunk on the bound device) */
-  int32_t gemm_split_bf16;    /* 0 (default) or 1: GEMM-shaped steps with at
-                                 least 2^7 rows on one side, 2^5 on the other
-                                 and 2^4 summed entries run on the tensor cores
-                                 (tcgen05) as split-BF16 products: each FP32
-                                 operand value becomes three BF16 terms, the six
-                                 term products above 2^-24 of the product are
-                                 kept and accumulated in FP32; -1: every GEMM
-                                 step on the FP32 cores */
+  int32_t gemm_precision;     /* GEMM-shaped steps whose tensor-core form exists
+                                 (one side >= 128 rows, batch entries counted
+                                 when the other side has no batch axis; the
+                                 other >= 32; 16 summed entries per chunk) run
+                                 on the tensor cores with FP32 accumulation
+                                 as split products of 16-bit terms:
+                                 0 (default) or 2: split FP16 -- each scaled
+                                 FP32 value x = h + l, h = fp16(x),
+                                 l = fp16(x - h), the products h h' + h l' +
+                                 l h' (22 significant bits, 12 MMAs per chunk
+                                 of a complex product);
+                                 1: split BF16 -- three 8-bit terms, the six
+                                 term products above 2^-24 (24 MMAs);
+                                 -1: every GEMM step on the FP32 cores (plain
+                                 complex64) */
 } qgm_plan_opts;
 
 enum {
@@ -323,7 +330,9 @@ int qgm_plan_kernel_source(const qgm_plan *p, int32_t chunk, int32_t part, int32
  * static device array of QGM_STATIC_SCRATCH_BYTES that every GPU loading this
  * library holds until exit; no qgm_plan_bind is needed and nothing is
  * allocated.  GEMM-shaped steps run on the FP32 cores here (the tensor-core
- * kernel's shared-memory limit is raised at bind).  d_bitstrings: device uint64[B]; d_out: device double[2B].
+ * kernel's shared-memory limit is raised at bind).  d_bitstrings: device
+ * uint64[B]; d_out: device double[2 * B * 2^k] with k = popcount(open_mask)
+ * (entry b * 2^k + c as in qgm_amplitudes; k = 0 gives double[2B]).
  * The first call on a device (that device current) looks the array's device
  * address up with cudaGetSymbolAddress; make that first call before any
  * stream capture.  Calls share the array: each reloads the plan's tables and

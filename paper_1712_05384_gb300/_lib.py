@@ -40,7 +40,7 @@ class qgm_plan_opts(C.Structure):
                 ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
                 ("no_gemm", C.c_int32), ("gradients", C.c_int32), ("trees", C.c_int32),
                 ("open_mask", C.c_uint64),
-                ("resident_chunk", C.c_int32), ("gemm_split_bf16", C.c_int32)]
+                ("resident_chunk", C.c_int32), ("gemm_precision", C.c_int32)]
 
 
 class qgm_xeb_result(C.Structure):
@@ -243,7 +243,7 @@ class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
                  resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=None,
-                 split_bf16=None):
+                 split_bf16=None, precision=None):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -257,9 +257,12 @@ class Plan:
         o.no_gemm = 0 if gemm else 1
         o.open_mask = open_mask
         o.trees = 0 if trees is None else (1 if trees else -1)
-        # GEMM steps on the tensor cores (split BF16): None or True where
-        # eligible (the default), False: FP32 cores
-        o.gemm_split_bf16 = 0 if split_bf16 is None else (1 if split_bf16 else -1)
+        # GEMM steps: "fp16" (split FP16 on the tensor cores, the default
+        # where eligible), "bf16" (split BF16 on the tensor cores) or "fp32"
+        # (FP32 cores); split_bf16=True/False is the same as "bf16"/"fp32"
+        if precision is None and split_bf16 is not None:
+            precision = "bf16" if split_bf16 else "fp32"
+        o.gemm_precision = {None: 0, "fp16": 2, "bf16": 1, "fp32": -1}[precision]
         # amplitudes per bitstring: its open qubits run over all 2^k values
         self.n_open = bin(open_mask).count("1") if output_mode == OUT_BATCH else 0
         self._order_buf = None

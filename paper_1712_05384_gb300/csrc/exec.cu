@@ -23,6 +23,7 @@
 // and adds e to the exponent it passes on.  Partial amplitudes of the slices
 // are summed in FP64 with their exponents applied.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -675,40 +676,49 @@ __global__ void __launch_bounds__(256) k_gemm(char *ws, const GemmDesc g, Meta *
 
 // ---------------------------------------------------------------------------
 // GEMM-shaped step on the tensor cores (tcgen05.mma kind::f16, FP32
-// accumulation in tensor memory), split BF16.  Each scaled FP32 operand value
-// x becomes x0 + x1 + x2 with x0 = bf16(x), x1 = bf16(x - x0) and
-// x2 = bf16(x - x0 - x1) (the differences are exact in FP32, and the three
-// 8-bit terms hold x exactly); a real product keeps the six term products
-// x_i y_j with i + j <= 2 (each dropped one is at most about 2^-24 |x y|), and
-// the complex product takes four real products: one chunk of 16 summed
-// entries is 24 MMAs of 128 x NT x 16.
+// accumulation in tensor memory) as split products of 16-bit terms.
 //
-// One CTA of 128 threads forms a 128 x NT output tile of one (s, batch
-// entry): D_re in tensor-memory columns [0, NT), D_im in [NT, 2 NT), tile row
-// r in lane r.  Per chunk, thread r gathers row r of A (and of B, r < NT)
-// through the bit maps, splits it and stores it in shared memory in the
-// K-major layout without swizzle: core matrices of 8 rows x 16 bytes, the two
-// 8-entry halves of a row 128 bytes apart, 8-row groups 256 bytes apart.
-// Thread 0 then issues the chunk's MMAs and commits them to an mbarrier, and
-// the threads gather the next chunk into registers while the tensor cores
-// run.  A plane holds one of the three terms of the real part, the
-// imaginary part or the negated imaginary part (A) of a 16-entry chunk.
-constexpr int TC_M = 128;
-constexpr int TC_PLANE_A = TC_M * 32;  // bytes of one 128 x 16 BF16 plane
+// Split.  Each operand value x, scaled by a power of two from the operand's
+// recorded maximum, is written as a sum of 16-bit terms once, by k_split,
+// into "planes" laid out exactly as the MMA reads them (see TcCfg):
+//  - FP16 (4 planes: re high, re low, im high, im low): the operand's
+//    maximum is put in [2^14, 2^15) (FP16's largest value is 65504),
+//    h = fp16(x) and l = fp16(x - h) (the difference is exact in FP32), so
+//    x - h - l is below 2^-22 |x| (below 2^-39 of the maximum where l is
+//    subnormal); a real product keeps h h' + h l' + l h', the dropped l l'
+//    being below 2^-22 |x x'|: three MMAs;
+//  - BF16 (6 planes: three terms of re, three of im): maximum in [0.5, 1),
+//    x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0 - x1) hold x exactly;
+//    the six term products x_i y_j with i + j <= 2 are kept (each dropped one
+//    is at most about 2^-24 |x y|): six MMAs.
+// A complex product takes four real ones -- re += Ar Br - Ai Bi (the minus
+// from the instruction's negate-A bit), im += Ar Bi + Ai Br -- so a chunk of
+// 16 summed entries is 12 (FP16) or 24 (BF16) MMAs of 128 x NT x 16.
+//
+// Product.  One CTA of 128 threads per 128 x NT output tile of one instance.
+// Warp 0 (one lane) streams the tile's plane blocks, one chunk per stage, with
+// bulk asynchronous copies (cp.async.bulk, the TMA unit) into a ring of
+// shared-memory stages, each completing a "full" mbarrier by its byte count;
+// warp 1 (one lane) waits for a stage, issues its MMAs and commits them to the
+// stage's "empty" mbarrier, which frees the stage for the next copy; after the
+// last chunk it commits to "done".  D_re sits in tensor-memory columns
+// [0, NT), D_im in [NT, 2 NT), tile row r in lane r; the four warps then read
+// their 32 lanes back (tcgen05.ld), undo the terms' scale, store through the
+// output's bit maps and record the maximum for the rescale.
+//
+// Every wait is bounded (about one second of %globaltimer).  A wait runs out
+// only if a copy or an MMA never completes; the kernel then stops issuing,
+// records QGM_ERR_TIMEOUT, and still ends with the MMA thread's final commit
+// (tcgen05.commit tracks every MMA that thread issued), which the epilogue
+// waits for before the tensor memory is released.
 
-__host__ __device__ constexpr int tc_smem_bytes(int nt) {
-  // nine A planes and six B planes; 128-column tiles ask for 80 KB so that
-  // at most two CTAs (2 x 256 tensor-memory columns) share an SM
-  return nt == 128 ? 80 * 1024 : 9 * TC_PLANE_A + 6 * nt * 32;
-}
-
+// Shared-memory matrix descriptor, K-major without swizzle: start address,
+// leading byte offset (the next 8 summed entries: 128 B), stride byte offset
+// (the next 8-row group: 256 B), descriptor version 1.
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Shared-memory matrix descriptor: start address, leading byte offset (the
-// next 16 bytes along K: 128), stride byte offset (the next 8-row group: 256),
-// descriptor version 1, no swizzle.
 __device__ __forceinline__ uint64_t tc_desc(uint32_t addr) {
   return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(256 >> 4) << 32) |
          (1ull << 46);
@@ -721,11 +731,16 @@ __device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint3
       "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Wait (about one second at most) for the completion of the mbarrier phase
 // of the given parity; false when the limit ran out.
 __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-  uint64_t t0, t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  const uint64_t t0 = gtimer();
   while (true) {
     uint32_t done;
     asm volatile(
@@ -735,9 +750,12 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (t - t0 > 1000000000ull) return false;
+    if (gtimer() - t0 > 1000000000ull) return false;
   }
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
 
 // 16 consecutive FP32 columns of this warp's 32 lanes, waited for
@@ -765,177 +783,295 @@ __device__ __forceinline__ void split3(float a, float b, uint32_t &t0, uint32_t 
   t2 = *reinterpret_cast<const uint32_t *>(&l);
 }
 
-template <int NT>
-__global__ void __launch_bounds__(128, 1)
-    k_gemm_tc(char *ws, const __grid_constant__ GemmDesc g, Meta *meta, Header *hdr, int Bp) {
-  extern __shared__ __align__(1024) uint8_t tsm[];
-  __shared__ __align__(8) uint64_t bar;
-  __shared__ uint32_t tbase;
-  __shared__ int64_t kloA[16], kloB[16], oOn[NT];
-  constexpr int PB = NT * 32;                  // bytes of one NT x 16 BF16 plane
+// Two values -> their FP16 high and low terms, each as a pair
+__device__ __forceinline__ void split2h(float a, float b, uint32_t &t0, uint32_t &t1) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  t0 = *reinterpret_cast<const uint32_t *>(&h);
+  t1 = *reinterpret_cast<const uint32_t *>(&l);
+}
+
+// One operand of a tensor-core step: its rows (m or n variables, batch
+// entries folded in when `fold`), summed and shared variables by bit
+// position in the operand's own index.
+struct SplitArgs {
+  int64_t src_off, dst_off;  // complex64 operand; its plane region
+  int32_t meta, batched, fold, perbeta, Bp;
+  int32_t nr, nk, ns;        // row, summed and shared variables
+  int32_t tr;                // rows per tile (128 for the M side, NT for N)
+  int64_t rows, rtiles, kc;  // rows per instance, row tiles, chunks of 16
+  int32_t fp16;              // 1: FP16 terms (4 planes), 0: BF16 (6 planes)
+  uint8_t rX[GMAXB], kX[GMAXB], sX[GMAXB];
+};
+
+// Thread = (batch entry b when per entry, row, 8 consecutive summed entries,
+// shared index), b fastest, then the row: reads of neighbouring threads share
+// sectors and each thread writes one 16-byte core-matrix row per plane.
+template <int P>
+__global__ void __launch_bounds__(256) k_split(char *ws, const __grid_constant__ SplitArgs a, Meta *meta,
+                                                Header *hdr) {
+  float sc;
+  int e;
+  operand_scale(meta, a.meta, hdr, &sc, &e);
+  if (P == 4) sc *= 32768.f;  // maximum in [2^14, 2^15): FP16 terms keep 22 bits down to 2^-18 of it
+  const int64_t nb = a.perbeta ? a.Bp : 1;
+  const int64_t RP = a.rtiles * a.tr, KG = a.kc * 2;
+  const int64_t n_items = ((int64_t)1 << a.ns) * KG * RP * nb;
+  const int64_t u = a.batched ? (int64_t)a.Bp * 8 : 8;
+  const int64_t pbytes = (int64_t)a.tr * 32;
+  for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n_items;
+       it += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = it % nb;
+    int64_t t = it / nb;
+    const int64_t rho = t % RP;
+    t /= RP;
+    const int64_t kg = t % KG;
+    const int64_t s = t / KG;
+    float2 v[8];
+    if (rho < a.rows) {
+      const int64_t m = a.fold ? rho / a.Bp : rho;
+      const int64_t beta = a.fold ? rho % a.Bp : b;
+      const int64_t base = a.src_off + (lin_bits((uint64_t)s, a.sX, a.ns) + lin_bits((uint64_t)m, a.rX, a.nr) +
+                                        lin_bits((uint64_t)(kg * 8), a.kX, a.nk)) * u +
+                           (a.batched ? beta * 8 : 0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const float2 x = __ldg(reinterpret_cast<const float2 *>(ws + base + lin_bits((uint64_t)q, a.kX, 3) * u));
+        v[q] = make_float2(x.x * sc, x.y * sc);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = make_float2(0.f, 0.f);
+    }
+    const int64_t inst = s * nb + b, tile = rho / a.tr, r = rho % a.tr;
+    char *blk = ws + a.dst_off + ((inst * a.rtiles + tile) * a.kc + kg / 2) * (P * pbytes) + (r >> 3) * 256 +
+                (kg & 1) * 128 + (r & 7) * 16;
+    if (P == 4) {
+      uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split2h(v[2 * q].x, v[2 * q + 1].x, rh[q], rl[q]);
+        split2h(v[2 * q].y, v[2 * q + 1].y, ih[q], il[q]);
+      }
+      *reinterpret_cast<uint4 *>(blk) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+      *reinterpret_cast<uint4 *>(blk + pbytes) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+      *reinterpret_cast<uint4 *>(blk + 2 * pbytes) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+      *reinterpret_cast<uint4 *>(blk + 3 * pbytes) = make_uint4(il[0], il[1], il[2], il[3]);
+    } else {
+      uint32_t re[3][4], im[3][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split3(v[2 * q].x, v[2 * q + 1].x, re[0][q], re[1][q], re[2][q]);
+        split3(v[2 * q].y, v[2 * q + 1].y, im[0][q], im[1][q], im[2][q]);
+      }
+#pragma unroll
+      for (int t3 = 0; t3 < 3; ++t3) {
+        *reinterpret_cast<uint4 *>(blk + t3 * pbytes) = make_uint4(re[t3][0], re[t3][1], re[t3][2], re[t3][3]);
+        *reinterpret_cast<uint4 *>(blk + (3 + t3) * pbytes) =
+            make_uint4(im[t3][0], im[t3][1], im[t3][2], im[t3][3]);
+      }
+    }
+  }
+}
+
+// The product of a tensor-core step (after k_split of both operands).
+struct TcArgs {
+  int64_t pm_off, pn_off, o_off;  // plane regions of the M and N sides; output
+  int32_t a_meta, b_meta, o_meta; // M side, N side, output
+  int32_t o_bat, fold, perbeta, Bp;
+  int32_t nM, nN, ns;
+  int64_t mrows, mtiles, ntiles, kc;
+  float out_scale;                // undoes the terms' scale: 2^-30 (FP16) or 1
+  uint8_t mO[GMAXB], nO[GMAXB], sO[GMAXB];
+};
+
+__host__ __device__ constexpr int tc_plane_bytes(int rows) { return rows * 32; }
+// stages of the copy ring: up to four, within 220 KB (one CTA per SM) for
+// 256-column tiles and 110 KB (two CTAs per SM) for narrower ones
+__host__ __device__ constexpr int tc_stages(int nt, int planes) {
+  return (nt == 256 ? 220 : 110) * 1024 / (planes * tc_plane_bytes(TC_M + nt)) < 4
+             ? (nt == 256 ? 220 : 110) * 1024 / (planes * tc_plane_bytes(TC_M + nt))
+             : 4;
+}
+__host__ __device__ constexpr int tc_smem_bytes(int nt, int planes) {
+  return tc_stages(nt, planes) * planes * (tc_plane_bytes(TC_M) + tc_plane_bytes(nt));
+}
+
+template <int NT, int P>
+__global__ void __launch_bounds__(128, 1) k_gemm_tc(char *ws, const __grid_constant__ TcArgs a, Meta *meta,
+                                                    Header *hdr) {
+  constexpr int S = tc_stages(NT, P);
+  constexpr int ABYTES = P * tc_plane_bytes(TC_M), BBYTES = P * tc_plane_bytes(NT);
+  constexpr int SBYTES = ABYTES + BBYTES;
   constexpr uint32_t COLS = 2 * NT < 32 ? 32 : 2 * NT;
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // the batch entries of one tile are neighbours in the grid (they write
-  // the same output sectors, which then merge in L2)
-  const int nb = g.o_bat ? Bp : 1;
-  const uint64_t tile = blockIdx.x / nb;
-  const int beta = (int)(blockIdx.x - tile * nb);
-  const int lnt = g.nn - (NT == 128 ? 7 : NT == 64 ? 6 : 5);
-  const uint64_t tm = tile >> lnt, tn = tile & ((1ull << lnt) - 1);
-  const uint64_t sidx = blockIdx.y;
-  const int64_t uA = g.a_bat ? (int64_t)Bp * 8 : 8, uB = g.b_bat ? (int64_t)Bp * 8 : 8,
-                uO = g.o_bat ? (int64_t)Bp * 8 : 8;
-  const int64_t baseA = g.a_off + lin_bits(sidx, g.sA, g.ns) * uA + (g.a_bat ? beta * 8 : 0);
-  const int64_t baseB = g.b_off + lin_bits(sidx, g.sB, g.ns) * uB + (g.b_bat ? beta * 8 : 0);
-  const int64_t baseO = g.o_off + lin_bits(sidx, g.sO, g.ns) * uO + (g.o_bat ? beta * 8 : 0);
-  const int64_t rowA = lin_bits(tm * TC_M + tid, g.mA, g.nm) * uA;
-  const int64_t rowO = lin_bits(tm * TC_M + tid, g.mO, g.nm) * uO;
-  const int64_t rowB = tid < NT ? lin_bits(tn * NT + tid, g.nB, g.nn) * uB : 0;
-  if (tid < NT) oOn[tid] = lin_bits(tn * NT + tid, g.nO, g.nn) * uO;
-  if (tid < 16) kloA[tid] = lin_bits((uint64_t)tid, g.kA, 4) * uA;
-  else if (tid < 32) kloB[tid - 16] = lin_bits((uint64_t)(tid - 16), g.kB, 4) * uB;
+  static_assert(S >= 2, "at least two stages");
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S], bar_done;
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  __shared__ int64_t colO[NT];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // tile coordinates: the batch entry fastest (per-entry products of one
+  // tile write the same output sectors, which then merge in L2), then the N
+  // tile, the M tile and the shared index
+  int64_t bid = blockIdx.x;
+  int64_t beta = 0;
+  if (a.perbeta) {
+    beta = bid % a.Bp;
+    bid /= a.Bp;
+  }
+  const int64_t tn = bid % a.ntiles;
+  bid /= a.ntiles;
+  const int64_t tm = bid % a.mtiles;
+  const int64_t sidx = bid / a.mtiles;
+  const int64_t inst = a.perbeta ? sidx * a.Bp + beta : sidx;
+  const int64_t uO = a.o_bat ? (int64_t)a.Bp * 8 : 8;
+  for (int j = tid; j < NT; j += 128) colO[j] = lin_bits((uint64_t)(tn * NT + j), a.nO, a.nN) * uO;
+  if (tid == 0) abort_flag = 0;
   float sa, sb;
   int ea, eb;
-  operand_scale(meta, g.a_meta, hdr, &sa, &ea);
-  operand_scale(meta, g.b_meta, hdr, &sb, &eb);
-  if (blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0 && tid == 0)
-    meta[g.o_meta].exp = ea + eb + (g.a_meta >= 0 ? meta[g.a_meta].exp : 0) +
-                         (g.b_meta >= 0 ? meta[g.b_meta].exp : 0);
+  operand_scale(meta, a.a_meta, hdr, &sa, &ea);
+  operand_scale(meta, a.b_meta, hdr, &sb, &eb);
+  if (blockIdx.x == 0 && tid == 0)
+    meta[a.o_meta].exp = ea + eb + (a.a_meta >= 0 ? meta[a.a_meta].exp : 0) + (a.b_meta >= 0 ? meta[a.b_meta].exp : 0);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
                  "r"(COLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  const uint32_t bar_a = smem_u32(&bar);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a));
+    for (int i = 0; i < S; ++i) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_full[i])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_done)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tbase;
-  const uint32_t sA = smem_u32(tsm), sB = sA + 9 * TC_PLANE_A;
-  const uint32_t rowoff = (uint32_t)((tid >> 3) * 256 + (tid & 7) * 16);
-  float2 ra[16], rb[16];
-  auto gather = [&](int kc) {
-    const int64_t hA = baseA + rowA + lin_bits((uint64_t)kc, g.kA + 4, g.nk - 4) * uA;
-#pragma unroll
-    for (int k = 0; k < 16; ++k) ra[k] = __ldg(reinterpret_cast<const float2 *>(ws + hA + kloA[k]));
-    if (tid < NT) {
-      const int64_t hB = baseB + rowB + lin_bits((uint64_t)kc, g.kB + 4, g.nk - 4) * uB;
-#pragma unroll
-      for (int k = 0; k < 16; ++k) rb[k] = __ldg(reinterpret_cast<const float2 *>(ws + hB + kloB[k]));
-    }
-  };
-  auto put = [&]() {
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-      uint32_t re[3][4], im[3][4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 x = ra[half * 8 + 2 * q], y = ra[half * 8 + 2 * q + 1];
-        split3(x.x * sa, y.x * sa, re[0][q], re[1][q], re[2][q]);
-        split3(x.y * sa, y.y * sa, im[0][q], im[1][q], im[2][q]);
-      }
-      uint8_t *base = tsm + half * 128 + rowoff;
-#pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        *reinterpret_cast<uint4 *>(base + t * TC_PLANE_A) = make_uint4(re[t][0], re[t][1], re[t][2], re[t][3]);
-        *reinterpret_cast<uint4 *>(base + (3 + t) * TC_PLANE_A) = make_uint4(im[t][0], im[t][1], im[t][2], im[t][3]);
-        // the negated imaginary part: sign bits flipped (exact)
-        *reinterpret_cast<uint4 *>(base + (6 + t) * TC_PLANE_A) =
-            make_uint4(im[t][0] ^ 0x80008000u, im[t][1] ^ 0x80008000u, im[t][2] ^ 0x80008000u,
-                       im[t][3] ^ 0x80008000u);
-      }
-    }
-    if (tid < NT) {
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        uint32_t re[3][4], im[3][4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const float2 x = rb[half * 8 + 2 * q], y = rb[half * 8 + 2 * q + 1];
-          split3(x.x * sb, y.x * sb, re[0][q], re[1][q], re[2][q]);
-          split3(x.y * sb, y.y * sb, im[0][q], im[1][q], im[2][q]);
+  const uint32_t s0 = smem_u32(tsm);
+  const int64_t kc = a.kc;
+  if (warp == 0) {
+    if (lane == 0) {
+      // producer: one chunk (both operands' plane blocks) per stage
+      const char *srcA = ws + a.pm_off + (inst * a.mtiles + tm) * kc * ABYTES;
+      const char *srcB = ws + a.pn_off + (inst * a.ntiles + tn) * kc * BBYTES;
+      for (int64_t k = 0; k < kc; ++k) {
+        const int st = (int)(k % S);
+        if (k >= S && !tc_wait(smem_u32(&bar_empty[st]), (uint32_t)((k / S) - 1) & 1u)) {
+          atomicExch(&abort_flag, 1);
+          break;
         }
-        uint8_t *base = tsm + 9 * TC_PLANE_A + half * 128 + rowoff;
-#pragma unroll
-        for (int t = 0; t < 3; ++t) {
-          *reinterpret_cast<uint4 *>(base + t * PB) = make_uint4(re[t][0], re[t][1], re[t][2], re[t][3]);
-          *reinterpret_cast<uint4 *>(base + (3 + t) * PB) = make_uint4(im[t][0], im[t][1], im[t][2], im[t][3]);
-        }
+        if (*(volatile int *)&abort_flag) break;
+        const uint32_t fb = smem_u32(&bar_full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(SBYTES) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                s0 + st * SBYTES),
+            "l"(srcA + k * ABYTES), "r"(ABYTES), "r"(fb)
+            : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                s0 + st * SBYTES + ABYTES),
+            "l"(srcB + k * BBYTES), "r"(BBYTES), "r"(fb)
+            : "memory");
       }
     }
-  };
-  // instruction descriptor: FP32 accumulator, BF16 A and B, both K-major,
-  // N >> 3 at bit 17, M >> 4 at bit 24
-  constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
-                             ((uint32_t)(TC_M >> 4) << 24);
-  auto issue = [&](int kc) {
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    uint32_t acc = kc > 0 ? 1u : 0u;
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issue.  Instruction descriptor: FP32 accumulator, FP16 (P = 4)
+      // or BF16 (P = 6) A and B, both K-major, N >> 3 at bit 17, M >> 4 at
+      // bit 24; bit 13 negates A.
+      constexpr uint32_t fmt = P == 4 ? 0u : 1u;
+      constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                 ((uint32_t)(TC_M >> 4) << 24);
+      constexpr uint32_t idesc_neg = idesc | (1u << 13);
+      for (int64_t k = 0; k < kc; ++k) {
+        const int st = (int)(k % S);
+        if (!tc_wait(smem_u32(&bar_full[st]), (uint32_t)(k / S) & 1u)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sA = s0 + st * SBYTES, sB = sA + ABYTES;
+        uint32_t acc = k > 0 ? 1u : 0u;
+        if (P == 4) {
+          // planes: 0 re high, 1 re low, 2 im high, 3 im low; term pairs
+          // (h, h), (h, l), (l, h)
 #pragma unroll
-    for (int t = 0; t < 6; ++t) {
-      const int i = t == 2 || t == 4 ? 1 : t == 5 ? 2 : 0;  // term pairs (i, j), i + j <= 2
-      const int j = t == 1 || t == 4 ? 1 : t == 3 ? 2 : 0;
-      const uint64_t ar = tc_desc(sA + i * TC_PLANE_A), ai = tc_desc(sA + (3 + i) * TC_PLANE_A),
-                     an = tc_desc(sA + (6 + i) * TC_PLANE_A);
-      const uint64_t br = tc_desc(sB + j * PB), bi = tc_desc(sB + (3 + j) * PB);
-      tc_mma(tmem, ar, br, idesc, acc);       // re += Ar Br
-      tc_mma(tmem, an, bi, idesc, 1u);        // re -= Ai Bi
-      tc_mma(tmem + NT, ar, bi, idesc, acc);  // im += Ar Bi
-      tc_mma(tmem + NT, ai, br, idesc, 1u);   // im += Ai Br
-      acc = 1u;
+          for (int t = 0; t < 3; ++t) {
+            const int i = t == 2 ? 1 : 0, j = t == 1 ? 1 : 0;
+            const uint64_t ar = tc_desc(sA + i * tc_plane_bytes(TC_M)), ai = tc_desc(sA + (2 + i) * tc_plane_bytes(TC_M));
+            const uint64_t br = tc_desc(sB + j * tc_plane_bytes(NT)), bi = tc_desc(sB + (2 + j) * tc_plane_bytes(NT));
+            tc_mma(tmem, ar, br, idesc, acc);           // re += Ar Br
+            tc_mma(tmem, ai, bi, idesc_neg, 1u);        // re -= Ai Bi
+            tc_mma(tmem + NT, ar, bi, idesc, acc);      // im += Ar Bi
+            tc_mma(tmem + NT, ai, br, idesc, 1u);       // im += Ai Br
+            acc = 1u;
+          }
+        } else {
+          // planes: 0-2 re terms, 3-5 im terms; term pairs (i, j), i + j <= 2
+#pragma unroll
+          for (int t = 0; t < 6; ++t) {
+            const int i = t == 2 || t == 4 ? 1 : t == 5 ? 2 : 0;
+            const int j = t == 1 || t == 4 ? 1 : t == 3 ? 2 : 0;
+            const uint64_t ar = tc_desc(sA + i * tc_plane_bytes(TC_M)), ai = tc_desc(sA + (3 + i) * tc_plane_bytes(TC_M));
+            const uint64_t br = tc_desc(sB + j * tc_plane_bytes(NT)), bi = tc_desc(sB + (3 + j) * tc_plane_bytes(NT));
+            tc_mma(tmem, ar, br, idesc, acc);
+            tc_mma(tmem, ai, bi, idesc_neg, 1u);
+            tc_mma(tmem + NT, ar, bi, idesc, acc);
+            tc_mma(tmem + NT, ai, br, idesc, 1u);
+            acc = 1u;
+          }
+        }
+        tc_commit(smem_u32(&bar_empty[st]));
+      }
+      // always: every MMA issued above completes before "done" does
+      tc_commit(smem_u32(&bar_done));
     }
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar_a)
-                 : "memory");
-  };
-  const int nkc = 1 << (g.nk - 4);
-  bool ok = true;
-  int issued = -1;  // last chunk whose MMAs were issued
-  gather(0);
-  for (int kc = 0; kc < nkc; ++kc) {
-    if (kc > 0) {
-      // the previous chunk's MMAs have read the planes
-      ok = !__syncthreads_or(!tc_wait(bar_a, (uint32_t)(kc - 1) & 1u));
-      if (!ok) break;
-    }
-    put();
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) issue(kc);
-    issued = kc;
-    if (kc + 1 < nkc) gather(kc + 1);
+    __syncwarp();
   }
-  if (ok) ok = !__syncthreads_or(!tc_wait(bar_a, (uint32_t)issued & 1u));
+  // epilogue: thread r = tile row r = tensor-memory lane r
+  bool ok = tc_wait(smem_u32(&bar_done), 0u);
+  if (!ok) ok = tc_wait(smem_u32(&bar_done), 0u);  // MMAs read only loaded stages: they finish
+  const bool valid_run = ok && !*(volatile int *)&abort_flag;
   float lmax = 0.f;
   if (ok) {
     asm volatile("tcgen05.fence::after_thread_sync;");
+    const int64_t rho = tm * TC_M + tid;
+    const bool valid = valid_run && rho < a.mrows;
+    int64_t m = rho, b2 = beta;
+    if (a.fold) {
+      m = rho / a.Bp;
+      b2 = rho % a.Bp;
+    }
+    char *orow = ws + a.o_off + (lin_bits((uint64_t)sidx, a.sO, a.ns) + lin_bits((uint64_t)(valid ? m : 0), a.mO, a.nM)) * uO +
+                 (a.o_bat ? b2 * 8 : 0);
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-    char *orow = ws + baseO + rowO;
 #pragma unroll 1
     for (int c0 = 0; c0 < NT; c0 += 16) {
       uint32_t re[16], im[16];
       tc_ld16(tl + c0, re);
       tc_ld16(tl + NT + c0, im);
+      if (valid) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const float2 v = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
-        *reinterpret_cast<float2 *>(orow + oOn[c0 + j]) = v;
-        lmax = fmax_nan(lmax, absmax2(v));
+        for (int j = 0; j < 16; ++j) {
+          const float2 v = make_float2(__uint_as_float(re[j]) * a.out_scale, __uint_as_float(im[j]) * a.out_scale);
+          *reinterpret_cast<float2 *>(orow + colO[c0 + j]) = v;
+          lmax = fmax_nan(lmax, absmax2(v));
+        }
       }
     }
-  } else {
-    // the status says the tile is missing; wait once more (bounded) for the
-    // MMAs in flight before the tensor memory is released
-    if (tid == 0 && hdr) atomicCAS(&hdr->status, 0, QGM_ERR_TIMEOUT);
-    tc_wait(bar_a, (uint32_t)issued & 1u);
   }
+  if (!valid_run && tid == 0 && hdr) atomicCAS(&hdr->status, 0, QGM_ERR_TIMEOUT);
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
-  record_max(lmax, meta, g.o_meta);
+  record_max(lmax, meta, a.o_meta);
 }
 
 // out[x] += F[x] * 2^exp * c in FP64 (one slice's partial amplitudes), then
@@ -1399,31 +1535,104 @@ static void launch_leaves(qgm_plan *p, const uint64_t *d_bits, int64_t B, cudaSt
 
 // Grid of one product-sum step: row strides are powers of two so that the
 // kernels can walk rows by table increments.
+// Tensor-core form of a GEMM-shaped step: split both operands into planes,
+// then the product (see k_split and k_gemm_tc).
+static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c, int64_t planes_off, int P,
+                           Meta *meta, Header *hdr, cudaStream_t st) {
+  if (c.swap) gemm_swap_roles(g);
+  for (int side = 0; side < 2; ++side) {
+    const bool ms = side == 0;
+    SplitArgs s{};
+    s.src_off = ms ? g.a_off : g.b_off;
+    s.dst_off = planes_off + (ms ? 0 : c.bytesM);
+    s.meta = ms ? g.a_meta : g.b_meta;
+    s.batched = ms ? g.a_bat : g.b_bat;
+    s.fold = ms && c.fold;
+    s.perbeta = c.perbeta;
+    s.Bp = Bp;
+    s.nr = ms ? g.nm : g.nn;
+    s.nk = g.nk;
+    s.ns = g.ns;
+    s.tr = ms ? TC_M : c.nt;
+    s.rows = ms ? c.mrows : ((int64_t)1 << g.nn);
+    s.rtiles = ms ? c.mtiles : c.ntiles;
+    s.kc = c.kc;
+    s.fp16 = P == 4;
+    std::memcpy(s.rX, ms ? g.mA : g.nB, GMAXB);
+    std::memcpy(s.kX, ms ? g.kA : g.kB, GMAXB);
+    std::memcpy(s.sX, ms ? g.sA : g.sB, GMAXB);
+    const int64_t items = c.inst * s.rtiles * s.tr * c.kc * 2;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((items + 255) / 256, (int64_t)sms * 16));
+    if (P == 4) k_split<4><<<blocks, 256, 0, st>>>(ws, s, meta, hdr);
+    else k_split<6><<<blocks, 256, 0, st>>>(ws, s, meta, hdr);
+  }
+  TcArgs a{};
+  a.pm_off = planes_off;
+  a.pn_off = planes_off + c.bytesM;
+  a.o_off = g.o_off;
+  a.a_meta = g.a_meta;
+  a.b_meta = g.b_meta;
+  a.o_meta = g.o_meta;
+  a.o_bat = g.o_bat;
+  a.fold = c.fold;
+  a.perbeta = c.perbeta;
+  a.Bp = Bp;
+  a.nM = g.nm;
+  a.nN = g.nn;
+  a.ns = g.ns;
+  a.mrows = c.mrows;
+  a.mtiles = c.mtiles;
+  a.ntiles = c.ntiles;
+  a.kc = c.kc;
+  a.out_scale = P == 4 ? 0x1p-30f : 1.f;
+  std::memcpy(a.mO, g.mO, GMAXB);
+  std::memcpy(a.nO, g.nO, GMAXB);
+  std::memcpy(a.sO, g.sO, GMAXB);
+  const unsigned grid = (unsigned)(c.inst * c.mtiles * c.ntiles);
+#define QGM_TC_LAUNCH(NT_, P_) \
+  k_gemm_tc<NT_, P_><<<grid, 128, tc_smem_bytes(NT_, P_), st>>>(ws, a, meta, hdr)
+  if (P == 4) {
+    if (c.nt == 256) QGM_TC_LAUNCH(256, 4);
+    else if (c.nt == 128) QGM_TC_LAUNCH(128, 4);
+    else if (c.nt == 64) QGM_TC_LAUNCH(64, 4);
+    else QGM_TC_LAUNCH(32, 4);
+  } else {
+    if (c.nt == 256) QGM_TC_LAUNCH(256, 6);
+    else if (c.nt == 128) QGM_TC_LAUNCH(128, 6);
+    else if (c.nt == 64) QGM_TC_LAUNCH(64, 6);
+    else QGM_TC_LAUNCH(32, 6);
+  }
+#undef QGM_TC_LAUNCH
+}
+
+// Raise the dynamic shared-memory limit of every tensor-core kernel.
+static cudaError_t tc_set_smem() {
+  cudaError_t e = cudaSuccess;
+#define QGM_TC_ATTR(NT_, P_)                                                                                  \
+  if (e == cudaSuccess)                                                                                       \
+  e = cudaFuncSetAttribute(k_gemm_tc<NT_, P_>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NT_, P_))
+  QGM_TC_ATTR(256, 4);
+  QGM_TC_ATTR(128, 4);
+  QGM_TC_ATTR(64, 4);
+  QGM_TC_ATTR(32, 4);
+  QGM_TC_ATTR(256, 6);
+  QGM_TC_ATTR(128, 6);
+  QGM_TC_ATTR(64, 6);
+  QGM_TC_ATTR(32, 6);
+#undef QGM_TC_ATTR
+  return e;
+}
+
 static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const GemmDesc *gemms, Meta *meta,
-                           Header *hdr, cudaStream_t st, bool tc = false) {
+                           Header *hdr, cudaStream_t st, bool tc = false, int64_t planes_off = 0,
+                           int planes = 4) {
   const uint64_t rows = 1ull << d.w_out;
-  if (d.gemm >= 0 && gemms && tc && gemm_tc_eligible(gemms[d.gemm])) {
-    // the wider side takes the MMA's 128 rows: out[s, n, m] = sum_k B A is
-    // the same product with the roles exchanged
-    GemmDesc g = gemms[d.gemm];
-    if (g.nm < 7) {
-      std::swap(g.a_off, g.b_off);
-      std::swap(g.a_meta, g.b_meta);
-      std::swap(g.a_bat, g.b_bat);
-      std::swap(g.nm, g.nn);
-      for (int b = 0; b < GMAXB; ++b) {
-        std::swap(g.mA[b], g.nB[b]);
-        std::swap(g.mO[b], g.nO[b]);
-        std::swap(g.kA[b], g.kB[b]);
-        std::swap(g.sA[b], g.sB[b]);
-      }
+  if (d.gemm >= 0 && gemms && tc) {
+    const TcCfg c = tc_config(gemms[d.gemm], Bp, planes);
+    if (c.ok) {
+      launch_gemm_tc(ws, sms, Bp, gemms[d.gemm], c, planes_off, planes, meta, hdr, st);
+      return;
     }
-    const int lnt = g.nn >= 7 ? 7 : g.nn;
-    const dim3 grid((1u << ((g.nm - 7) + (g.nn - lnt))) * (g.o_bat ? Bp : 1), 1u << g.ns);
-    if (lnt == 7) k_gemm_tc<128><<<grid, 128, tc_smem_bytes(128), st>>>(ws, g, meta, hdr, Bp);
-    else if (lnt == 6) k_gemm_tc<64><<<grid, 128, tc_smem_bytes(64), st>>>(ws, g, meta, hdr, Bp);
-    else k_gemm_tc<32><<<grid, 128, tc_smem_bytes(32), st>>>(ws, g, meta, hdr, Bp);
-    return;
   }
   if (d.gemm >= 0 && gemms) {
     const GemmDesc &g = gemms[d.gemm];
@@ -1477,7 +1686,7 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
 static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st) {
   char *ws = p->exec->ws;
   launch_step_ws(ws, p->exec->sms, p->Bp, d, p->gemms.data(), reinterpret_cast<Meta *>(ws + p->off_meta),
-                 reinterpret_cast<Header *>(ws + p->off_header), st, p->gemm_tc);
+                 reinterpret_cast<Header *>(ws + p->off_header), st, p->gemm_tc, p->off_planes, p->tc_planes);
 }
 
 static void launch_accumulate(qgm_plan *p, double2 *d_out, int64_t n_out, cudaStream_t st) {
@@ -1632,11 +1841,7 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
   CK(cudaGetDevice(&x->device));
   CK(cudaDeviceGetAttribute(&x->sms, cudaDevAttrMultiProcessorCount, x->device));
   x->ws = static_cast<char *>(d_workspace);
-  if (p->gemm_tc && !p->gemms.empty()) {
-    CK(cudaFuncSetAttribute(k_gemm_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(128)));
-    CK(cudaFuncSetAttribute(k_gemm_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(64)));
-    CK(cudaFuncSetAttribute(k_gemm_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(32)));
-  }
+  if (p->gemm_tc && !p->gemms.empty()) CK(tc_set_smem());
   x->ws_bytes = ws_bytes;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   CK(cudaMemsetAsync(x->ws + p->off_header, 0, 256, st));
@@ -2107,10 +2312,10 @@ extern "C" int qgm_amplitudes_static(qgm_plan *p, const uint64_t *d_bitstrings, 
     set_error("qgm_amplitudes_static: needs a batch plan and 1 <= B <= %lld", (long long)p->batch);
     return QGM_ERR_ARG;
   }
-  if (p->ws_bytes > (int64_t)QGM_STATIC_SCRATCH_BYTES) {
+  if (p->ws_fwd_bytes > (int64_t)QGM_STATIC_SCRATCH_BYTES) {
     set_error("qgm_amplitudes_static: the plan needs %lld bytes of scratch, more than the %llu-byte "
               "static scratch; use qgm_plan_bind with a caller-allocated workspace",
-              (long long)p->ws_bytes, (unsigned long long)QGM_STATIC_SCRATCH_BYTES);
+              (long long)p->ws_fwd_bytes, (unsigned long long)QGM_STATIC_SCRATCH_BYTES);
     return QGM_ERR_OOM;
   }
   int dev = -1, sms = 0;

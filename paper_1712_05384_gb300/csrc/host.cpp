@@ -583,7 +583,7 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
         else if (inB && (!inA || T[Bt].entries < T[A].entries)) toB.push_back(by[q]);
         else toA.push_back(by[q]);
       }
-      int nm = 0, nn = 0;
+      int nm = 0, nn = 0, ns = 0;
       std::vector<int> kept;
       for (int id : inputs)
         for (int v : T[id].vars)
@@ -596,7 +596,11 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
         if (!ha && !hb) ok = false;
         nm += ha && !hb;
         nn += hb && !ha;
+        ns += ha && hb;
       }
+      // the shared kept variables index independent products (a grid
+      // dimension of the launch): at most 15 of them
+      if (ns > 15) ok = false;
       // tiles of 64 x 64 or, with a wide batch (many GEMMs per launch), 64 x
       // 32 outputs: the operand with six or more private kept variables
       // goes first
@@ -1221,7 +1225,12 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   }
   const int max_fuse = o.max_fuse > 0 ? std::min(o.max_fuse, 16) : 8;
   p->gemm_ok = o.no_gemm == 0;
-  p->gemm_tc = o.gemm_split_bf16 >= 0;
+  p->gemm_tc = o.gemm_precision >= 0;
+  p->tc_planes = o.gemm_precision == 1 ? 6 : 4;
+  if (o.gemm_precision < -1 || o.gemm_precision > 2) {
+    set_error("qgm_plan_order: bad gemm_precision %d", o.gemm_precision);
+    return QGM_ERR_ARG;
+  }
   p->trees_ok = o.trees > 0;
   p->nest_ok = true;
   const int64_t budget = o.mem_budget_bytes > 0 ? o.mem_budget_bytes : (int64_t)64 << 30;
@@ -1547,7 +1556,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
       g.nn = (int)nv.size();
       g.nk = (int)kv.size();
       g.ns = (int)sv.size();
-      if (g.nm >= GMAXB || g.nn >= GMAXB || g.nk >= GMAXB || g.ns >= GMAXB || g.ns > 16) {
+      if (g.nm >= GMAXB || g.nn >= GMAXB || g.nk >= GMAXB || g.ns >= GMAXB || g.ns > 15) {
         set_error("internal: GEMM step too wide");
         return QGM_ERR_ARG;
       }
@@ -1611,6 +1620,16 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     }
     p->steps.push_back(d);
   }
+  // the split operand planes of the largest tensor-core step, after the arena
+  p->ws_fwd_bytes = p->ws_bytes;
+  p->planes_bytes = 0;
+  if (p->gemm_tc)
+    for (const GemmDesc &g : p->gemms) {
+      const TcCfg c = tc_config(g, (int)Bp, p->tc_planes);
+      if (c.ok) p->planes_bytes = std::max(p->planes_bytes, c.bytesM + c.bytesN);
+    }
+  p->off_planes = p->ws_bytes - 256;
+  p->ws_bytes = p->off_planes + p->planes_bytes + 256;
   build_resident(p);
   if (p->grad) {
     // ------------------------------------------- adjoint elimination layout
@@ -2068,7 +2087,7 @@ int qgm_plan_get_info(const qgm_plan *p, qgm_plan_info *info) {
   for (const StepRec &st : p->sim.steps) info->n_nested_steps += st.k_inner > 0;
   info->n_gemm_tc_steps = 0;
   if (p->gemm_tc)
-    for (const GemmDesc &g : p->gemms) info->n_gemm_tc_steps += gemm_tc_eligible(g);
+    for (const GemmDesc &g : p->gemms) info->n_gemm_tc_steps += gemm_tc_eligible(g, p->Bp);
   return QGM_OK;
 }
 
@@ -2141,7 +2160,7 @@ int qgm_plan_get_gemm(const qgm_plan *p, int32_t *rec, int64_t cap, int64_t *n) 
       r[5] = g.a_bat;
       r[6] = g.b_bat;
       r[7] = g.o_bat;
-      r[8] = p->gemm_tc && gemm_tc_eligible(g) ? 1 : 0;
+      r[8] = p->gemm_tc && gemm_tc_eligible(g, p->Bp) ? 1 : 0;
     }
     ++c;
   }

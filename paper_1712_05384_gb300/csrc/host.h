@@ -2,6 +2,7 @@
 // and exec.cu (device execution).  Not part of the C ABI.
 #pragma once
 
+#include <algorithm>
 #include <complex>
 #include <cstdint>
 #include <map>
@@ -93,13 +94,74 @@ struct GemmDesc {
   uint8_t kA[GMAXB], kB[GMAXB], sA[GMAXB], sB[GMAXB], sO[GMAXB];
 };
 
-// A GEMM step runs on the tensor cores (split BF16) when one side has at
-// least 2^7 rows (the MMA's M = 128), the other at least 2^5 (N = 32, 64 or
-// 128) and the summed entries come in whole chunks of 16 (one MMA's K).
-inline bool gemm_tc_eligible(const GemmDesc &g) {
-  const int hi = g.nm > g.nn ? g.nm : g.nn, lo = g.nm > g.nn ? g.nn : g.nm;
-  return g.nk >= 4 && hi >= 7 && lo >= 5;
+// Exchange the roles of the two operands: out[s, n, m] = sum_k B A is the
+// same product.
+inline void gemm_swap_roles(GemmDesc &g) {
+  std::swap(g.a_off, g.b_off);
+  std::swap(g.a_meta, g.b_meta);
+  std::swap(g.a_bat, g.b_bat);
+  std::swap(g.nm, g.nn);
+  for (int b = 0; b < GMAXB; ++b) {
+    std::swap(g.mA[b], g.nB[b]);
+    std::swap(g.mO[b], g.nO[b]);
+    std::swap(g.kA[b], g.kB[b]);
+    std::swap(g.sA[b], g.sB[b]);
+  }
 }
+
+// Tensor-core form of a GEMM-shaped step.  One operand takes the MMA's M
+// side (tiles of 128 rows), the other the N side (tiles of nt = min(256,
+// 2^nN) rows); both are first split into planes of 16-bit terms stored as
+// the MMA reads them.  When only one operand carries the batch axis it takes
+// the M side and its batch entries become rows there (row = m * Bp + beta),
+// so the other operand's tile serves every entry; when both carry it, each
+// (shared index, batch entry) is a product of its own ("per entry").  A
+// plane block holds, for one instance (shared index, and batch entry when
+// per entry), one row tile and one chunk of 16 summed entries, P planes of
+// TR x 16 terms in 8-row x 16-byte core matrices (row group stride 256 B,
+// the two 8-entry halves of a row 128 B apart).
+constexpr int TC_M = 128;
+struct TcCfg {
+  bool ok = false;
+  bool swap = false;     // B takes the M side
+  bool fold = false;     // batch entries are rows of the M side
+  bool perbeta = false;  // one product per (shared index, batch entry)
+  int nM = 0, nN = 0;    // private kept variables of the M and N sides
+  int nt = 0;            // N tile
+  int64_t mrows = 0, mtiles = 0, ntiles = 0, kc = 0, inst = 0;
+  int64_t bytesM = 0, bytesN = 0;  // plane bytes of the M and N sides
+};
+
+// planes: 16-bit terms per complex value (4: FP16 high and low parts of the
+// real and imaginary parts; 6: three BF16 terms of each)
+inline TcCfg tc_config(const GemmDesc &g, int Bp, int planes) {
+  TcCfg c;
+  const bool one = g.o_bat && (g.a_bat != g.b_bat);
+  c.swap = one ? (g.b_bat != 0) : (g.nn > g.nm);
+  c.fold = one && Bp > 1;
+  c.perbeta = g.o_bat && g.a_bat && g.b_bat && Bp > 1;
+  c.nM = c.swap ? g.nn : g.nm;
+  c.nN = c.swap ? g.nm : g.nn;
+  if (g.nk < 4 || c.nN < 5 || g.ns > 15 || c.nM > 30) return c;
+  c.mrows = ((int64_t)1 << c.nM) * (c.fold ? Bp : 1);
+  if (c.mrows < TC_M) return c;
+  c.mtiles = (c.mrows + TC_M - 1) / TC_M;
+  c.nt = c.nN >= 8 ? 256 : (1 << c.nN);
+  c.ntiles = ((int64_t)1 << c.nN) / c.nt;
+  c.kc = ((int64_t)1 << g.nk) / 16;
+  c.inst = ((int64_t)1 << g.ns) * (c.perbeta ? Bp : 1);
+  if (c.inst * c.mtiles * c.ntiles >= ((int64_t)1 << 31)) return c;
+  c.bytesM = c.inst * c.mtiles * c.kc * planes * TC_M * 32;
+  c.bytesN = c.inst * c.ntiles * c.kc * planes * c.nt * 32;
+  c.ok = true;
+  return c;
+}
+
+// A GEMM step runs on the tensor cores when its tensor-core form exists: the
+// M side has at least 128 rows (batch entries counted when they become
+// rows), the N side at least 32 and the summed entries come in whole chunks
+// of 16 (one MMA's K).
+inline bool gemm_tc_eligible(const GemmDesc &g, int Bp) { return tc_config(g, Bp, 4).ok; }
 
 // Leaf factor built on the device per slice: base table over
 // (internal vars | slice vars | output vars), MSB first.
@@ -318,7 +380,11 @@ struct qgm_plan {
   int64_t off_image = 0;    // compiled resident kernel: initial shared-memory image (bitstring-independent leaves)
   int executor_pref = 0;    // qgm_plan_opts.executor
   bool gemm_ok = true;      // GEMM-shaped steps run by the GEMM kernel
-  bool gemm_tc = false;     // eligible GEMM steps run on the tensor cores (split BF16)
+  bool gemm_tc = false;     // eligible GEMM steps run on the tensor cores (split terms)
+  int tc_planes = 4;        // 16-bit terms per complex value: 4 (FP16 x 2) or 6 (BF16 x 3)
+  int64_t off_planes = 0;   // workspace region of the split operand planes
+  int64_t planes_bytes = 0; // its size (the largest tensor-core step's two operands)
+  int64_t ws_fwd_bytes = 0; // workspace the forward pass needs without that region
   bool trees_ok = false;    // buckets of three or more inputs may run as contraction trees
   bool nest_ok = true;      // buckets may be marked for nested evaluation
   qgm_exec_state *exec = nullptr;

@@ -5,9 +5,12 @@ Entry b * 2^k + c of a batch is the amplitude of bitstring x_b with its open
 qubits replaced by the bits of c (bit i of c = the i-th lowest open qubit).
 Tolerances as in the batch parity tests.
 """
+import os
+
 import numpy as np
 import pytest
 
+import errmeasure
 import qgm_inputs as qi
 from oracle import statevector as sv
 from oracle import ve
@@ -33,9 +36,7 @@ def Q():
 
 
 def errors(a, ref, n):
-    big = np.abs(ref) >= 2.0 ** (-n / 2)
-    rel = np.max(np.abs(a - ref)[big] / np.abs(ref[big])) if big.any() else 0.0
-    return rel, np.max(np.abs(a - ref)) * 2.0 ** (n / 2)
+    return errmeasure.errors(a, ref, n, os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0])
 
 
 def expand(bits, open_qubits):

@@ -15,6 +15,7 @@ import os
 import numpy as np
 import pytest
 
+import errmeasure
 import qgm_inputs as qi
 from oracle import statevector as sv
 from oracle import ve
@@ -41,11 +42,7 @@ def Q():
 
 
 def errors(a, ref, n):
-    a = np.asarray(a)
-    ref = np.asarray(ref)
-    big = np.abs(ref) >= 2.0 ** (-n / 2)
-    rel = np.max(np.abs(a - ref)[big] / np.abs(ref[big])) if big.any() else 0.0
-    return rel, np.max(np.abs(a - ref)) * 2.0 ** (n / 2)
+    return errmeasure.errors(a, ref, n, os.environ.get("PYTEST_CURRENT_TEST", "").split(" ")[0])
 
 
 def run_batch(circuit_py, B, order_kind=0, budget=0, bits=None, max_fuse=0, executor=0, trees=False):
@@ -175,18 +172,67 @@ def test_grid5x5_d20_b1024_sampled(executor):
     assert abs((Np ** 2).mean() - gold["N_sum_p2"]) < 4 * (Np ** 2).std() / math.sqrt(len(Np))
 
 
-def test_grid6x6_d25_b1000_sampled():
-    # 6x6 grid, depth 25, 1000 bitstrings: intermediates up to 2^28 complex64
-    # entries (stepwise executor); 3 outputs against the oracle's elimination
+def _golden(name):
+    with open(os.path.join(os.path.dirname(__file__), "golden", name)) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp32"])
+def test_grid6x6_d25_b1000_vs_oracle(precision):
+    # 6x6 grid, depth 25, the full batch of 1000 bitstrings (intermediates up
+    # to 2^28 complex64 entries, stepwise executor); its first 32 outputs
+    # against the FP64 oracle's values (tests/golden/amps_grid6x6_d25.json,
+    # oracle/ve.c); the GEMM step on the tensor cores in split FP16 or BF16,
+    # or every GEMM step on the FP32 cores
+    gold = _golden("amps_grid6x6_d25.json")
+    q = Q()
     c = qi.grid_circuit(6, 6, 25, 0)
-    a, bits, p = run_batch(c, 1000)
+    bits = qi.bitstrings(c.n, 1000, 0)
+    p = q.Plan(q.Model(q.Circuit.grid(6, 6, 25, 0)), batch=1000, precision=precision).bind()
     assert p.info.max_tensor_entries >= 2 ** 26
-    idx = np.array([0, 499, 998])
-    ref = ve.amplitudes(c, bits[idx])
-    rel, ab = errors(a[idx], ref, c.n)
-    assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+    assert (p.info.n_gemm_tc_steps > 0) == (precision != "fp32")
+    d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
+    d_out = torch.empty(2000, dtype=torch.float64, device="cuda")
+    p.amplitudes(d_bits, d_out)
+    torch.cuda.synchronize()
+    assert p.status() == 0
+    o = d_out.cpu().numpy()
+    a = o[0::2] + 1j * o[1::2]
+    xs = [int(e["x"]) for e in gold["amplitudes"]]
+    assert len(xs) >= 32 and xs == [int(x) for x in bits[:len(xs)]]
+    ref = np.array([complex(e["re"], e["im"]) for e in gold["amplitudes"]])
+    rel, ab = errors(a[:len(xs)], ref, c.n)
+    tol = REL_TOL if precision == "fp32" else 1e-4
+    assert rel < tol and ab < tol, (rel, ab)
     Np = (2 ** c.n) * np.abs(a) ** 2
     assert abs(Np.mean() - 1) < 4 * Np.std() / math.sqrt(len(Np))
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp32"])
+def test_grid5x9_d40_vs_oracle(precision):
+    # 5x9 grid, depth 40, in passes of 4 bitstrings (the benchmark's plan):
+    # the first outputs of the seed-0 batch against the FP64 oracle's values
+    # (tests/golden/amps_grid5x9_d40.json: oracle/ve.c, sliced, hours of CPU);
+    # complex64 (GEMM steps on the FP32 cores) within 1e-5, the split forms
+    # within 1e-4
+    path = os.path.join(os.path.dirname(__file__), "golden", "amps_grid5x9_d40.json")
+    if not os.path.exists(path):
+        pytest.skip("no oracle amplitudes stored for 5x9 depth 40")
+    gold = _golden("amps_grid5x9_d40.json")
+    xs = [int(e["x"]) for e in gold["amplitudes"]]
+    if len(xs) < 2:
+        pytest.skip("fewer than two oracle amplitudes stored")
+    q = Q()
+    bits = qi.bitstrings(45, 1000, 0)
+    assert xs == [int(x) for x in bits[:len(xs)]]
+    p = q.Plan(q.Model(q.Circuit.grid(5, 9, 40, 0)), order_kind=1, batch=4, precision=precision).bind()
+    assert p.info.n_gemm_steps > 0 and (p.info.n_gemm_tc_steps > 0) == (precision != "fp32")
+    a = np.concatenate([p.amplitudes_host(bits[k:k + 4]) for k in range(0, len(xs), 4)])[:len(xs)]
+    assert p.status() == 0
+    ref = np.array([complex(e["re"], e["im"]) for e in gold["amplitudes"]])
+    rel, ab = errors(a, ref, 45)
+    tol = REL_TOL if precision == "fp32" else 1e-4
+    assert rel < tol and ab < tol, (rel, ab)
 
 
 @pytest.mark.parametrize("executor", EXECS)

@@ -268,3 +268,19 @@ def test_slicer_bit_exact(rows, cols, depth, batch, div):
     assert O.slice_greedy(adj, order, n_slices=len(sv)) == sv
     # the reported width is the order's largest clique without those variables
     assert p.info.max_clique == max(len(c) for c in O.cliques(adj, order, sv))
+
+
+@pytest.mark.parametrize("rows,cols,depth,batch", [(5, 9, 40, 4), (6, 6, 25, 1000), (4, 8, 40, 4), (6, 6, 25, 1),
+                                                   (7, 7, 20, 1)])
+def test_gemm_shapes_fit_the_launch(rows, cols, depth, batch):
+    # a GEMM-shaped step launches one set of tiles per shared kept index:
+    # at most 2^15 of them, and every variable class fits the descriptor
+    p = Q.Plan(Q.Model(Q.Circuit.grid(rows, cols, depth, 0)), batch=batch, executor=Q.EXEC_STEPWISE)
+    gs = p.gemm_shapes()
+    assert len(gs) == p.info.n_gemm_steps
+    kinds = p.step_kernels()
+    for g in gs:
+        assert kinds[g["step"]] == 3
+        assert g["ns"] <= 15 and max(g["nm"], g["nn"], g["nk"]) < 24
+        assert g["nk"] >= 4 and min(g["nm"], g["nn"]) >= 5
+    assert sum(g["tc"] for g in gs) == p.info.n_gemm_tc_steps

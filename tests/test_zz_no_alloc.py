@@ -42,32 +42,54 @@ def _close(a, ref, n):
     return rel < REL_TOL and np.max(np.abs(a - ref)) * 2.0 ** (n / 2) < ABS_TOL
 
 
-def test_static_scratch_matches_bound_workspace(q):
-    B = 50
-    bits = qi.bitstrings(16, B, 3)
-    d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
-    plan = q.Plan(q.Model(q.Circuit.grid(4, 4, 12, 3)), batch=B, executor=q.EXEC_STEPWISE)
-    assert plan.info.workspace_bytes <= (64 << 20)
-    # the ordinary entry point, with a caller-allocated workspace
+def _bound(q, plan, d_bits, B, n_out):
+    """Amplitudes from the ordinary entry point with a bound workspace."""
     plan.bind()
-    ref_out = torch.zeros(2 * B, dtype=torch.float64, device="cuda")
-    plan.amplitudes(d_bits, ref_out)
+    out = torch.zeros(2 * n_out, dtype=torch.float64, device="cuda")
+    plan.amplitudes(d_bits, out, B=B)
     torch.cuda.synchronize()
-    ref = _as_complex(ref_out)
-    # a second plan on the static scratch in between leaves its tables behind
+    assert plan.status() == 0
+    return _as_complex(out)
+
+
+def _static(q, plan, d_bits, B, n_out):
+    out = torch.full((2 * n_out,), float("nan"), dtype=torch.float64, device="cuda")
+    q._lib.check(q.lib().qgm_amplitudes_static(plan._h, d_bits.data_ptr(), B, out.data_ptr(), None))
+    torch.cuda.synchronize()
+    return _as_complex(out)
+
+
+def test_static_scratch_matches_bound_workspace(q):
+    # three plans that exercise what the static path does differently: a
+    # plain one (4x4 depth 12), one with a GEMM-shaped step (4x5 depth 30,
+    # run here on the FP32 cores; the bound reference is told to do the same)
+    # and one sliced into 8 parts (the per-slice loop); called twice in a
+    # row, with another plan's call in between leaving its tables behind
+    cases = []
+    for rows, cols, depth, B, kw in [(4, 4, 12, 50, {}), (4, 5, 30, 4, {"precision": "fp32", "order_kind": 1}),
+                                     (4, 5, 30, 4, {"precision": "fp32", "order_kind": 1, "div": 4})]:
+        kw = dict(kw)
+        div = kw.pop("div", 0)
+        m = q.Model(q.Circuit.grid(rows, cols, depth, 3))
+        if div:
+            full = q.Plan(m, batch=B, executor=q.EXEC_STEPWISE, **kw)
+            kw["mem_budget_bytes"] = full.info.arena_bytes // div
+        plan = q.Plan(m, batch=B, executor=q.EXEC_STEPWISE, **kw)
+        assert plan.info.workspace_bytes <= (64 << 20)
+        bits = qi.bitstrings(rows * cols, B, 3)
+        d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
+        cases.append((plan, d_bits, B, rows * cols))
+    assert cases[1][0].info.n_gemm_steps > 0 and cases[2][0].info.n_slices > 1
     other = q.Plan(q.Model(q.Circuit.grid(3, 3, 9, 1)), batch=8)
     o_bits = torch.from_numpy(qi.bitstrings(9, 8, 1).astype(np.int64)).cuda()
-    o_out = torch.zeros(16, dtype=torch.float64, device="cuda")
-    for call in range(2):
-        out = torch.full((2 * B,), float("nan"), dtype=torch.float64, device="cuda")
-        q._lib.check(q.lib().qgm_amplitudes_static(plan._h, d_bits.data_ptr(), B, out.data_ptr(),
-                                                   None))
-        torch.cuda.synchronize()
-        a = _as_complex(out)
-        assert _close(a, ref, 16), f"call {call}"
-        q._lib.check(q.lib().qgm_amplitudes_static(other._h, o_bits.data_ptr(), 8,
-                                                   o_out.data_ptr(), None))
-        torch.cuda.synchronize()
+    o_ref = _bound(q, other, o_bits, 8, 8)
+    for plan, d_bits, B, n in cases:
+        ref = _bound(q, plan, d_bits, B, B)
+        for call in range(2):
+            a = _static(q, plan, d_bits, B, B)
+            assert _close(a, ref, n), f"{n} qubits, call {call}"
+            o = _static(q, other, o_bits, 8, 8)
+            assert _close(o, o_ref, 9), f"interleaved plan, call {call}"
 
 
 def test_static_scratch_rejects_large_plans(q):
