@@ -1,10 +1,15 @@
 """Benchmark: amplitudes/s of random grid circuits by complex graphical-model
 variable elimination on one GB300 (and N replicas under torchrun).
 
-Default workload: 5x5 grid, depth 20, seed 0, a batch of 1024 uniformly random
-output bitstrings, complex64 elimination with an FP64 slice sum.  One step =
-one full pass of the path (leaf factors for the batch, every elimination step,
-FP64 accumulation) over one batch.  Prints ONE JSON line (rank 0).
+Default workload: 5x9 grid, depth 40, seed 0, a batch of 1000 uniformly random
+output bitstrings, computed in passes of 4 (the plan that fits one GPU: a
+55 GB workspace).  One step = one full pass of the path (leaf factors for the
+pass's bitstrings, every elimination step -- GEMM-shaped steps on the tensor
+cores as split-FP16 products, the rest on the FP32 cores --, FP64
+accumulation).  The same passes are also timed with split-BF16 GEMM steps and
+with every GEMM step on the FP32 cores (plain complex64); each precision's
+error against the FP64 oracle's stored amplitudes is stated.  Prints ONE JSON
+line (rank 0).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
   python bench.py --impl reference   # the FP64 CPU oracle on a bounded sample
@@ -14,7 +19,6 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
-import math
 import os
 import statistics
 import subprocess
@@ -31,53 +35,63 @@ import qgm_inputs as qi  # noqa: E402
 METRIC = "amplitudes/sec on 1 GB300 at stated rel. error vs FP64; % of tensor/HBM roofline"
 UNIT = "amplitudes/s"
 L2_BYTES = 129 * 2 ** 20
+# bitstrings per pass where the whole batch does not fit one plan
+PASS_BATCH = {"grid5x9_d40_b1000": 4}
+# FP64 oracle amplitudes stored for the workloads (tests/golden/, written by
+# tests/golden/make_golden.py from the oracle only)
+GOLDEN = {"grid5x9_d40_b1000": "amps_grid5x9_d40.json", "grid6x6_d25_b1000": "amps_grid6x6_d25.json"}
+PRECISIONS = [("split_fp16", "fp16"), ("split_bf16", "bf16"), ("c64", "fp32")]
 
-# DRAM traffic per launch of the dominant kernel from one ncu capture, keyed by
-# the sha1 of the kernel source it was taken on (null once the source changed):
-# for the compiled resident executor, the CUDA source generated for the plan.
-NCU_TRAFFIC = {"e03135235b82": 141824.0}   # qgm_resident_plan, profiles/qgm_resident_plan_grid5x5_d20_b1024.md
+# DRAM traffic per launch of the dominant kernel from one ncu capture, keyed
+# by workload and the sha1 of exec.cu it was taken on (null once it changed)
+NCU_TRAFFIC = {}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid5x5_d20_b1024", choices=sorted(qi.WORKLOADS))
+    ap.add_argument("--workload", default="grid5x9_d40_b1000", choices=sorted(
+        k for k, v in qi.WORKLOADS.items() if v[3] > 0))
+    ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"],
+                    help="GEMM steps of the headline value: split FP16, split BF16 or FP32 cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precisions", action="store_true", help="time the headline precision only")
     ap.add_argument("--executor", type=int, default=0, help="0 auto, 1 stepwise, 2 resident, 3 compiled resident")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
-    return ap.parse_args()
+    ap.add_argument("--custom", default=None, metavar="RxC,DEPTH,BATCH",
+                    help="a smaller seed-0 grid circuit instead of a workload (profiling captures), e.g. 4x8,40,4")
+    a = ap.parse_args()
+    if a.custom:
+        g, d, b = a.custom.split(",")
+        r, c = g.split("x")
+        name = f"grid{r}x{c}_d{d}_b{b}"
+        qi.WORKLOADS[name] = (int(r), int(c), int(d), int(b), False)
+        PASS_BATCH[name] = int(b)
+        a.workload = name
+    return a
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
 def peaks():
-    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
-        with open(p) as f:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d["bf16_tflops_sustained"]), "source": "measured"}
     except Exception:
-        return 6800.0, "fallback"
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
-def kernel_hash(plan=None, chunk=1):
-    """sha1 (12 hex digits) of the dominant kernel's source: the CUDA source
-    generated for the plan when the compiled resident executor runs it, else
-    exec.cu (the other executors' kernels)."""
+def exec_hash():
     h = hashlib.sha1()
-    if plan is not None:
-        h.update(plan.kernel_source(chunk, 0).encode())
-    else:
-        with open(os.path.join(ROOT, "paper_1712_05384_gb300", "csrc", "exec.cu"), "rb") as f:
-            h.update(f.read())
+    with open(os.path.join(ROOT, "paper_1712_05384_gb300", "csrc", "exec.cu"), "rb") as f:
+        h.update(f.read())
     return h.hexdigest()[:12]
 
 
@@ -90,6 +104,7 @@ class Clocks:
     def __init__(self, gpu_index):
         self.idx = gpu_index
         self.proc = None
+        self.out = ""
 
     def __enter__(self):
         try:
@@ -109,8 +124,6 @@ class Clocks:
             except Exception:
                 self.proc.kill()
                 self.out = ""
-        else:
-            self.out = ""
 
     def summary(self):
         sm, mx, reasons = [], None, set()
@@ -129,24 +142,94 @@ class Clocks:
                     reasons.add(n)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_rate(c, bits, seconds):
-    """FP64 oracle (bucket elimination, vertical order) on a time-bounded sample."""
-    from oracle import ugm, ve
+def golden(workload):
+    name = GOLDEN.get(workload)
+    path = os.path.join(ROOT, "tests", "golden", name) if name else None
+    if not path or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    xs = np.array([int(e["x"]) for e in d["amplitudes"]], dtype=np.uint64)
+    ref = np.array([complex(e["re"], e["im"]) for e in d["amplitudes"]])
+    return (xs, ref) if len(xs) else None
+
+
+def reference_amplitudes(workload, c, bits):
+    """(bitstrings, FP64 oracle amplitudes) to state the error against: the
+    stored oracle values, else the state vector on a sample (n <= 25)."""
+    g = golden(workload)
+    if g is not None:
+        return g
+    if c.n <= 25:
+        from oracle import statevector as sv
+        xs = bits[:64]
+        return xs, sv.amplitudes(c, xs)
+    return None
+
+
+def error_measures(a, ref, n):
+    d = np.abs(a - ref)
+    rms = 2.0 ** (-n / 2)
+    big = np.abs(ref) >= rms
+    wide = np.abs(ref) >= 1e-3 * rms
+    return {"max_rel_err": float(np.max(d[big] / np.abs(ref[big]))) if big.any() else None,
+            "max_rel_err_cut": "|a_ref| >= 2^-n/2",
+            "max_rel_err_1e3": float(np.max(d[wide] / np.abs(ref[wide]))) if wide.any() else None,
+            "excluded_1e3": int((~wide).sum()),
+            "max_abs_err_rms": float(np.max(d) * 2.0 ** (n / 2)), "count": int(len(ref)), "against": "FP64 oracle"}
+
+
+def cpu_oracle_sample(workload, c, bits):
+    """The FP64 oracle (oracle/ve.c, plain C, OpenMP over each bucket's
+    entries on every host core) on a bounded sample: (amplitudes/s, sample
+    description, cores).  5x9 depth 40: one of the 2^7 conditioned parts of
+    one bitstring (the oracle slices it to fit host memory), scaled to a
+    whole amplitude; smaller circuits: whole amplitudes for about 10 s."""
+    from oracle import order as O
+    from oracle import ugm, vec
+    cores = os.cpu_count() or 1
     m = ugm.build(c)
-    order = ve.vertical_order(m, c)
+    adj = O.graph(m)
+    order, w = O.min_fill(adj)
+    pr = vec.Prepared(m)
+    if w > 31:
+        sl = O.slice_greedy(adj, order, max_clique=30)
+        part = [v for v in sl]
+        fixed_first = part[:]  # time slice 0 of the first bitstring
+        t0 = time.perf_counter()
+        _one_slice(m, pr, order, fixed_first, int(bits[0]))
+        dt = time.perf_counter() - t0
+        n_parts = 2 ** len(sl)
+        return 1.0 / (dt * n_parts), (f"one of the {n_parts} conditioned parts (slices) of bitstring 0 in "
+                                      f"{dt:.1f} s, scaled to a whole amplitude; oracle/ve.c FP64 bucket "
+                                      f"elimination, min-fill order, {cores} threads"), cores
     t0 = time.perf_counter()
     done = 0
-    for x in bits:
-        ve.amplitude(c, x, m, order)
+    while done < len(bits) and time.perf_counter() - t0 < 10.0:
+        vec.amplitude(c, int(bits[done]), order=order, model=m, prepared=pr)
         done += 1
-        if time.perf_counter() - t0 > seconds:
-            break
     dt = time.perf_counter() - t0
-    return done / dt, done, dt
+    return done / dt, (f"{done} bitstrings in {dt:.1f} s; oracle/ve.c FP64 bucket elimination, min-fill "
+                       f"order, {cores} threads"), cores
+
+
+def _one_slice(m, pr, order, slice_vars, x):
+    from oracle import vec
+    fixed = np.full(m.n_vars, -1, dtype=np.int32)
+    for v in m.inputs:
+        fixed[v] = 0
+    for j, v in enumerate(m.outputs):
+        fixed[v] = (x >> j) & 1
+    for v in slice_vars:
+        fixed[v] = 0
+    elim = np.array([v for v in order if v not in set(slice_vars)], dtype=np.int32)
+    out = np.zeros(2)
+    vec.lib().ve_amplitude(m.n_vars, len(m.factors), pr.rank.ctypes.data, pr.off.ctypes.data, pr.vars.ctypes.data,
+                           pr.toff.ctypes.data, pr.tables.ctypes.data, fixed.ctypes.data, elim.ctypes.data,
+                           len(elim), 0, out.ctypes.data)
 
 
 def run_reference(args, rank, world):
@@ -154,33 +237,25 @@ def run_reference(args, rank, world):
         return
     rows, cols, depth, B, param = qi.WORKLOADS[args.workload]
     c = qi.grid_circuit(rows, cols, depth, 0, param=param)
-    bits = qi.bitstrings(c.n, max(B, 1), 0)
-    per_step = max(1, min(len(bits), 8))
-    from oracle import ugm, ve
-    m = ugm.build(c)
-    order = ve.vertical_order(m, c)
-    for w in range(args.warmup):
-        for x in bits[:per_step]:
-            ve.amplitude(c, x, m, order)
-    t0 = time.perf_counter()
-    for s in range(args.steps):
-        sel = bits[(s * per_step) % len(bits):][:per_step]
-        for x in sel:
-            ve.amplitude(c, x, m, order)
-    dt = time.perf_counter() - t0
-    n_amp = per_step * args.steps
-    v = n_amp / dt
-    sample = (f"{per_step} bitstrings per step of the {args.workload} workload, "
-              f"FP64 bucket elimination in the vertical order (oracle/ve.py)")
+    bits = qi.bitstrings(c.n, B, 0)
+    cores = os.cpu_count() or 1
+    ts, dts = [], []
+    sample = ""
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        rate, sample, cores = cpu_oracle_sample(args.workload, c, bits[s % len(bits):])
+        if s >= args.warmup:
+            ts.append(rate)
+            dts.append(time.perf_counter() - t0)
+    v = float(np.mean(ts))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic",
-        "config": {"workload": args.workload, "grid": f"{rows}x{cols}", "depth": depth,
-                   "batch_per_gpu": B, "seed": 0, "parallelism": "replicas1",
-                   "sample_per_step": per_step},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(dts)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": f"{rows}x{cols}", "depth": depth, "batch": B, "seed": 0,
+                   "parallelism": "replicas1"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: " + sample},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -194,7 +269,7 @@ def main():
     import torch
     import torch.distributed as dist
     import paper_1712_05384_gb300 as q
-    from paper_1712_05384_gb300 import build
+    from paper_1712_05384_gb300 import build, shard
 
     if world > 1:
         dist.init_process_group("nccl")
@@ -207,135 +282,226 @@ def main():
     q.lib()
 
     rows, cols, depth, B, param = qi.WORKLOADS[args.workload]
-    if B == 0:
-        raise SystemExit("the benchmark runs batch workloads")
+    P = PASS_BATCH.get(args.workload, B)
     c_py = qi.grid_circuit(rows, cols, depth, 0, param=param)
-    # weak scaling: each rank takes its own batch of B bitstrings (a
-    # contiguous block of the job's B * world; no data-path collective)
-    from paper_1712_05384_gb300 import shard
-    all_bits = qi.bitstrings(c_py.n, B * world, 0)
-    bits = shard.shard(all_bits, rank, world)
-    plan = q.Plan(q.Model(q.Circuit.grid(rows, cols, depth, 0, param)), batch=B,
-                  executor=args.executor).bind()
-    info = plan.info
+    n = c_py.n
+    # weak scaling: each rank takes its own block of B bitstrings (no
+    # data-path collective)
+    bits = shard.shard(qi.bitstrings(n, B * world, 0), rank, world)
+    model = q.Model(q.Circuit.grid(rows, cols, depth, 0, param))
     stream = torch.cuda.current_stream(dev)
-    d_bits = torch.from_numpy(bits.astype(np.int64)).to(dev)
-    d_out = torch.empty(2 * B, dtype=torch.float64, device=dev)
+    d_all = torch.from_numpy(bits.astype(np.int64)).to(dev)
+    d_pass = torch.empty(P, dtype=torch.int64, device=dev)
+    d_out = torch.empty(2 * P, dtype=torch.float64, device=dev)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    n_pass = (len(bits) + P - 1) // P
+    ref = reference_amplitudes(args.workload, c_py, bits) if rank == 0 else None
+    pk = peaks()
 
-    def step():
-        plan.amplitudes(d_bits, d_out, B=B, stream=stream)
+    def make_plan(precision):
+        return q.Plan(model, batch=P, executor=args.executor, precision=precision,
+                      order_kind=q.ORDER_MINFILL if P < B else q.ORDER_AUTO).bind()
 
-    for _ in range(max(args.warmup, 3)):
-        step()
-    torch.cuda.synchronize()
-    if plan.status(stream) != 0:
-        raise RuntimeError("device status not OK after warm-up")
+    def run_pass(plan, i):
+        k = i % n_pass
+        m = min(P, len(bits) - k * P)
+        d_pass[:m].copy_(d_all[k * P:k * P + m])
+        plan.amplitudes(d_pass, d_out, B=m, stream=stream)
 
-    # device-timed region: K steps, L2 flushed (untimed) between them
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        for i in range(args.steps):
+    def amplitudes_of(plan, xs):
+        out = []
+        for k in range(0, len(xs), P):
+            out.append(plan.amplitudes_host(np.asarray(xs[k:k + P], dtype=np.uint64)))
+        return np.concatenate(out)
+
+    def timed(plan, steps, warmup, clocks=None):
+        for i in range(max(warmup, 3)):
+            run_pass(plan, i)
+        torch.cuda.synchronize()
+        if plan.status(stream) != 0:
+            raise RuntimeError("device status not OK after warm-up")
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ctx = Clocks(local) if clocks else None
+        if ctx:
+            ctx.__enter__()
+        for i in range(steps):
             flush.fill_(float(i))
             evs[i][0].record(stream)
-            step()
+            run_pass(plan, i)
             evs[i][1].record(stream)
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    t_ms = sum(a.elapsed_time(b) for a, b in evs)
-    if world > 1:
-        t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-    value = world * B * args.steps / (t_ms / 1e3)
+        if ctx:
+            ctx.__exit__()
+        if plan.status(stream) != 0:
+            raise RuntimeError("device status not OK in the timed region")
+        t_ms = sum(a.elapsed_time(b) for a, b in evs)
+        if world > 1:
+            dist.barrier()
+            t = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_ms = float(t.item())
+        return t_ms, ctx
 
-    # end to end through the public host API: host bitstrings in, host
+    # ---- headline precision
+    plan = make_plan(args.precision)
+    info = plan.info
+    t_ms, clk = timed(plan, args.steps, args.warmup, clocks=True)
+    amps_per_step = min(P, len(bits))
+    value = world * amps_per_step * args.steps / (t_ms / 1e3)
+    err = error_measures(amplitudes_of(plan, ref[0]), ref[1], n) if ref is not None else None
+
+    # ---- end to end through the public host API: host bitstrings in, host
     # amplitudes out, copies inside the timed region
-    hb = torch.from_numpy(bits.view(np.int64).copy()).pin_memory()
-    hout = torch.empty(2 * B, dtype=torch.float64).pin_memory()
+    hb = torch.from_numpy(bits[:P].view(np.int64).copy()).pin_memory()
+    hout = torch.empty(2 * P, dtype=torch.float64).pin_memory()
     for _ in range(3):
-        q._lib.check(q.lib().qgm_amplitudes_host(plan._h, hb.data_ptr(), B, hout.data_ptr(),
-                                                 stream.cuda_stream))
+        q._lib.check(q.lib().qgm_amplitudes_host(plan._h, hb.data_ptr(), P, hout.data_ptr(), stream.cuda_stream))
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
-        q._lib.check(q.lib().qgm_amplitudes_host(plan._h, hb.data_ptr(), B, hout.data_ptr(),
-                                                 stream.cuda_stream))
+    for i in range(args.steps):
+        k = i % n_pass
+        m = min(P, len(bits) - k * P)
+        hb[:m].copy_(torch.from_numpy(bits[k * P:k * P + m].view(np.int64)))
+        q._lib.check(q.lib().qgm_amplitudes_host(plan._h, hb.data_ptr(), m, hout.data_ptr(), stream.cuda_stream))
     e2e_s = time.perf_counter() - t0
     if world > 1:
         t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
-    e2e = world * B * args.steps / e2e_s
+    e2e = world * amps_per_step * args.steps / e2e_s
 
-    # roofline of the dominant kernel, per-launch times from a pass with CUDA
-    # events on the launching stream
+    # ---- roofline per step class, from per-launch CUDA events of one pass
     step_bytes, step_flops = plan.step_costs()
     ex_kind, ex_chunk, ex_smem = plan.executor()
-    reps = 5
-    ms = np.zeros(info.n_steps + 2)
-    for _ in range(reps):
-        flush.fill_(1.0)
-        ms += plan.profile(d_bits, d_out, B=B, stream=stream)
-    ms /= reps
-    traffic = NCU_TRAFFIC.get(kernel_hash(plan if ex_kind == q.EXEC_COMPILED else None, ex_chunk))
-    if ex_kind in (q.EXEC_RESIDENT, q.EXEC_COMPILED):
-        # all intermediates live in shared memory: bound by the SM's FP32/ALU
-        # issue, peak = 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz
+    kinds = plan.step_kernels()
+    gemms = plan.gemm_shapes()
+    reps = 3
+    roof_steps = {}
+    fp32_peak = q._lib.measure_fp32_peak(stream.cuda_stream) if hasattr(q._lib, "measure_fp32_peak") else None
+    if ex_kind == q.EXEC_STEPWISE:
+        ms = np.zeros(info.n_steps + 2)
+        ms_split = np.zeros(len(gemms))
+        ms_prod = np.zeros(len(gemms))
+        for _ in range(reps):
+            flush.fill_(1.0)
+            ms += plan.profile(d_pass, d_out, B=P, stream=stream)
+            flush.fill_(1.0)
+            a, b = plan.profile_gemm(d_pass, d_out, B=P, stream=stream)
+            ms_split += a
+            ms_prod += b
+        ms /= reps
+        ms_split /= reps
+        ms_prod /= reps
+        tc = [g for g in gemms if g["tc"]]
+        tc_idx = [i for i, g in enumerate(gemms) if g["tc"]]
+        g_flops = float(sum(step_flops[g["step"]] for g in tc))
+        g_ms = float(ms_prod[tc_idx].sum()) if tc_idx else 0.0
+        ps = [s for s in range(info.n_steps) if kinds[s] != 3]
+        ps_bytes = float(step_bytes[ps].sum())
+        ps_ms = float(ms[[1 + s for s in ps]].sum())
+        pass_ms = float(ms.sum())
+        if tc and g_ms > 0:
+            ach = g_flops / (g_ms / 1e3) / 1e12
+            roof = {"bound": "tensor", "achieved": ach, "peak": pk["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / pk["bf16_tflops"], "traffic": NCU_TRAFFIC.get((args.workload, exec_hash())),
+                    "kernel": f"k_gemm_tc (GEMM-shaped steps, split {'FP16' if args.precision == 'fp16' else 'BF16'} "
+                              f"on tcgen05; algorithmic flops 8*M*N*K per complex product, split terms not counted)",
+                    "frac_sustained": ach / pk["bf16_tflops_sustained"], "peak_source": pk["source"] + " (bf16 burst)",
+                    "algorithmic_flops_per_pass": g_flops, "kernel_ms_per_pass": g_ms,
+                    "tensor_pipe_flops_per_algorithmic_flop": 3.0 if args.precision == "fp16" else 6.0}
+        else:
+            ach = ps_bytes / (ps_ms / 1e3) / 1e9
+            roof = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / pk["hbm_gbs"], "traffic": None, "kernel": "product-sum steps",
+                    "algorithmic_bytes_per_pass": ps_bytes, "kernel_ms_per_pass": ps_ms,
+                    "peak_source": pk["source"]}
+        roof_steps = {
+            "pass_ms_kernel_by_kernel": pass_ms,
+            "gemm_tensor_core": {"steps": len(tc), "algorithmic_tflop": g_flops / 1e12, "ms": g_ms,
+                                 "tflops": g_flops / (g_ms / 1e3) / 1e12 if g_ms else None,
+                                 "frac_bf16_burst": (g_flops / (g_ms / 1e3) / 1e12) / pk["bf16_tflops"] if g_ms else None,
+                                 "frac_bf16_sustained": (g_flops / (g_ms / 1e3) / 1e12) / pk["bf16_tflops_sustained"]
+                                 if g_ms else None},
+            "gemm_operand_split": {"ms": float(ms_split.sum())},
+            "gemm_fp32_cores": {"steps": len(gemms) - len(tc),
+                                "ms": float(ms_prod[[i for i, g in enumerate(gemms) if not g["tc"]]].sum())
+                                if len(gemms) > len(tc) else 0.0},
+            "product_sum": {"steps": len(ps), "algorithmic_gb": ps_bytes / 1e9, "ms": ps_ms,
+                            "gbs": ps_bytes / (ps_ms / 1e3) / 1e9 if ps_ms else None,
+                            "frac_hbm": ps_bytes / (ps_ms / 1e3) / 1e9 / pk["hbm_gbs"] if ps_ms else None},
+            "per_gemm": [dict(g, split_ms=float(ms_split[i]), product_ms=float(ms_prod[i]),
+                              tflops=float(step_flops[g["step"]] / (ms_prod[i] / 1e3) / 1e12) if ms_prod[i] else None)
+                         for i, g in enumerate(gemms)],
+        }
+        launches = args.steps * int(info.n_slices * (info.n_steps + 2 + 2 * len(tc)) + 1)
+    else:
+        ms = np.zeros(info.n_steps + 2)
+        for _ in range(reps):
+            flush.fill_(1.0)
+            ms += plan.profile(d_pass, d_out, B=P, stream=stream)
+        ms /= reps
         k_ms = float(ms[0])
-        peak = 152 * 128 * 2 * 2.070e9 / 1e12
-        achieved = float(step_flops.sum()) / (k_ms / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic,
+        peak = fp32_peak or 152 * 128 * 2 * 2.070e9 / 1e12
+        ach = float(step_flops.sum()) / (k_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                "traffic": None,
                 "kernel": f"{'qgm_resident_plan (compiled for this plan)' if ex_kind == q.EXEC_COMPILED else 'k_resident'}"
                           f" (whole pass, {ex_chunk} bitstring(s) per CTA, {ex_smem} B shared memory)",
-                "algorithmic_flops_per_pass": float(step_flops.sum()),
-                "algorithmic_bytes_per_pass": float(step_bytes.sum()),
-                "kernel_ms_per_pass": k_ms,
-                "peak_source": "derived: FP32 lanes x SMs x max SM clock"}
+                "algorithmic_flops_per_pass": float(step_flops.sum()), "kernel_ms_per_pass": k_ms,
+                "peak_source": "measured FP32 FMA microbenchmark (qgm_measure_fp32_peak)" if fp32_peak else
+                               "derived: FP32 lanes x SMs x max SM clock"}
         launches = args.steps
-    else:
-        k_ms = float(ms[1:-1].sum())
-        achieved = float(step_bytes.sum()) / (k_ms / 1e3) / 1e9
-        peak, peak_kind = peaks()
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_step_batched (all elimination steps)",
-                "algorithmic_bytes_per_pass": float(step_bytes.sum()),
-                "kernel_ms_per_pass": k_ms, "peak_source": peak_kind}
-        launches = args.steps * int(info.n_slices * (info.n_steps + 2) + 1)
 
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+        "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp16": "c64 (GEMM steps split-fp16 x3)", "bf16": "c64 (GEMM steps split-bf16 x6)",
+                  "fp32": "c64"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": args.workload, "grid": f"{rows}x{cols}", "depth": depth,
-                   "batch_per_gpu": B, "seed": 0, "order": info.order_kind,
-                   "max_clique": info.max_clique, "steps_per_pass": info.n_steps,
-                   "slices": info.n_slices, "parallelism": f"replicas{world}",
+        "config": {"workload": args.workload, "grid": f"{rows}x{cols}", "depth": depth, "batch_per_gpu": B,
+                   "bitstrings_per_step": amps_per_step, "seed": 0, "order": info.order_kind,
+                   "max_clique": info.max_clique, "steps_per_pass": info.n_steps, "slices": info.n_slices,
+                   "workspace_gb": info.workspace_bytes / 1e9, "parallelism": f"replicas{world}",
                    "executor": {1: "stepwise", 2: "resident", 3: "compiled resident"}.get(ex_kind), "chunk": ex_chunk,
-                   "gemm_steps": info.n_gemm_steps, "gemm_steps_split_bf16": info.n_gemm_tc_steps,
-                   "l2": "flushed between timed steps (264 MB write, untimed)"},
-        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * B,
-                "d2h_bytes_per_step": 16 * B},
+                   "gemm_steps": info.n_gemm_steps, "gemm_steps_tensor_core": info.n_gemm_tc_steps,
+                   "gemm_precision": args.precision,
+                   "l2": "flushed between timed steps (264 MB write, untimed); the pass's tensors exceed L2"},
+        "error": err,
+        "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * amps_per_step,
+                "d2h_bytes_per_step": 16 * amps_per_step},
         "roofline": roof,
+        "roofline_steps": roof_steps,
+        "fp32_peak_tflops_measured": fp32_peak,
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clk.summary() if clk else None,
     }
+    # ---- the same passes with each precision of the GEMM steps
+    if not args.no_precisions:
+        del plan
+        torch.cuda.empty_cache()
+        per = {}
+        for name, prec in PRECISIONS:
+            p2 = make_plan(prec)
+            ks = max(2, args.steps // 2)
+            t2, _ = timed(p2, ks, 1)
+            per[name] = {"value": world * amps_per_step * ks / (t2 / 1e3), "ms_per_step": t2 / ks,
+                         "gemm_steps_tensor_core": p2.info.n_gemm_tc_steps,
+                         "error": error_measures(amplitudes_of(p2, ref[0]), ref[1], n) if ref is not None else None}
+            del p2
+            torch.cuda.empty_cache()
+        res["precisions"] = per
+        if per["c64"]["value"]:
+            res["speedup_split_fp16_vs_c64"] = per["split_fp16"]["value"] / per["c64"]["value"]
+            res["speedup_split_bf16_vs_c64"] = per["split_bf16"]["value"] / per["c64"]["value"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, done, dt = cpu_oracle_rate(c_py, bits, args.cpu_seconds)
-        res["cpu_baseline"] = {
-            "value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"first {done} of the {B} bitstrings, {dt:.1f} s, FP64 bucket elimination "
-                      f"(oracle/ve.py, vertical order, numpy single thread)"}
+        rate, sample, cores = cpu_oracle_sample(args.workload, c_py, bits)
+        res["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

@@ -306,7 +306,22 @@ int qgm_eliminate(qgm_plan *p, double *d_out, void *stream);
 int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
                      float *ms, void *stream);
 
-/* Executor chosen at bind time: *kind (QGM_EXEC_STEPWISE, _RESIDENT or
+/* Per GEMM-shaped step (in step order, as qgm_plan_get_gemm lists them) of
+ * slice 0 of a stepwise plan: milliseconds of the operand split into 16-bit
+ * planes in ms_split[c] (0 for a step on the FP32 cores) and of the product
+ * kernel in ms_product[c] (CUDA events on `stream` around each launch;
+ * host float arrays of the number of GEMM steps).  Synchronises.  Errors:
+ * QGM_ERR_ARG (not stepwise, bad sizes), QGM_ERR_CUDA. */
+int qgm_plan_profile_gemm(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
+                          float *ms_split, float *ms_product, void *stream);
+
+/* Measurement utility (no counterpart in the paper): FP32 FMA throughput of
+ * the current device in TFLOP/s (2 flops per FMA), from independent FMA
+ * chains on every SM timed with CUDA events on `stream`; the peak against
+ * which kernels bound by FP32 arithmetic are reported.  Synchronises. */
+int qgm_measure_fp32_peak(double *tflops, void *stream);
+
+/* Executor chosen at bind time:/* Executor chosen at bind time: *kind (QGM_EXEC_STEPWISE, _RESIDENT or
  * _COMPILED), the bitstrings per CTA *chunk and the dynamic shared memory per
  * CTA (resident and compiled). */
 int qgm_plan_get_executor(const qgm_plan *p, int32_t *kind, int32_t *chunk, int64_t *smem_bytes);

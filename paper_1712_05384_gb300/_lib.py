@@ -89,6 +89,8 @@ _SIGS = {
     "qgm_plan_get_step_cost": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64],
     "qgm_plan_get_gemm": [_P, _I32P, C.c_int64, _I64P],
     "qgm_plan_profile": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), _P],
+    "qgm_plan_profile_gemm": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), C.POINTER(C.c_float), _P],
+    "qgm_measure_fp32_peak": [C.POINTER(C.c_double), _P],
     "qgm_plan_free": [_P],
     "qgm_plan_bind": [_P, _P, C.c_size_t, _P],
     "qgm_amplitudes": [_P, _P, C.c_int64, _P, _P],
@@ -364,6 +366,17 @@ class Plan:
                                      ms.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
         return ms
 
+    def profile_gemm(self, d_bits, d_out, B=None, stream=None):
+        """Per GEMM step: (split ms, product ms) arrays of one slice."""
+        B = d_bits.numel() if B is None else B
+        n = self.info.n_gemm_steps
+        a = np.zeros(max(n, 1), dtype=np.float32)
+        b = np.zeros(max(n, 1), dtype=np.float32)
+        check(lib().qgm_plan_profile_gemm(self._h, _ptr(d_bits), B, _ptr(d_out),
+                                          a.ctypes.data_as(C.POINTER(C.c_float)),
+                                          b.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
+        return a[:n], b[:n]
+
     def kernel_source(self, chunk=1, part=0, min_blocks=0) -> str:
         """CUDA source of the compiled resident kernel for this plan (no GPU needed)."""
         n = C.c_int64()
@@ -390,6 +403,13 @@ class Plan:
         if getattr(self, "_h", None) and _lib is not None:
             _lib.qgm_plan_free(self._h)
             self._h = None
+
+
+def measure_fp32_peak(stream=None):
+    """FP32 FMA throughput of the current device, TFLOP/s (microbenchmark)."""
+    t = C.c_double()
+    check(lib().qgm_measure_fp32_peak(C.byref(t), _stream(stream)))
+    return t.value
 
 
 # ---------------------------------------------------------------- App. B, C

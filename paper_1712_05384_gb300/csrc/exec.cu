@@ -1237,6 +1237,25 @@ __global__ void k_sample(const double *cdf, int64_t t, int64_t m, uint64_t seed,
   }
 }
 
+// FP32 peak microbenchmark: independent FMA chains per thread (enough of
+// them to cover the FMA latency), the result kept live through a sink.
+constexpr int FMA_CHAINS = 8;
+__device__ float g_fma_sink;
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, float x) {
+  float acc[FMA_CHAINS];
+#pragma unroll
+  for (int c = 0; c < FMA_CHAINS; ++c) acc[c] = x + (float)(threadIdx.x + c);
+  const float m = 0.999999f, a = 1e-7f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < FMA_CHAINS; ++c) acc[c] = fmaf(acc[c], m, a);
+  }
+  float t = 0.f;
+#pragma unroll
+  for (int c = 0; c < FMA_CHAINS; ++c) t += acc[c];
+  if (t == 12345.678f) g_fma_sink = t;
+}
+
 // Zero the FP64 result and the status, restart at slice 0.
 __global__ void k_init(double2 *out, int64_t n_out, Header *hdr) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < n_out;
@@ -1538,7 +1557,7 @@ static void launch_leaves(qgm_plan *p, const uint64_t *d_bits, int64_t B, cudaSt
 // Tensor-core form of a GEMM-shaped step: split both operands into planes,
 // then the product (see k_split and k_gemm_tc).
 static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c, int64_t planes_off, int P,
-                           Meta *meta, Header *hdr, cudaStream_t st) {
+                           Meta *meta, Header *hdr, cudaStream_t st, cudaEvent_t mid = nullptr) {
   if (c.swap) gemm_swap_roles(g);
   for (int side = 0; side < 2; ++side) {
     const bool ms = side == 0;
@@ -1566,6 +1585,7 @@ static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c
     if (P == 4) k_split<4><<<blocks, 256, 0, st>>>(ws, s, meta, hdr);
     else k_split<6><<<blocks, 256, 0, st>>>(ws, s, meta, hdr);
   }
+  if (mid) cudaEventRecord(mid, st);
   TcArgs a{};
   a.pm_off = planes_off;
   a.pn_off = planes_off + c.bytesM;
@@ -1625,12 +1645,12 @@ static cudaError_t tc_set_smem() {
 
 static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const GemmDesc *gemms, Meta *meta,
                            Header *hdr, cudaStream_t st, bool tc = false, int64_t planes_off = 0,
-                           int planes = 4) {
+                           int planes = 4, cudaEvent_t mid = nullptr) {
   const uint64_t rows = 1ull << d.w_out;
   if (d.gemm >= 0 && gemms && tc) {
     const TcCfg c = tc_config(gemms[d.gemm], Bp, planes);
     if (c.ok) {
-      launch_gemm_tc(ws, sms, Bp, gemms[d.gemm], c, planes_off, planes, meta, hdr, st);
+      launch_gemm_tc(ws, sms, Bp, gemms[d.gemm], c, planes_off, planes, meta, hdr, st, mid);
       return;
     }
   }
@@ -1683,10 +1703,10 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
   }
 }
 
-static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st) {
+static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st, cudaEvent_t mid = nullptr) {
   char *ws = p->exec->ws;
   launch_step_ws(ws, p->exec->sms, p->Bp, d, p->gemms.data(), reinterpret_cast<Meta *>(ws + p->off_meta),
-                 reinterpret_cast<Header *>(ws + p->off_header), st, p->gemm_tc, p->off_planes, p->tc_planes);
+                 reinterpret_cast<Header *>(ws + p->off_header), st, p->gemm_tc, p->off_planes, p->tc_planes, mid);
 }
 
 static void launch_accumulate(qgm_plan *p, double2 *d_out, int64_t n_out, cudaStream_t st) {
@@ -2111,6 +2131,81 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
   CK(cudaEventSynchronize(ev[n]));
   for (int i = 0; i < n; ++i) CK(cudaEventElapsedTime(&ms[i], ev[i], ev[i + 1]));
   for (auto &e : ev) cudaEventDestroy(e);
+  return QGM_OK;
+}
+
+int qgm_plan_profile_gemm(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out, float *ms_split,
+                          float *ms_product, void *stream) {
+  int rc = check_bound(p, "qgm_plan_profile_gemm");
+  if (rc) return rc;
+  if (p->output_mode != QGM_OUT_BATCH || B < 1 || B > p->batch || !d_bitstrings || !d_out || !ms_split ||
+      !ms_product) {
+    set_error("qgm_plan_profile_gemm: need a batch plan, 1 <= B <= %lld and non-null buffers",
+              (long long)p->batch);
+    return QGM_ERR_ARG;
+  }
+  if (p->exec->kind != QGM_EXEC_STEPWISE) {
+    set_error("qgm_plan_profile_gemm: needs the stepwise executor");
+    return QGM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Header *hdr = reinterpret_cast<Header *>(p->exec->ws + p->off_header);
+  k_init<<<1, 256, 0, st>>>(reinterpret_cast<double2 *>(d_out), B << p->open_in_batch, hdr);
+  launch_leaves(p, d_bitstrings, B, st);
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> n_ev;
+  for (const StepDesc &d : p->steps) {
+    if (d.gemm < 0) {
+      launch_step(p, d, st);
+      continue;
+    }
+    cudaEvent_t e[3];
+    for (auto &x : e) CK(cudaEventCreate(&x));
+    CK(cudaEventRecord(e[0], st));
+    const bool tc = p->gemm_tc && tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes).ok;
+    launch_step(p, d, st, tc ? e[1] : nullptr);
+    if (!tc) CK(cudaEventRecord(e[1], st));
+    CK(cudaEventRecord(e[2], st));
+    for (auto &x : e) ev.push_back(x);
+  }
+  launch_accumulate(p, reinterpret_cast<double2 *>(d_out), B << p->open_in_batch, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  for (size_t c = 0; c < ev.size() / 3; ++c) {
+    CK(cudaEventElapsedTime(&ms_split[c], ev[3 * c], ev[3 * c + 1]));
+    CK(cudaEventElapsedTime(&ms_product[c], ev[3 * c + 1], ev[3 * c + 2]));
+  }
+  for (auto &x : ev) cudaEventDestroy(x);
+  return QGM_OK;
+}
+
+int qgm_measure_fp32_peak(double *tflops, void *stream) {
+  if (!tflops) {
+    set_error("qgm_measure_fp32_peak: null argument");
+    return QGM_ERR_ARG;
+  }
+  int dev = 0, sms = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int iters = 1 << 14;
+  const dim3 grid((unsigned)sms * 8), block(256);
+  k_fma_peak<<<grid, block, 0, st>>>(iters, 1.f);  // warm-up
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, st));
+  const int reps = 5;
+  for (int r = 0; r < reps; ++r) k_fma_peak<<<grid, block, 0, st>>>(iters, 1.f);
+  CK(cudaEventRecord(b, st));
+  CK(cudaGetLastError());
+  CK(cudaEventSynchronize(b));
+  float ms = 0;
+  CK(cudaEventElapsedTime(&ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  const double flops = (double)reps * grid.x * block.x * (double)iters * FMA_CHAINS * 2.0;
+  *tflops = flops / (ms * 1e-3) / 1e12;
   return QGM_OK;
 }
 
