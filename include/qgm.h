@@ -187,6 +187,13 @@ typedef struct {
   int32_t resident_chunk;     /* bitstrings per CTA of the resident executor:
                                  1, 2, 4 or 8; 0 = chosen at bind (fewest
                                  waves x chunk on the bound device) */
+  int32_t autotune;           /* 1: qgm_plan_bind times the candidate launch
+                                 parameters of every step that has several (the
+                                 tensor-core GEMM's N tile: 256, 128 or 64
+                                 columns; the batched product-sum kernel's term
+                                 groups: 1, 2 or 4) on the bound device, on
+                                 tensors from one pass over an all-zero batch,
+                                 and keeps the fastest; 0: fixed rules */
   int32_t gemm_precision;     /* GEMM-shaped steps whose tensor-core form exists
                                  (one side >= 128 rows, batch entries counted
                                  when the other side has no batch axis; the
@@ -258,6 +265,19 @@ int qgm_plan_get_step_kernels(const qgm_plan *p, int32_t *kind, int64_t cap);
 /* Algorithmic cost of step s: bytes[s] (inputs read once + output written,
  * complex64) and flops[s] (real flops of the products and sums). */
 int qgm_plan_get_step_cost(const qgm_plan *p, double *bytes, double *flops, int64_t cap);
+/* Structure of step s for reports and tests: rec = [U, k, m, then per input
+ * i: r_i, batched_i, and the positions in the step's union (summed variables
+ * first, each group in elimination order) of its r_i variables].  *n = the
+ * record's length; rec may be NULL to query it.  Host only. */
+int qgm_plan_get_step_inputs(const qgm_plan *p, int32_t step, int32_t *rec, int64_t cap, int64_t *n);
+
+/* Autotuner choices (qgm_plan_opts.autotune, after qgm_plan_bind): for the
+ * c-th tuned step, rec[4c .. 4c+3] = step index, tensor-core N tile cap (0:
+ * not a tensor-core step), product-sum term groups (0: not tuned), and
+ * ms[2c], ms[2c+1] = milliseconds with the fixed rules and with the choice.
+ * *n = the number of tuned steps; rec/ms may be NULL to query it. */
+int qgm_plan_get_tuning(const qgm_plan *p, int32_t *rec, float *ms, int64_t cap, int64_t *n);
+
 /* Shapes of the GEMM-shaped steps (Sec. IV, Eq. par_sum with two large
  * operands sharing every summed variable): for the c-th such step, c < cap,
  * rec[9c .. 9c+8] = step index, nm, nn, nk, ns (variables private to A, to B,
@@ -314,6 +334,12 @@ int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, doubl
  * QGM_ERR_ARG (not stepwise, bad sizes), QGM_ERR_CUDA. */
 int qgm_plan_profile_gemm(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out,
                           float *ms_split, float *ms_product, void *stream);
+
+/* Per step s of the last slice run on the bound workspace: the recorded
+ * maximum of its output (float bits of max(|re|, |im|) of the scaled values,
+ * maxbits[s]) and the output's power-of-two exponent (exps[s]); host arrays
+ * of n_steps.  For tests and reports of the rescaling (A7).  Synchronises. */
+int qgm_plan_step_stats(qgm_plan *p, uint32_t *maxbits, int32_t *exps, int64_t cap, void *stream);
 
 /* Measurement utility (no counterpart in the paper): FP32 FMA throughput of
  * the current device in TFLOP/s (2 flops per FMA), from independent FMA

@@ -40,7 +40,7 @@ class qgm_plan_opts(C.Structure):
                 ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
                 ("no_gemm", C.c_int32), ("gradients", C.c_int32), ("trees", C.c_int32),
                 ("open_mask", C.c_uint64),
-                ("resident_chunk", C.c_int32), ("gemm_precision", C.c_int32)]
+                ("resident_chunk", C.c_int32), ("autotune", C.c_int32), ("gemm_precision", C.c_int32)]
 
 
 class qgm_xeb_result(C.Structure):
@@ -88,9 +88,12 @@ _SIGS = {
     "qgm_plan_get_step_kernels": [_P, _I32P, C.c_int64],
     "qgm_plan_get_step_cost": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64],
     "qgm_plan_get_gemm": [_P, _I32P, C.c_int64, _I64P],
+    "qgm_plan_get_tuning": [_P, _I32P, C.POINTER(C.c_float), C.c_int64, _I64P],
+    "qgm_plan_get_step_inputs": [_P, C.c_int32, _I32P, C.c_int64, _I64P],
     "qgm_plan_profile": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), _P],
     "qgm_plan_profile_gemm": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), C.POINTER(C.c_float), _P],
     "qgm_measure_fp32_peak": [C.POINTER(C.c_double), _P],
+    "qgm_plan_step_stats": [_P, C.POINTER(C.c_uint32), _I32P, C.c_int64, _P],
     "qgm_plan_free": [_P],
     "qgm_plan_bind": [_P, _P, C.c_size_t, _P],
     "qgm_amplitudes": [_P, _P, C.c_int64, _P, _P],
@@ -245,7 +248,7 @@ class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
                  resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=None,
-                 split_bf16=None, precision=None):
+                 split_bf16=None, precision=None, autotune=False):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -265,6 +268,7 @@ class Plan:
         if precision is None and split_bf16 is not None:
             precision = "bf16" if split_bf16 else "fp32"
         o.gemm_precision = {None: 0, "fp16": 2, "bf16": 1, "fp32": -1}[precision]
+        o.autotune = 1 if autotune else 0
         # amplitudes per bitstring: its open qubits run over all 2^k values
         self.n_open = bin(open_mask).count("1") if output_mode == OUT_BATCH else 0
         self._order_buf = None
@@ -315,6 +319,33 @@ class Plan:
         check(lib().qgm_plan_get_step_cost(self._h, b.ctypes.data_as(C.POINTER(C.c_double)),
                                            f.ctypes.data_as(C.POINTER(C.c_double)), n))
         return b[:n], f[:n]
+
+    def step_inputs(self, step):
+        """(union size, k, [(vars as union positions, batched) per input]) of a
+        step; union positions < k are the summed variables."""
+        n = C.c_int64()
+        check(lib().qgm_plan_get_step_inputs(self._h, step, None, 0, C.byref(n)))
+        a = np.zeros(max(n.value, 1), dtype=np.int32)
+        check(lib().qgm_plan_get_step_inputs(self._h, step, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
+        U, k, m = int(a[0]), int(a[1]), int(a[2])
+        i, ins = 3, []
+        for _ in range(m):
+            r, b = int(a[i]), int(a[i + 1])
+            ins.append((list(map(int, a[i + 2:i + 2 + r])), b))
+            i += 2 + r
+        return U, k, ins
+
+    def tuning(self):
+        """Autotuner choices after bind: list of dicts (step, nt_cap, T,
+        ms_rule, ms_best)."""
+        n = C.c_int64()
+        check(lib().qgm_plan_get_tuning(self._h, None, None, 0, C.byref(n)))
+        r = np.zeros(4 * max(n.value, 1), dtype=np.int32)
+        m = np.zeros(2 * max(n.value, 1), dtype=np.float32)
+        check(lib().qgm_plan_get_tuning(self._h, r.ctypes.data_as(_I32P), m.ctypes.data_as(C.POINTER(C.c_float)),
+                                        n.value, C.byref(n)))
+        return [{"step": int(r[4 * c]), "nt_cap": int(r[4 * c + 1]), "T": int(r[4 * c + 2]),
+                 "ms_rule": float(m[2 * c]), "ms_best": float(m[2 * c + 1])} for c in range(n.value)]
 
     def gemm_shapes(self):
         """GEMM-shaped steps: list of dicts (step, nm, nn, nk, ns, a_bat,
@@ -376,6 +407,15 @@ class Plan:
                                           a.ctypes.data_as(C.POINTER(C.c_float)),
                                           b.ctypes.data_as(C.POINTER(C.c_float)), _stream(stream)))
         return a[:n], b[:n]
+
+    def step_stats(self, stream=None):
+        """(max |value| of each step's scaled output, its exponent) after a run."""
+        n = self.info.n_steps
+        mb = np.zeros(max(n, 1), dtype=np.uint32)
+        ex = np.zeros(max(n, 1), dtype=np.int32)
+        check(lib().qgm_plan_step_stats(self._h, mb.ctypes.data_as(C.POINTER(C.c_uint32)), ex.ctypes.data_as(_I32P),
+                                        n, _stream(stream)))
+        return mb[:n].view(np.float32).copy(), ex[:n]
 
     def kernel_source(self, chunk=1, part=0, min_blocks=0) -> str:
         """CUDA source of the compiled resident kernel for this plan (no GPU needed)."""

@@ -191,9 +191,10 @@ __device__ void build_tables(const StepDesc &d, int r0, int lt, int Bp, int64_t 
 // Product-sum step, batched output: thread (x, y) = (pair of batch entries,
 // term group).  Rows are walked at stride gridDim.y (a power of two), terms
 // at stride blockDim.y (a power of two); addresses advance by table lookups.
-__global__ void __launch_bounds__(1024)
+template <int M>
+__global__ void __launch_bounds__(512)
     k_step_batched(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp, int logP) {
-  __shared__ float4 part[1024];
+  __shared__ float4 part[512];
   __shared__ int64_t rowtab[MAXIN][ROWTAB];
   __shared__ int64_t etab[MAXIN][ETAB];
   const int tx = threadIdx.x, ty = threadIdx.y, T = blockDim.y;
@@ -206,16 +207,16 @@ __global__ void __launch_bounds__(1024)
   build_tables(d, r0, lt, Bp, rowtab, etab, tid, STEP_THREADS * T);
   const int bp = logP < 0 ? (blockIdx.x * STEP_THREADS + tx) * 2 : (tx & ((1 << logP) - 1)) * 2;
   const bool active = bp < Bp;
-  float scale[MAXIN];
+  float scale[M];
   int esum = 0;
-  int64_t rowb[MAXIN], eb0[MAXIN];
+  int64_t rowb[M], eb0[M];
   const uint64_t j0 = logP < 0 ? blockIdx.y : ((uint64_t)blockIdx.y << rpb_log) + (tx >> logP);
 #pragma unroll
-  for (int i = 0; i < MAXIN; ++i) {
+  for (int i = 0; i < M; ++i) {
     scale[i] = 1.f;
     rowb[i] = 0;
     eb0[i] = 0;
-    if (i < d.m) {
+    {
       const InDesc &in = d.in[i];
       int e;
       operand_scale(meta, in.meta, hdr, &scale[i], &e);
@@ -245,26 +246,20 @@ __global__ void __launch_bounds__(1024)
     if (it) {
       const int t = __ffsll((long long)it) - 1;
 #pragma unroll
-      for (int i = 0; i < MAXIN; ++i)
-        if (i < d.m) rowb[i] += rowtab[i][t];
+      for (int i = 0; i < M; ++i)
+        rowb[i] += rowtab[i][t];
     }
     float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
     const bool live = active && j < rows;
     if (live) {
-      int64_t eb[MAXIN];
+      int64_t eb[M];
 #pragma unroll
-      for (int i = 0; i < MAXIN; ++i) eb[i] = eb0[i];
-      for (int jt = 0; jt < tcount; ++jt) {
-        if (jt) {
-          const int t = __ffs(jt) - 1;
-#pragma unroll
-          for (int i = 0; i < MAXIN; ++i)
-            if (i < d.m) eb[i] += etab[i][t];
-        }
+      for (int i = 0; i < M; ++i) eb[i] = eb0[i];
+      if (tcount == 1) {
         float2 p0 = make_float2(1.f, 0.f), p1 = p0;
 #pragma unroll
-        for (int i = 0; i < MAXIN; ++i) {
-          if (i < d.m) {
+        for (int i = 0; i < M; ++i) {
+          {
             const char *a = ws + rowb[i] + eb[i];
             if (d.in[i].batched) {
               const float4 v = __ldg(reinterpret_cast<const float4 *>(a));
@@ -278,8 +273,46 @@ __global__ void __launch_bounds__(1024)
             }
           }
         }
-        a0.x += p0.x; a0.y += p0.y;
-        a1.x += p1.x; a1.y += p1.y;
+        a0 = p0;
+        a1 = p1;
+      } else {
+        // two terms per iteration (their loads in flight together): term jt
+        // at eb, term jt + 1 one carry into bit 0 away
+        for (int jt = 0; jt < tcount; jt += 2) {
+          float2 p0 = make_float2(1.f, 0.f), p1 = p0, q0 = p0, q1 = p0;
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            {
+              const char *a = ws + rowb[i] + eb[i];
+              const char *b = a + etab[i][0];
+              if (d.in[i].batched) {
+                const float4 v = __ldg(reinterpret_cast<const float4 *>(a));
+                const float4 w = __ldg(reinterpret_cast<const float4 *>(b));
+                p0 = cmul(p0, make_float2(v.x * scale[i], v.y * scale[i]));
+                p1 = cmul(p1, make_float2(v.z * scale[i], v.w * scale[i]));
+                q0 = cmul(q0, make_float2(w.x * scale[i], w.y * scale[i]));
+                q1 = cmul(q1, make_float2(w.z * scale[i], w.w * scale[i]));
+              } else {
+                const float2 v = __ldg(reinterpret_cast<const float2 *>(a));
+                const float2 w = __ldg(reinterpret_cast<const float2 *>(b));
+                const float2 sv = make_float2(v.x * scale[i], v.y * scale[i]);
+                const float2 sw = make_float2(w.x * scale[i], w.y * scale[i]);
+                p0 = cmul(p0, sv);
+                p1 = cmul(p1, sv);
+                q0 = cmul(q0, sw);
+                q1 = cmul(q1, sw);
+              }
+            }
+          }
+          a0.x += p0.x + q0.x; a0.y += p0.y + q0.y;
+          a1.x += p1.x + q1.x; a1.y += p1.y + q1.y;
+          if (jt + 2 < tcount) {
+            const int t = __ffs(jt + 2) - 1;
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+              eb[i] += etab[i][0] + etab[i][t];
+          }
+        }
       }
     }
     if (T > 1) {
@@ -829,16 +862,30 @@ __global__ void __launch_bounds__(256) k_split(char *ws, const __grid_constant__
     const int64_t kg = t % KG;
     const int64_t s = t / KG;
     float2 v[8];
-    if (rho < a.rows) {
+    const int klow = a.nk < 3 ? a.nk : 3;  // summed variables inside a group of 8
+    if (rho < a.rows && kg * 8 < ((int64_t)1 << a.nk)) {
       const int64_t m = a.fold ? rho / a.Bp : rho;
       const int64_t beta = a.fold ? rho % a.Bp : b;
       const int64_t base = a.src_off + (lin_bits((uint64_t)s, a.sX, a.ns) + lin_bits((uint64_t)m, a.rX, a.nr) +
                                         lin_bits((uint64_t)(kg * 8), a.kX, a.nk)) * u +
                            (a.batched ? beta * 8 : 0);
+      if (klow == 3) {
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const float2 x = __ldg(reinterpret_cast<const float2 *>(ws + base + lin_bits((uint64_t)q, a.kX, 3) * u));
-        v[q] = make_float2(x.x * sc, x.y * sc);
+        for (int q = 0; q < 8; ++q) {
+          const float2 x = __ldg(reinterpret_cast<const float2 *>(ws + base + lin_bits((uint64_t)q, a.kX, 3) * u));
+          v[q] = make_float2(x.x * sc, x.y * sc);
+        }
+      } else {
+        // fewer than 8 summed entries: the rest of the group is zero padding
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (q < (1 << klow)) {
+            const float2 x = __ldg(reinterpret_cast<const float2 *>(ws + base + lin_bits((uint64_t)q, a.kX, klow) * u));
+            v[q] = make_float2(x.x * sc, x.y * sc);
+          } else {
+            v[q] = make_float2(0.f, 0.f);
+          }
+        }
       }
     } else {
 #pragma unroll
@@ -1645,16 +1692,16 @@ static cudaError_t tc_set_smem() {
 
 static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const GemmDesc *gemms, Meta *meta,
                            Header *hdr, cudaStream_t st, bool tc = false, int64_t planes_off = 0,
-                           int planes = 4, cudaEvent_t mid = nullptr) {
+                           int planes = 4, cudaEvent_t mid = nullptr, const StepTune *tn = nullptr) {
   const uint64_t rows = 1ull << d.w_out;
   if (d.gemm >= 0 && gemms && tc) {
-    const TcCfg c = tc_config(gemms[d.gemm], Bp, planes);
+    const TcCfg c = tc_config(gemms[d.gemm], Bp, planes, tn && tn->nt_cap ? tn->nt_cap : 256);
     if (c.ok) {
       launch_gemm_tc(ws, sms, Bp, gemms[d.gemm], c, planes_off, planes, meta, hdr, st, mid);
       return;
     }
   }
-  if (d.gemm >= 0 && gemms) {
+  if (d.gemm >= 0 && gemms && gemm_fp32_ok(gemms[d.gemm])) {
     const GemmDesc &g = gemms[d.gemm];
     const dim3 grid(1u << ((g.nm - 6) + (g.nn - (g.nn >= 6 ? 6 : 5))), g.o_bat ? Bp : 1, 1u << g.ns);
     if (g.nn >= 6) {
@@ -1684,9 +1731,10 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
     const uint64_t cap = (uint64_t)std::max(1, sms * 16 / bx);
     // split the summed terms over threadIdx.y while the grid is small
     int T = 1;
-    while (T < 8 && (T * 2) <= (1 << std::min(d.k, 4)) &&
+    while (T < 4 && (T * 2) <= (1 << std::min(d.k, 4)) &&
            row_blocks * (uint64_t)bx * STEP_THREADS * T < (uint64_t)sms * 1024)
       T *= 2;
+    if (tn && tn->T > 0 && tn->T <= 4 && tn->T <= (1 << std::min(d.k, 4))) T = tn->T;
     if (d.tile_t > 0) {
       // rows are counted over the output bits outside the tile
       const uint64_t orows = rows >> d.tile_t;
@@ -1696,17 +1744,113 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
       return;
     }
     const uint64_t gy = pow2_floor(std::min<uint64_t>(row_blocks, std::min<uint64_t>(cap, 32768)));
-    k_step_batched<<<dim3(bx, (unsigned)gy), dim3(STEP_THREADS, T), 0, st>>>(ws, d, meta, hdr, Bp, logP);
+    const dim3 g2(bx, (unsigned)gy), b2(STEP_THREADS, T);
+    switch (d.m) {
+      case 1: k_step_batched<1><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      case 2: k_step_batched<2><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      case 3: k_step_batched<3><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      case 4: k_step_batched<4><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      case 5: k_step_batched<5><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      case 6: k_step_batched<6><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      case 7: k_step_batched<7><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      default: k_step_batched<8><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+    }
   } else {
     const uint64_t blocks = pow2_floor(std::max<uint64_t>(1, std::min<uint64_t>((rows + 255) / 256, (uint64_t)sms * 8)));
     k_step_plain<<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr);
   }
 }
 
+// The autotuner's parameters of a forward step (none for the adjoint steps).
+static const StepTune *tune_of(const qgm_plan *p, const StepDesc &d) {
+  if (p->steps.empty() || &d < p->steps.data() || &d >= p->steps.data() + p->steps.size()) return nullptr;
+  const size_t i = (size_t)(&d - p->steps.data());
+  return i < p->tune.size() ? &p->tune[i] : nullptr;
+}
+
 static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st, cudaEvent_t mid = nullptr) {
   char *ws = p->exec->ws;
   launch_step_ws(ws, p->exec->sms, p->Bp, d, p->gemms.data(), reinterpret_cast<Meta *>(ws + p->off_meta),
-                 reinterpret_cast<Header *>(ws + p->off_header), st, p->gemm_tc, p->off_planes, p->tc_planes, mid);
+                 reinterpret_cast<Header *>(ws + p->off_header), st, p->gemm_tc, p->off_planes, p->tc_planes, mid,
+                 tune_of(p, d));
+}
+
+// Autotuner (qgm_plan_opts.autotune): one pass over an all-zero batch puts
+// real tensors in the workspace; then, step by step in order, every
+// candidate launch configuration of a step with several is run once to
+// warm up and three times under CUDA events, and the fastest is kept (the
+// candidates compute the same products; only a term split changes the
+// order of a sum).  Steps whose fixed-rule launch takes under 0.05 ms are
+// left alone.  Ends with the status word cleared.
+static int autotune(qgm_plan *p, cudaStream_t st) {
+  qgm_exec_state *x = p->exec;
+  uint64_t *d_bits = reinterpret_cast<uint64_t *>(x->ws + p->off_bits);
+  CK(cudaMemsetAsync(d_bits, 0, (size_t)p->Bp * 8, st));
+  launch_leaves(p, d_bits, p->batch, st);
+  for (const StepDesc &d : p->steps) launch_step(p, d, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  auto time_step = [&](const StepDesc &d, float *ms) -> int {
+    launch_step(p, d, st);
+    CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < 3; ++r) launch_step(p, d, st);
+    CK(cudaEventRecord(e1, st));
+    CK(cudaGetLastError());
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    *ms /= 3.f;
+    return QGM_OK;
+  };
+  for (size_t si = 0; si < p->steps.size(); ++si) {
+    const StepDesc &d = p->steps[si];
+    StepTune &tn = p->tune[si];
+    std::vector<StepTune> cand;
+    if (d.gemm >= 0 && p->gemm_tc && tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes).ok) {
+      const int wide = tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes).nt;
+      for (int cap : {256, 128, 64})
+        if (cap <= wide) {
+          StepTune t;
+          t.nt_cap = cap;
+          cand.push_back(t);
+        }
+    } else if (d.gemm < 0 && d.batched_out && d.tile_t == 0) {
+      for (int T : {1, 2, 4})
+        if (T <= (1 << std::min(d.k, 4))) {
+          StepTune t;
+          t.T = T;
+          cand.push_back(t);
+        }
+    }
+    if (cand.size() < 2) continue;
+    float ms_rule = 0.f;
+    tn = StepTune{};
+    int rc = time_step(d, &ms_rule);
+    if (rc) return rc;
+    if (ms_rule < 0.05f) continue;
+    StepTune best{};
+    float best_ms = ms_rule;
+    for (const StepTune &c : cand) {
+      tn = c;
+      float ms = 0.f;
+      rc = time_step(d, &ms);
+      if (rc) return rc;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    tn = best;
+    tn.ms_rule = ms_rule;
+    tn.ms_best = best_ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CK(cudaMemsetAsync(x->ws + p->off_header, 0, sizeof(int32_t), st));
+  CK(cudaStreamSynchronize(st));
+  return QGM_OK;
 }
 
 static void launch_accumulate(qgm_plan *p, double2 *d_out, int64_t n_out, cudaStream_t st) {
@@ -1879,11 +2023,13 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
   // chunk size by fewest waves x chunk
   x->kind = QGM_EXEC_STEPWISE;
   x->layout = -1;
+  for (StepTune &t : p->tune) t = StepTune{};
   if (p->executor_pref == QGM_EXEC_STEPWISE || p->resident.empty()) {
     if (p->executor_pref == QGM_EXEC_RESIDENT || p->executor_pref == QGM_EXEC_COMPILED) {
       set_error("qgm_plan_bind: this plan has no resident layout (one slice, batch outputs only)");
       return QGM_ERR_ARG;
     }
+    if (p->opts.autotune && p->output_mode == QGM_OUT_BATCH) return autotune(p, st);
     return QGM_OK;
   }
   int optin = 0, sm_smem = 0, reserved = 0;
@@ -2004,6 +2150,7 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
     set_error("qgm_plan_bind: no resident layout fits this device's shared memory");
     return QGM_ERR_ARG;
   }
+  if (x->kind == QGM_EXEC_STEPWISE && p->opts.autotune && p->output_mode == QGM_OUT_BATCH) return autotune(p, st);
   return QGM_OK;
 }
 
@@ -2176,6 +2323,25 @@ int qgm_plan_profile_gemm(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, 
     CK(cudaEventElapsedTime(&ms_product[c], ev[3 * c + 1], ev[3 * c + 2]));
   }
   for (auto &x : ev) cudaEventDestroy(x);
+  return QGM_OK;
+}
+
+int qgm_plan_step_stats(qgm_plan *p, uint32_t *maxbits, int32_t *exps, int64_t cap, void *stream) {
+  int rc = check_bound(p, "qgm_plan_step_stats");
+  if (rc) return rc;
+  if (!maxbits || !exps) {
+    set_error("qgm_plan_step_stats: null argument");
+    return QGM_ERR_ARG;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<Meta> m((size_t)std::max(p->n_meta, 1));
+  CK(cudaMemcpyAsync(m.data(), p->exec->ws + p->off_meta, (size_t)p->n_meta * sizeof(Meta), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  for (int64_t s = 0; s < std::min<int64_t>(cap, (int64_t)p->steps.size()); ++s) {
+    const int slot = p->steps[s].out_meta;
+    maxbits[s] = slot >= 0 && slot < p->n_meta ? m[slot].maxbits : 0u;
+    exps[s] = slot >= 0 && slot < p->n_meta ? m[slot].exp : 0;
+  }
   return QGM_OK;
 }
 

@@ -566,7 +566,7 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
   auto contract = [&](std::vector<int> inputs, const std::vector<int> &summed) -> int {
     shrink(inputs);
     const int k = (int)summed.size();
-    if (p->gemm_ok && k >= 4 && inputs.size() >= 2) {
+    if (p->gemm_ok && k >= (p->gemm_tc ? 2 : 4) && inputs.size() >= 2) {
       std::vector<int> by = inputs;
       std::stable_sort(by.begin(), by.end(), [&](int a, int b) { return T[a].vars.size() > T[b].vars.size(); });
       const int A = by[0], Bt = by[1];
@@ -601,14 +601,32 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       // the shared kept variables index independent products (a grid
       // dimension of the launch): at most 15 of them
       if (ns > 15) ok = false;
-      // tiles of 64 x 64 or, with a wide batch (many GEMMs per launch), 64 x
-      // 32 outputs: the operand with six or more private kept variables
-      // goes first
+      // FP32-core kernel: tiles of 64 x 64 or, with a wide batch (many GEMMs
+      // per launch), 64 x 32 outputs, the operand with six or more private
+      // kept variables first, 16 summed entries per chunk
       const int min_side = Bp >= 64 ? 5 : 6;
-      if (ok && std::max(nm, nn) >= 6 && std::min(nm, nn) >= min_side && nm < GMAXB && nn < GMAXB) {
+      const bool fp32_ok = k >= 4 && std::max(nm, nn) >= 6 && std::min(nm, nn) >= min_side;
+      // tensor cores: whenever the step's tensor-core form exists (fewer than
+      // 16 summed entries are padded with zeros to one chunk, worth it only
+      // for large outputs)
+      bool tc_ok = false;
+      if (ok && p->gemm_tc && !fp32_ok) {
+        GemmDesc tg{};
+        tg.nm = nm;
+        tg.nn = nn;
+        tg.nk = k;
+        tg.ns = ns;
+        for (int id : toA) tg.a_bat |= T[id].batched ? 1 : 0;
+        for (int id : toB) tg.b_bat |= T[id].batched ? 1 : 0;
+        tg.o_bat = tg.a_bat | tg.b_bat;
+        const double out_entries = std::ldexp(tg.o_bat ? (double)Bp : 1.0, nm + nn + ns);
+        tc_ok = tc_config(tg, (int)Bp, 4).ok && (k >= 4 || out_entries >= 1048576.0);
+      }
+      if (ok && (fp32_ok || tc_ok) && nm < GMAXB && nn < GMAXB) {
         auto premul = [&](std::vector<int> &grp) { return grp.size() == 1 ? grp[0] : hold(emit(grp, {})); };
         const int a2 = premul(toA), b2 = premul(toB);
-        return nm >= 6 ? emit({a2, b2}, summed, true) : emit({b2, a2}, summed, true);
+        const bool a_first = fp32_ok ? nm >= 6 : nm >= nn;
+        return a_first ? emit({a2, b2}, summed, true) : emit({b2, a2}, summed, true);
       }
     }
     if (nest && inputs.size() >= 3 && k >= 2) {
@@ -725,6 +743,10 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       bat[t] = bat[t & (t - 1)] | (T[inputs[i]].batched ? 1 : 0);
     }
     for (int t = 1; t <= full; ++t) res[t] = all[t] & ~(smask & ~all[full ^ t]);
+    // variables of a child as its parent sees them: a node's result, but an
+    // input itself (nothing is summed inside a single input)
+    std::vector<uint64_t> cv(full + 1, 0);
+    for (int t = 1; t <= full; ++t) cv[t] = (t & (t - 1)) ? res[t] : all[t];
     const int limit = std::max(widest, __builtin_popcountll(res[full])) + 1;
     auto ent = [&](uint64_t mask, bool b) { return std::ldexp(b ? (double)Bp : 1.0, __builtin_popcountll(mask)); };
     const double step_over = 256.0;
@@ -739,7 +761,7 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       for (int sub = (rest - 1) & rest;; sub = (sub - 1) & rest) {
         const int t1 = low | sub, t2 = t ^ t1;
         if (best[t1] < 1e299 && best[t2] < 1e299) {
-          const double c = best[t1] + best[t2] + ent(res[t1] | res[t2], bat[t]) + ent(res[t], bat[t]) + step_over;
+          const double c = best[t1] + best[t2] + ent(cv[t1] | cv[t2], bat[t]) + ent(res[t], bat[t]) + step_over;
           if (c < best[t]) {
             best[t] = c;
             split_of[t] = t1;
@@ -760,14 +782,14 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       if (!(t & (t - 1))) return inputs[__builtin_ctz(t)];
       // flatten children whose contraction is better done inside this node
       std::vector<int> kids = {split_of[t], t ^ split_of[t]};
-      const uint64_t u = res[split_of[t]] | res[t ^ split_of[t]];
+      const uint64_t u = cv[split_of[t]] | cv[t ^ split_of[t]];
       bool changed = true;
       while (changed) {
         changed = false;
         for (size_t q = 0; q < kids.size(); ++q) {
           const int c = kids[q];
           if (!(c & (c - 1))) continue;
-          const uint64_t uc = res[split_of[c]] | res[c ^ split_of[c]];
+          const uint64_t uc = cv[split_of[c]] | cv[c ^ split_of[c]];
           if (uc & ~u) continue;
           const double sep = ent(uc, bat[c]) + ent(res[c], bat[c]) + step_over;
           if (ent(u, bat[t]) <= sep) {
@@ -785,7 +807,7 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
       }
       std::vector<int> sm;
       uint64_t gone = 0;
-      for (int c : kids) gone |= res[c];
+      for (int c : kids) gone |= cv[c];
       gone &= ~res[t];
       for (int b = 0; b < U; ++b)
         if ((gone >> b) & 1) sm.push_back(uni[b]);
@@ -846,6 +868,18 @@ static SimResult simulate(const qgm_plan *p, const std::vector<int> &order_in,
   }
   R.final_tensors = finals;
   R.arena_peak = arena.peak;
+  if (want_steps) {
+    // bucket elimination is a tree: every tensor but the final one feeds
+    // exactly one step
+    std::vector<int> uses(T.size(), 0);
+    for (const StepRec &st : R.steps)
+      for (int id : st.inputs) uses[id]++;
+    for (size_t id = 0; id < T.size(); ++id)
+      if ((int)id != R.final_tensor && uses[id] != 1) {
+        R.tree_error = (int)id;
+        break;
+      }
+  }
   return R;
 }
 
@@ -1360,6 +1394,10 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   }
   p->sim = simulate(p, p->order, sliced, max_fuse, true);
   SimResult &S = p->sim;
+  if (S.tree_error >= 0) {
+    set_error("internal: tensor %d of the elimination is consumed other than once", S.tree_error);
+    return QGM_ERR_ARG;
+  }
   // induced width along the order on the graph without the sliced variables
   {
     std::vector<char> ig = in_graph;
@@ -1620,6 +1658,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     }
     p->steps.push_back(d);
   }
+  p->tune.assign(p->steps.size(), StepTune{});
   // the split operand planes of the largest tensor-core step, after the arena
   p->ws_fwd_bytes = p->ws_bytes;
   p->planes_bytes = 0;
@@ -2050,7 +2089,19 @@ int qgm_plan_order(const qgm_model *m, const qgm_plan_opts *opts, qgm_plan **out
     qgm_plan_opts o2 = *opts;
     o2.trees = 1;
     qgm_plan *t = new qgm_plan;
-    if (build_plan(m->m, o2, t) == QGM_OK && t->sim.flops < 0.9 * p->sim.flops &&
+    // work weighted by where it runs: products of a tensor-core GEMM step
+    // count 1/16 (split FP16 runs them more than an order of magnitude
+    // faster than the FP32 product-sum kernels)
+    auto weighted = [](const qgm_plan *q) {
+      double w = 0;
+      for (size_t si = 0; si < q->steps.size() && si < q->sim.steps.size(); ++si) {
+        const StepDesc &d = q->steps[si];
+        const bool tc = d.gemm >= 0 && q->gemm_tc && gemm_tc_eligible(q->gemms[d.gemm], q->Bp);
+        w += q->sim.steps[si].flops * (tc ? 1.0 / 16.0 : 1.0);
+      }
+      return w;
+    };
+    if (build_plan(m->m, o2, t) == QGM_OK && weighted(t) < 0.9 * weighted(p) &&
         t->ws_bytes <= std::max<int64_t>(2 * p->ws_bytes, p->ws_bytes + ((int64_t)4 << 30))) {
       delete p;
       p = t;
@@ -2137,6 +2188,56 @@ int qgm_plan_get_step_kernels(const qgm_plan *p, int32_t *kind, int64_t cap) {
     const StepDesc &d = p->steps[s];
     kind[s] = d.gemm >= 0 ? 3 : (d.tile_t > 0 ? 2 : (d.batched_out ? 1 : 0));
   }
+  return QGM_OK;
+}
+
+int qgm_plan_get_step_inputs(const qgm_plan *p, int32_t step, int32_t *rec, int64_t cap, int64_t *n) {
+  if (!p || !n || step < 0 || step >= (int32_t)p->sim.steps.size()) {
+    set_error("qgm_plan_get_step_inputs: bad arguments");
+    return QGM_ERR_ARG;
+  }
+  const StepRec &s = p->sim.steps[step];
+  std::vector<int32_t> out;
+  out.push_back((int32_t)s.uni.size());
+  out.push_back(s.k);
+  out.push_back((int32_t)s.inputs.size());
+  for (int id : s.inputs) {
+    const SymTensor &t = p->sim.tensors[id];
+    out.push_back((int32_t)t.vars.size());
+    out.push_back(t.batched ? 1 : 0);
+    for (int v : t.vars)
+      out.push_back((int32_t)(std::find(s.uni.begin(), s.uni.end(), v) - s.uni.begin()));
+  }
+  *n = (int64_t)out.size();
+  if (rec)
+    for (int64_t i = 0; i < std::min<int64_t>(cap, *n); ++i) rec[i] = out[i];
+  return QGM_OK;
+}
+
+int qgm_plan_get_tuning(const qgm_plan *p, int32_t *rec, float *ms, int64_t cap, int64_t *n) {
+  if (!p || !n) {
+    set_error("qgm_plan_get_tuning: null argument");
+    return QGM_ERR_ARG;
+  }
+  int64_t c = 0;
+  for (size_t s = 0; s < p->tune.size(); ++s) {
+    const StepTune &t = p->tune[s];
+    if (t.ms_rule <= 0.f) continue;
+    if (c < cap) {
+      if (rec) {
+        rec[4 * c] = (int32_t)s;
+        rec[4 * c + 1] = t.nt_cap;
+        rec[4 * c + 2] = t.T;
+        rec[4 * c + 3] = 0;
+      }
+      if (ms) {
+        ms[2 * c] = t.ms_rule;
+        ms[2 * c + 1] = t.ms_best;
+      }
+    }
+    ++c;
+  }
+  *n = c;
   return QGM_OK;
 }
 

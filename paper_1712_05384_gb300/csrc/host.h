@@ -134,7 +134,7 @@ struct TcCfg {
 
 // planes: 16-bit terms per complex value (4: FP16 high and low parts of the
 // real and imaginary parts; 6: three BF16 terms of each)
-inline TcCfg tc_config(const GemmDesc &g, int Bp, int planes) {
+inline TcCfg tc_config(const GemmDesc &g, int Bp, int planes, int nt_cap = 256) {
   TcCfg c;
   const bool one = g.o_bat && (g.a_bat != g.b_bat);
   c.swap = one ? (g.b_bat != 0) : (g.nn > g.nm);
@@ -142,13 +142,14 @@ inline TcCfg tc_config(const GemmDesc &g, int Bp, int planes) {
   c.perbeta = g.o_bat && g.a_bat && g.b_bat && Bp > 1;
   c.nM = c.swap ? g.nn : g.nm;
   c.nN = c.swap ? g.nm : g.nn;
-  if (g.nk < 4 || c.nN < 5 || g.ns > 15 || c.nM > 30) return c;
+  if (g.nk < 1 || c.nN < 5 || g.ns > 15 || c.nM > 30) return c;
   c.mrows = ((int64_t)1 << c.nM) * (c.fold ? Bp : 1);
   if (c.mrows < TC_M) return c;
   c.mtiles = (c.mrows + TC_M - 1) / TC_M;
   c.nt = c.nN >= 8 ? 256 : (1 << c.nN);
+  if (c.nt > nt_cap && nt_cap >= 32) c.nt = nt_cap;  // narrower N tiles: two CTAs per SM
   c.ntiles = ((int64_t)1 << c.nN) / c.nt;
-  c.kc = ((int64_t)1 << g.nk) / 16;
+  c.kc = (((int64_t)1 << g.nk) + 15) / 16;  // fewer than 16 summed entries: one chunk, zero-padded
   c.inst = ((int64_t)1 << g.ns) * (c.perbeta ? Bp : 1);
   if (c.inst * c.mtiles * c.ntiles >= ((int64_t)1 << 31)) return c;
   c.bytesM = c.inst * c.mtiles * c.kc * planes * TC_M * 32;
@@ -157,11 +158,26 @@ inline TcCfg tc_config(const GemmDesc &g, int Bp, int planes) {
   return c;
 }
 
+// Launch parameters of one step chosen by the autotuner (qgm_plan_opts.autotune)
+// by timing its candidates on the bound device; zeros are the fixed rules.
+struct StepTune {
+  int32_t nt_cap = 0;     // tensor-core GEMM: N tile at most 256, 128 or 64 (0: 256)
+  int32_t T = 0;          // batched product-sum: term groups per row (0: rule)
+  float ms_rule = 0.f;    // measured time with the fixed rules (ms)
+  float ms_best = 0.f;    // measured time of the chosen candidate (ms)
+};
+
 // A GEMM step runs on the tensor cores when its tensor-core form exists: the
 // M side has at least 128 rows (batch entries counted when they become
-// rows), the N side at least 32 and the summed entries come in whole chunks
-// of 16 (one MMA's K).
+// rows), the N side at least 32 (summed entries are zero-padded to whole
+// chunks of 16, one MMA's K).
 inline bool gemm_tc_eligible(const GemmDesc &g, int Bp) { return tc_config(g, Bp, 4).ok; }
+
+// The FP32-core GEMM kernel's shapes: 64-row A tiles, 32- or 64-column B
+// tiles, chunks of 16 summed entries.  Other GEMM steps (accepted for the
+// tensor cores) run with the product-sum kernels where the tensor cores are
+// not used.
+inline bool gemm_fp32_ok(const GemmDesc &g) { return g.nk >= 4 && g.nm >= 6 && g.nn >= 5; }
 
 // Leaf factor built on the device per slice: base table over
 // (internal vars | slice vars | output vars), MSB first.
@@ -321,6 +337,7 @@ struct SimResult {
   std::vector<StepRec> steps;
   std::vector<int> final_tensors;
   int final_tensor = -1;
+  int tree_error = -1;  // a tensor consumed other than once (plan invariant broken)
 };
 
 }  // namespace qgm
@@ -385,6 +402,7 @@ struct qgm_plan {
   int64_t off_planes = 0;   // workspace region of the split operand planes
   int64_t planes_bytes = 0; // its size (the largest tensor-core step's two operands)
   int64_t ws_fwd_bytes = 0; // workspace the forward pass needs without that region
+  std::vector<qgm::StepTune> tune;  // per step of `steps` (autotuner choices)
   bool trees_ok = false;    // buckets of three or more inputs may run as contraction trees
   bool nest_ok = true;      // buckets may be marked for nested evaluation
   qgm_exec_state *exec = nullptr;

@@ -443,7 +443,7 @@ def test_narrow_gemm_tiles_with_wide_batch():
     bits = qi.bitstrings(c.n, 64, 0)
     m = q.Model(q.Circuit.grid(4, 6, 30, 0))
     p = q.Plan(m, batch=64, trees=True, executor=1, split_bf16=False)
-    assert p.info.n_gemm_steps > q.Plan(m, batch=8, trees=True, executor=1).info.n_gemm_steps
+    assert p.info.n_gemm_steps > q.Plan(m, batch=8, trees=True, executor=1, precision="fp32").info.n_gemm_steps
     assert p.info.n_gemm_tc_steps == 0
     a = p.bind().amplitudes_host(bits)
     b = q.Plan(m, batch=64, trees=True, executor=1, gemm=False).bind().amplitudes_host(bits)

@@ -43,13 +43,14 @@ def errors(a, ref, n):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-@pytest.mark.parametrize("rows,cols,depth,B,n_tc", [(4, 5, 30, 16, 1), (4, 6, 34, 6, 2)])
+@pytest.mark.parametrize("rows,cols,depth,B,n_tc", [(4, 5, 30, 16, 1), (4, 6, 34, 6, 4)])
 def test_split_gemm_vs_state_vector(rows, cols, depth, B, n_tc, precision):
     # 4x5 d30: one GEMM step, both operands batched (one product per batch
-    # entry), 128 x 64 tiles; 4x6 d34: two of three GEMM steps on the tensor
-    # cores, each with one batch-free operand (the batch entries become rows
-    # of the other; one with the roles exchanged), the third (2^6 rows on
-    # both sides, both batched) left to the FP32 kernel
+    # entry), 128 x 64 tiles; 4x6 d34: four of five GEMM steps on the tensor
+    # cores -- two with one batch-free operand (the batch entries become rows
+    # of the other; one with the roles exchanged), two with 4 summed entries
+    # (zero-padded to one chunk of 16), one without a batch axis -- and the
+    # fifth (2^6 rows on both sides, both batched) left to the FP32 kernel
     q = Q()
     c = qi.grid_circuit(rows, cols, depth, 0)
     bits = qi.bitstrings(c.n, B, 0)
@@ -65,16 +66,16 @@ def test_split_gemm_vs_state_vector(rows, cols, depth, B, n_tc, precision):
 
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_split_matches_fp32_gemm_4x8_d40(precision):
-    # 4x8 depth 40, 4 bitstrings: three GEMM steps (one folded with roles
-    # exchanged, one folded, one per entry) with 2^8 summed entries (16
-    # chunks); no oracle runs 32 qubits at depth 40 in a test, so the
+    # 4x8 depth 40, 4 bitstrings: four GEMM steps (one folded with roles
+    # exchanged, one folded, two per entry, one of those with 4 summed
+    # entries); no oracle runs 32 qubits at depth 40 in a test, so the
     # FP32-core GEMM plan is the comparison (it is checked against the oracle
     # at smaller sizes)
     q = Q()
     m = q.Model(q.Circuit.grid(4, 8, 40, 0))
     bits = qi.bitstrings(32, 4, 0)
     pt = q.Plan(m, order_kind=1, batch=4, precision=precision)
-    assert pt.info.n_gemm_tc_steps == pt.info.n_gemm_steps == 3
+    assert pt.info.n_gemm_tc_steps == pt.info.n_gemm_steps == 4
     a = pt.bind().amplitudes_host(bits)
     assert pt.status() == 0
     b = q.Plan(m, order_kind=1, batch=4, precision="fp32").bind().amplitudes_host(bits)

@@ -170,20 +170,26 @@ def test_contraction_trees_need_fewer_products():
     assert st["k"].sum() == tree.info.n_free
 
 
-@pytest.mark.parametrize("rows,cols,depth,B,n_gemm,n_tc", [(4, 5, 30, 16, 1, 1), (4, 6, 34, 6, 3, 2),
-                                                         (4, 8, 40, 4, 3, 3)])
-def test_tensor_core_gemm_steps(rows, cols, depth, B, n_gemm, n_tc):
-    # GEMM steps (min-fill) and their (m, n, k) variable counts:
-    # 4x5 d30 (7, 6, 6); 4x6 d34 (8, 6, 8), (9, 6, 4), (6, 6, 8); 4x8 d40
-    # (8, 8, 8), (11, 7, 8), (11, 9, 8).  A step goes to the tensor cores when
-    # one side has >= 7 variables (the MMA's 128 rows), the other >= 5 and
-    # k >= 4 (16 summed entries per MMA): all but (6, 6, 8)
+@pytest.mark.parametrize("rows,cols,depth,B,n_gemm,n_tc,n_fp32", [(4, 5, 30, 16, 1, 1, 1), (4, 6, 34, 6, 5, 4, 3),
+                                                                (4, 8, 40, 4, 4, 4, 3)])
+def test_tensor_core_gemm_steps(rows, cols, depth, B, n_gemm, n_tc, n_fp32):
+    # GEMM steps (min-fill) and their (m, n, k, s) variable counts with both
+    # operands' batch flags.  For the FP32-core kernel a step needs >= 6
+    # private variables on one side, >= 6 (>= 5 with 64 or more batch
+    # entries) on the other and k >= 4: 4x6 d34 has (8, 6, 8), (9, 6, 4),
+    # (6, 6, 8); 4x8 d40 (8, 8, 8), (11, 7, 8), (11, 9, 8).  On the tensor
+    # cores a step needs an M side of >= 128 rows (batch entries count as
+    # rows when the other operand has no batch axis: 4x6 d34's batch of 6
+    # pads to 8), an N side of >= 32 and, below 16 summed entries, an output
+    # of >= 2^20 entries (the chunk is zero-padded): 4x6 d34 gains (7, 7, 2)
+    # and (11, 5, 2) and loses (6, 6, 8) (2^6 rows, both batched); 4x8 d40
+    # gains (10, 9, 2)
     m = Q.Model(Q.Circuit.grid(rows, cols, depth, 0))
     p = Q.Plan(m, order_kind=1, batch=B)
     assert (p.info.n_gemm_steps, p.info.n_gemm_tc_steps) == (n_gemm, n_tc)
-    assert Q.Plan(m, order_kind=1, batch=B, split_bf16=True).info.n_gemm_tc_steps == n_tc
-    off = Q.Plan(m, order_kind=1, batch=B, split_bf16=False)
-    assert (off.info.n_gemm_steps, off.info.n_gemm_tc_steps) == (n_gemm, 0)
+    assert Q.Plan(m, order_kind=1, batch=B, precision="bf16").info.n_gemm_tc_steps == n_tc
+    off = Q.Plan(m, order_kind=1, batch=B, precision="fp32")
+    assert (off.info.n_gemm_steps, off.info.n_gemm_tc_steps) == (n_fp32, 0)
     assert Q.Plan(m, order_kind=1, batch=B, gemm=False).info.n_gemm_tc_steps == 0
 
 
@@ -282,5 +288,24 @@ def test_gemm_shapes_fit_the_launch(rows, cols, depth, batch):
     for g in gs:
         assert kinds[g["step"]] == 3
         assert g["ns"] <= 15 and max(g["nm"], g["nn"], g["nk"]) < 24
-        assert g["nk"] >= 4 and min(g["nm"], g["nn"]) >= 5
+        if g["tc"]:
+            assert g["nk"] >= 2 and min(g["nm"], g["nn"]) >= 5
+        else:
+            assert g["nk"] >= 4 and max(g["nm"], g["nn"]) >= 6 and min(g["nm"], g["nn"]) >= 5
     assert sum(g["tc"] for g in gs) == p.info.n_gemm_tc_steps
+
+
+@pytest.mark.parametrize("rows,cols,depth,batch,kw", [(5, 9, 40, 4, {"gemm": False, "trees": True}),
+                                                     (5, 9, 40, 4, {"trees": True}), (4, 8, 40, 4, {"trees": True}),
+                                                     (6, 6, 25, 1000, {"trees": True}), (5, 5, 20, 64, {"trees": True})])
+def test_contraction_trees_keep_every_tensor(rows, cols, depth, batch, kw):
+    # App. A bucket elimination is a tree: every intermediate feeds exactly
+    # one step (the planner refuses a plan that breaks this).  A bucket's
+    # contraction tree must sum a variable held by a single input at that
+    # input's parent: 5x9 depth 40 with trees has such buckets; each summed
+    # variable must disappear exactly once (sum of k = eliminated variables)
+    m = Q.Model(Q.Circuit.grid(rows, cols, depth, 0))
+    p = Q.Plan(m, order_kind=1, batch=batch, executor=Q.EXEC_STEPWISE, **kw)
+    st = p.steps()
+    assert st["k"].sum() == p.info.n_free
+    assert st["out_rank"][-1] == 0
