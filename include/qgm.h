@@ -407,13 +407,27 @@ int qgm_sample_from_set(const double *d_amps, int64_t t, int64_t m, uint64_t see
  * (synchronises `stream`): QGM_OK, QGM_ERR_NONFINITE or QGM_ERR_TIMEOUT. */
 int qgm_status(qgm_plan *p, void *stream);
 
+/* New angles for the parametrised gates of the plan's circuit (RXY, Sec.
+ * "Numerical results" gate set extended by exp(-i theta (cos phi X + sin
+ * phi Y) / 2)): params[2p] = theta_p, params[2p+1] = phi_p in the order of
+ * qgm_circuit_param_gates, n = 2 * number of RXY gates.  The gate tables, the
+ * merged leaf tables (and their derivative tables) and the constant are
+ * recomputed on the host and, when a workspace is bound, copied into it on
+ * `stream` (synchronised); the order, steps and layout are unchanged, so no
+ * re-planning happens.  Later qgm_amplitudes / qgm_amplitude_grad calls use
+ * the new angles.  Errors: QGM_ERR_ARG (count, structure), QGM_ERR_CUDA. */
+int qgm_plan_set_params(qgm_plan *p, const double *params, int64_t n, void *stream);
+
 /* Gradient (adjoint elimination) for a parametrised circuit.  The forward
  * elimination keeps every intermediate; the backward pass runs the steps in
  * reverse, each step of Eq. par_sum giving the adjoint of each input as the
  * product of the output's adjoint with the other inputs, summed over the
  * variables the input does not hold (bucket elimination is a tree, so every
- * tensor has exactly one consumer).  Needs a plan made with opts.gradients = 1
- * and one slice.  Given
+ * tensor has exactly one consumer).  Needs a plan made with opts.gradients = 1.
+ * A sliced plan (opts.mem_budget_bytes) recomputes, slice by slice, the
+ * forward intermediates of that slice before its adjoint pass and adds each
+ * slice's share of the gradient (a = sum_s a_s), so the live set stays that
+ * of one slice.  Given
  * g_b = dL/d(conj a_b) for the B bitstrings (device double[2B]), writes
  * d_grad[i] = dL/dp_i = 2 Re sum_b conj(g_b) da_b/dp_i for the n_params
  * parameters (theta, phi of each RXY gate, see qgm_circuit_param_gates) into

@@ -10,8 +10,12 @@ per assignment (distributivity).  The model and its factor tables come from
 It exists for the circuits the numpy elimination cannot hold (5x9 depth 40):
 each bucket's product-sum is a loop over its output entries, so only tensors
 of the order's cliques are ever stored.
+``amplitude_derivative(c, x, p, which)``: d<x|C|0>/d(theta_p or phi_p) by
+derivative insertion (the circuit is linear in each gate: the amplitude with
+gate p's table replaced by the derivative of its matrix).
 Parity: pinned (App. D 1/2; the state vector on small grids; the numpy
-elimination; tests/test_oracle_vec.py).
+elimination; derivative insertion against the state-vector oracle's;
+tests/test_oracle_vec.py).
 """
 from __future__ import annotations
 
@@ -21,6 +25,7 @@ import subprocess
 
 import numpy as np
 
+from . import gates as G
 from . import order as O
 from . import ugm
 
@@ -108,3 +113,22 @@ def amplitude(circuit, x, order=None, slice_vars=(), model=None, prepared=None, 
             raise RuntimeError("ve_amplitude: a free variable is missing from the order")
         total += complex(out[0], out[1])
     return total
+
+
+def amplitude_derivative(circuit, x, p, which, order=None, model=None, prepared=None, threads=0) -> complex:
+    """d<x|C|0>/d theta_p (which = 0) or d phi_p (which = 1) for the p-th
+    parametrised gate (circuit.param_gates order): the elimination with that
+    gate's factor table replaced by its derivative matrix."""
+    m = model or ugm.build(circuit)
+    pr = prepared or Prepared(m)
+    gi = circuit.param_gates[p]
+    fi = next(i for i, f in enumerate(m.factors) if f.gate == gi)
+    g = circuit.gates[gi]
+    dM = np.asarray(G.drot(g.theta, g.phi)[which], dtype=np.complex128).reshape(-1)
+    saved = pr.tables.copy()
+    t0 = 2 * int(pr.toff[fi])
+    pr.tables[t0:t0 + 8] = np.stack([dM.real, dM.imag], axis=1).reshape(-1)
+    try:
+        return amplitude(circuit, x, order=order, model=m, prepared=pr, threads=threads)
+    finally:
+        pr.tables[:] = saved

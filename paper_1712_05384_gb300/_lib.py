@@ -103,6 +103,7 @@ _SIGS = {
     "qgm_plan_get_executor": [_P, _I32P, _I32P, _I64P],
     "qgm_amplitudes_static": [_P, _P, C.c_int64, _P, _P],
     "qgm_amplitude_grad": [_P, _P, C.c_int64, _P, _P, _P, _P],
+    "qgm_plan_set_params": [_P, C.POINTER(C.c_double), C.c_int64, _P],
     "qgm_xeb_stats": [_P, C.c_int64, C.c_int, _P, C.POINTER(qgm_xeb_result), _P],
     "qgm_sample_from_set": [_P, C.c_int64, C.c_int64, C.c_uint64, _P, _P, _P],
     "qgm_last_error": [],
@@ -283,6 +284,7 @@ class Plan:
         check(lib().qgm_plan_get_info(self._h, C.byref(self.info)))
         self.batch = batch
         self.output_mode = output_mode
+        self.gradients = bool(gradients)
         self._ws = None
 
     def order(self):
@@ -433,6 +435,11 @@ class Plan:
 
     def status(self, stream=None):
         return lib().qgm_status(self._h, _stream(stream))
+
+    def set_params(self, params, stream=None):
+        """New (theta, phi) of the RXY gates (flat, 2 per gate) without re-planning."""
+        a = np.ascontiguousarray(np.asarray(params, dtype=np.float64).reshape(-1))
+        check(lib().qgm_plan_set_params(self._h, a.ctypes.data_as(C.POINTER(C.c_double)), a.size, _stream(stream)))
 
     def amplitude_grad(self, d_bits, d_dL_dconja, d_grad, d_amp=None, B=None, stream=None):
         B = d_bits.numel() if B is None else B

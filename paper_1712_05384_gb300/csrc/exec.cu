@@ -1172,13 +1172,17 @@ __global__ void k_seed(float2 *seed, int Bp, Meta *meta, int slot) {
 // g_b = dL/d conj(a_b); accumulated in FP64.
 __global__ void k_grad_reduce(const char *ws, const GradParam *gp, const uint64_t *bits, int64_t B,
                               int Bp, const double2 *g, const Meta *meta, double c_re, double c_im,
-                              double *grad) {
+                              double *grad, int slice, int accumulate) {
   __shared__ double red_r[256], red_i[256];
   const int pidx = blockIdx.x >> 1, which = blockIdx.x & 1;
   const GradParam P = gp[pidx];
   const float2 *adj = reinterpret_cast<const float2 *>(ws + P.adj_off);
   const float2 *db = reinterpret_cast<const float2 *>(ws + P.dbase_off[which]);
   const int64_t rows = (int64_t)1 << P.n_int;
+  // this slice's values of the leaf's sliced variables (between its
+  // internal and output variables in the table index)
+  int sbits = 0;
+  for (int a = 0; a < P.n_slice; ++a) sbits |= ((slice >> P.slice_bit[a]) & 1) << (P.n_slice - 1 - a);
   double sr = 0.0, si = 0.0;
   for (int64_t t = threadIdx.x; t < rows * B; t += blockDim.x) {
     const int64_t r = t / B, b = t - r * B;
@@ -1188,7 +1192,7 @@ __global__ void k_grad_reduce(const char *ws, const GradParam *gp, const uint64_
       const uint64_t x = bits[b];
       for (int q = 0; q < P.n_out; ++q) ob |= (int)((x >> P.out_qubit[q]) & 1ull) << (P.n_out - 1 - q);
     }
-    const float2 d = db[(r << P.n_out) | ob];
+    const float2 d = db[(((r << P.n_slice) | sbits) << P.n_out) | ob];
     const double xr = (double)a.x * d.x - (double)a.y * d.y;
     const double xi = (double)a.x * d.y + (double)a.y * d.x;
     const double2 gb = g[b];
@@ -1208,7 +1212,8 @@ __global__ void k_grad_reduce(const char *ws, const GradParam *gp, const uint64_
   if (threadIdx.x == 0) {
     const double sc = ldexp(1.0, meta[P.adj_meta].exp);
     const double Sr = red_r[0] * sc, Si = red_i[0] * sc;
-    grad[blockIdx.x] = 2.0 * (c_re * Sr - c_im * Si);
+    const double v = 2.0 * (c_re * Sr - c_im * Si);
+    grad[blockIdx.x] = accumulate ? grad[blockIdx.x] + v : v;
   }
 }
 
@@ -1978,6 +1983,29 @@ static int check_bound(qgm_plan *p, const char *fn) {
   return QGM_OK;
 }
 
+// Initial shared memory of the compiled resident kernel: zeros (tensor
+// metadata included) with the bitstring-independent leaf rows in place and
+// the recorded maxima of the steps with a static bound (2^k, exponent 0).
+static int upload_image(qgm_plan *p, const ResidentLayout &L, int smem, cudaStream_t st) {
+  const int64_t shift = worklist_bytes(L);
+  std::vector<float> img((size_t)smem / 4, 0.f);
+  for (const RJob &j : L.jobs) {
+    if (j.batched) continue;
+    const int64_t d = (j.dst - shift) / 4, s2 = 2 * (int64_t)j.src - p->off_base / 4;
+    img[d] = p->base_tables[s2];
+    img[d + 1] = p->base_tables[s2 + 1];
+  }
+  for (const auto &sb : static_bounds(L)) {
+    const uint32_t bits = (uint32_t)(127 + sb.second.first) << 23;
+    const int32_t ex = sb.second.second;
+    std::memcpy(&img[2 * (size_t)sb.first], &bits, 4);
+    std::memcpy(&img[2 * (size_t)sb.first + 1], &ex, 4);
+  }
+  CK(cudaMemcpyAsync(p->exec->ws + p->off_image, img.data(), img.size() * 4, cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+  return QGM_OK;
+}
+
 extern "C" {
 
 int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream) {
@@ -2090,27 +2118,8 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
         if (kp) CK(cudaKernelSetAttributeForDevice(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, smem, x->device));
         int rc = upload(L);
         if (rc) return rc;
-        // initial shared memory: zeros (tensor metadata included) with the
-        // bitstring-independent leaf rows in place
-        {
-          const int64_t shift = worklist_bytes(L);
-          std::vector<float> img((size_t)smem / 4, 0.f);
-          for (const RJob &j : L.jobs) {
-            if (j.batched) continue;
-            const int64_t d = (j.dst - shift) / 4, s2 = 2 * (int64_t)j.src - p->off_base / 4;
-            img[d] = p->base_tables[s2];
-            img[d + 1] = p->base_tables[s2 + 1];
-          }
-          // recorded maxima of the steps with a static bound: 2^k, exponent 0
-          for (const auto &sb : static_bounds(L)) {
-            const uint32_t bits = (uint32_t)(127 + sb.second.first) << 23;
-            const int32_t ex = sb.second.second;
-            std::memcpy(&img[2 * (size_t)sb.first], &bits, 4);
-            std::memcpy(&img[2 * (size_t)sb.first + 1], &ex, 4);
-          }
-          CK(cudaMemcpyAsync(x->ws + p->off_image, img.data(), img.size() * 4, cudaMemcpyHostToDevice, st));
-          CK(cudaStreamSynchronize(st));
-        }
+        rc = upload_image(p, L, smem, st);
+        if (rc) return rc;
         x->jit = k;
         x->jit_pre = kp;
         x->layout = best_li;
@@ -2151,6 +2160,30 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
     return QGM_ERR_ARG;
   }
   if (x->kind == QGM_EXEC_STEPWISE && p->opts.autotune && p->output_mode == QGM_OUT_BATCH) return autotune(p, st);
+  return QGM_OK;
+}
+
+int qgm_plan_set_params(qgm_plan *p, const double *params, int64_t n, void *stream) {
+  if (!p || (!params && n > 0)) {
+    set_error("qgm_plan_set_params: null argument");
+    return QGM_ERR_ARG;
+  }
+  if (n != 2 * (int64_t)p->model.param_factor.size()) {
+    set_error("qgm_plan_set_params: %lld values for %zu parameters", (long long)n, 2 * p->model.param_factor.size());
+    return QGM_ERR_ARG;
+  }
+  int rc = plan_set_params(p, params);
+  if (rc) return rc;
+  if (!p->exec || !p->exec->ws) return QGM_OK;  // uploaded at bind
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (!p->base_tables.empty())
+    CK(cudaMemcpyAsync(p->exec->ws + p->off_base, p->base_tables.data(), p->base_tables.size() * sizeof(float),
+                       cudaMemcpyHostToDevice, st));
+  if (p->exec->kind == QGM_EXEC_COMPILED) {
+    const ResidentLayout &L = p->resident[p->exec->layout];
+    return upload_image(p, L, (int)compiled_smem(L), st);
+  }
+  CK(cudaStreamSynchronize(st));
   return QGM_OK;
 }
 
@@ -2486,20 +2519,26 @@ static void enqueue_grad(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, c
   Meta *meta = reinterpret_cast<Meta *>(ws + p->off_meta);
   const int64_t iblocks = std::min<int64_t>((B + 255) / 256, (int64_t)x->sms * 4);
   k_init<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(amp, B, hdr);
-  launch_leaves(p, d_bitstrings, B, st);
-  for (const StepDesc &d : p->gfwd) launch_step(p, d, st);
   const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
-  k_accumulate<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(
-      ws, p->g_final_off, p->g_final_meta, 1, 0, B, amp, meta, hdr, c.real(), c.imag(), 0, p->Bp);
-  k_seed<<<(p->Bp + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2 *>(ws + p->g_seed_off), p->Bp, meta,
-                                               p->g_seed_meta);
-  for (const StepDesc &d : p->gbwd) launch_step(p, d, st);
   const int n_gates = (int)p->gparams.size();
-  if (n_gates > 0)
-    k_grad_reduce<<<2 * n_gates, 256, 0, st>>>(ws, reinterpret_cast<const GradParam *>(ws + p->off_gparams),
-                                               d_bitstrings, B, p->Bp,
-                                               reinterpret_cast<const double2 *>(d_dL_dconja), meta, c.real(),
-                                               c.imag(), d_grad);
+  // a = sum over slices of a_s: per slice the forward intermediates are
+  // recomputed (leaves for that slice, every step kept), then the adjoint
+  // pass of that slice; the per-gate reduction adds each slice's share
+  const int64_t nslices = (int64_t)1 << p->slice_vars.size();
+  for (int64_t s = 0; s < nslices; ++s) {
+    launch_leaves(p, d_bitstrings, B, st);
+    for (const StepDesc &d : p->gfwd) launch_step(p, d, st);
+    k_accumulate<<<(unsigned)std::max<int64_t>(iblocks, 1), 256, 0, st>>>(
+        ws, p->g_final_off, p->g_final_meta, 1, 0, B, amp, meta, hdr, c.real(), c.imag(), 0, p->Bp);
+    k_seed<<<(p->Bp + 255) / 256, 256, 0, st>>>(reinterpret_cast<float2 *>(ws + p->g_seed_off), p->Bp, meta,
+                                                 p->g_seed_meta);
+    for (const StepDesc &d : p->gbwd) launch_step(p, d, st);
+    if (n_gates > 0)
+      k_grad_reduce<<<2 * n_gates, 256, 0, st>>>(ws, reinterpret_cast<const GradParam *>(ws + p->off_gparams),
+                                                 d_bitstrings, B, p->Bp,
+                                                 reinterpret_cast<const double2 *>(d_dL_dconja), meta, c.real(),
+                                                 c.imag(), d_grad, (int)s, s > 0 ? 1 : 0);
+  }
 }
 
 // ===========================================================================

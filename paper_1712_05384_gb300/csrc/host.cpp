@@ -1233,6 +1233,71 @@ static void build_resident(qgm_plan *p) {
   }
 }
 
+// Numeric contents of the base tables (complex64): each leaf's table laid
+// out over (internal | slice | output variables), and, with gradients, the
+// derivative tables of the leaves holding an RXY gate -- d(leaf)/dp = product
+// of the other members x d(RXY)/dp, for p = theta and phi.
+static void fill_tables(qgm_plan *p) {
+  const Model &m = p->model;
+  for (size_t li = 0; li < p->leaves.size(); ++li) {
+    const LeafFactor &L = p->leaves[li];
+    const std::vector<int> &layout = p->leaf_layout[li];
+    std::vector<cd> tab = expand_table(L.scope, L.table, layout);
+    for (size_t i = 0; i < tab.size(); ++i) {
+      p->base_tables[p->base_at[li] + 2 * i] = (float)tab[i].real();
+      p->base_tables[p->base_at[li] + 2 * i + 1] = (float)tab[i].imag();
+    }
+    if (p->grad && p->rxy_member[li] >= 0) {
+      for (int which = 0; which < 2; ++which) {
+        std::vector<cd> dt(tab.size(), 1.0);
+        for (int fi : L.members) {
+          std::vector<cd> mt = member_table(m, fi, layout, fi == p->rxy_member[li] ? which : -1);
+          for (size_t i = 0; i < dt.size(); ++i) dt[i] *= mt[i];
+        }
+        const int64_t at = p->dbase_at[li] + 2 * which * (int64_t)tab.size();
+        for (size_t i = 0; i < dt.size(); ++i) {
+          p->base_tables[at + 2 * i] = (float)dt[i].real();
+          p->base_tables[at + 2 * i + 1] = (float)dt[i].imag();
+        }
+      }
+    }
+  }
+}
+
+// New angles for the RXY gates of the plan's circuit (params: theta_p at 2p,
+// phi_p at 2p+1, the order of qgm_circuit_param_gates): the gate tables,
+// the merged leaf tables and the constant are recomputed on the host; the
+// variable structure -- and so the order, the steps and the layout -- does
+// not depend on the angles.
+int plan_set_params(qgm_plan *p, const double *params) {
+  Model &m = p->model;
+  for (size_t q = 0; q < m.param_factor.size(); ++q) {
+    MFactor &f = m.factors[m.param_factor[q]];
+    qgm_gate &g = m.gates[f.gate];
+    g.theta = params[2 * q];
+    g.phi = params[2 * q + 1];
+    gate_table(g, f.t, &f.half_pow);
+  }
+  std::vector<LeafFactor> leaves;
+  cd constant;
+  int hp = 0;
+  reduce_factors(m, leaves, constant, hp);
+  if (leaves.size() != p->leaves.size() || hp != p->half_pow_total) {
+    set_error("qgm_plan_set_params: the leaf structure changed");
+    return QGM_ERR_ARG;
+  }
+  for (size_t li = 0; li < leaves.size(); ++li) {
+    if (leaves[li].scope != p->leaves[li].scope || leaves[li].members != p->leaves[li].members) {
+      set_error("qgm_plan_set_params: the leaf structure changed");
+      return QGM_ERR_ARG;
+    }
+    p->leaves[li].table = leaves[li].table;
+  }
+  p->constant = constant;
+  fill_tables(p);
+  return QGM_OK;
+}
+
 int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   p->model = m;
   p->opts = o;
@@ -1430,8 +1495,8 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   p->n_meta = n_meta;
   p->n_meta_fwd = n_meta;
   p->grad = o.gradients != 0;
-  if (p->grad && (o.output_mode != QGM_OUT_BATCH || !p->slice_vars.empty() || p->open_in_batch)) {
-    set_error("qgm_plan_order: gradients need a batch plan without slices");
+  if (p->grad && (o.output_mode != QGM_OUT_BATCH || p->open_in_batch)) {
+    set_error("qgm_plan_order: gradients need a batch plan without open outputs");
     return QGM_ERR_ARG;
   }
   // with gradients: one more slot per adjoint (at most one per tensor) + seed
@@ -1466,6 +1531,10 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   }
   p->off_base = take(base_floats * 4);
   p->base_tables.assign(base_floats, 0.f);
+  p->leaf_layout.clear();
+  p->base_at = base_at;
+  p->dbase_at = dbase_at;
+  p->rxy_member = rxy_member;
   int64_t leaf_bytes = 0;
   for (size_t li = 0; li < p->leaves.size(); ++li) {
     const LeafFactor &L = p->leaves[li];
@@ -1488,26 +1557,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
       set_error("internal: leaf %zu has %zu variables", li, layout.size());
       return QGM_ERR_ARG;
     }
-    std::vector<cd> tab = expand_table(L.scope, L.table, layout);
-    for (size_t i = 0; i < tab.size(); ++i) {
-      p->base_tables[base_at[li] + 2 * i] = (float)tab[i].real();
-      p->base_tables[base_at[li] + 2 * i + 1] = (float)tab[i].imag();
-    }
-    if (p->grad && rxy_member[li] >= 0) {
-      // d(leaf)/dp = (product of the other members) x d(RXY)/dp
-      for (int which = 0; which < 2; ++which) {
-        std::vector<cd> dt(tab.size(), 1.0);
-        for (int fi : L.members) {
-          std::vector<cd> mt = member_table(m, fi, layout, fi == rxy_member[li] ? which : -1);
-          for (size_t i = 0; i < dt.size(); ++i) dt[i] *= mt[i];
-        }
-        const int64_t at = dbase_at[li] + 2 * which * (int64_t)tab.size();
-        for (size_t i = 0; i < dt.size(); ++i) {
-          p->base_tables[at + 2 * i] = (float)dt[i].real();
-          p->base_tables[at + 2 * i + 1] = (float)dt[i].imag();
-        }
-      }
-    }
+    p->leaf_layout.push_back(layout);
     LeafDesc d{};
     d.base_off = p->off_base + base_at[li] * 4;
     d.n_int = (int)intv.size();
@@ -1522,6 +1572,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     leaf_bytes += ((pow2(d.n_int) * (d.batched ? Bp : 1) * 8) + 255) & ~int64_t(255);
     p->leafdesc.push_back(d);
   }
+  fill_tables(p);
   p->off_leaf = take(leaf_bytes);
   for (size_t li = 0; li < p->leafdesc.size(); ++li) {
     p->leafdesc[li].out_off += p->off_leaf;
@@ -1779,7 +1830,11 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
       g.adj_meta = adj_meta[li];
       g.n_int = p->leafdesc[li].n_int;
       g.n_out = p->leafdesc[li].n_out;
-      for (int a = 0; a < MAXLEAFV; ++a) g.out_qubit[a] = p->leafdesc[li].out_qubit[a];
+      g.n_slice = p->leafdesc[li].n_slice;
+      for (int a = 0; a < MAXLEAFV; ++a) {
+        g.out_qubit[a] = p->leafdesc[li].out_qubit[a];
+        g.slice_bit[a] = p->leafdesc[li].slice_bit[a];
+      }
       p->gparams.push_back(g);
     }
     p->off_gparams = gtake((int64_t)std::max<size_t>(p->gparams.size(), 1) * sizeof(GradParam));

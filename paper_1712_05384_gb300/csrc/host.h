@@ -292,9 +292,9 @@ struct GradParam {
   int64_t dbase_off[2];  // complex64 derivative base tables (bytes into the workspace)
   int64_t adj_off;       // adjoint of the leaf: rows x batch_padded complex64
   int32_t adj_meta;
-  int32_t n_int, n_out;
+  int32_t n_int, n_out, n_slice;  // derivative table over (internal | slice | output) variables
   int32_t out_qubit[MAXLEAFV];
-  int32_t pad_;
+  int32_t slice_bit[MAXLEAFV];    // bit of the slice id for each slice variable
 };
 
 struct SymTensor {
@@ -403,6 +403,11 @@ struct qgm_plan {
   int64_t planes_bytes = 0; // its size (the largest tensor-core step's two operands)
   int64_t ws_fwd_bytes = 0; // workspace the forward pass needs without that region
   std::vector<qgm::StepTune> tune;  // per step of `steps` (autotuner choices)
+  // per leaf: table layout (internal | slice | output variables), offset of
+  // its base table and of its derivative tables (floats), its RXY member
+  std::vector<std::vector<int>> leaf_layout;
+  std::vector<int64_t> base_at, dbase_at;
+  std::vector<int> rxy_member;
   bool trees_ok = false;    // buckets of three or more inputs may run as contraction trees
   bool nest_ok = true;      // buckets may be marked for nested evaluation
   qgm_exec_state *exec = nullptr;
@@ -410,6 +415,7 @@ struct qgm_plan {
 
 namespace qgm {
 int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p);
+int plan_set_params(qgm_plan *p, const double *params);
 // CUDA source of the resident kernel specialised to one layout (jit.cpp):
 // the whole pass, its batched part, or its bitstring-independent part
 enum { RES_WHOLE = 0, RES_MAIN = 1, RES_PRE = 2 };

@@ -19,6 +19,12 @@ variables.  Hours of CPU time; written one bitstring at a time.
 
 amps_grid6x6_d25.json: the same for 32 bitstrings of the 6x6 depth-25 batch
 (unsliced).
+
+grad_grid6x6_d20.json: the gradient of L = sum_x log |a_x|^2 over all 256
+bitstrings of the parametrised 6x6 depth-20 batch (seed 0) with respect to
+48 of its angles (24 RXY gates spread over the circuit, theta and phi), by
+derivative insertion with the plain-C elimination: dL/dp = 2 Re sum_x
+conj(a_x / |a_x|^2) da_x/dp (App. B's log-probability loss).
 """
 import hashlib
 import json
@@ -100,6 +106,33 @@ def amps(rows, cols, depth, count, max_clique, fname, threads=0):
         print(f"x={int(x)} a={a!r} {time.time() - t0:.0f}s", flush=True)
 
 
+def grad6x6():
+    c = qi.grid_circuit(6, 6, 20, 0, param=True)
+    m = ugm.build(c)
+    pr = vec.Prepared(m)
+    order, _ = O.min_fill(O.graph(m))
+    bits = qi.bitstrings(c.n, 256, 0)
+    a = np.array([vec.amplitude(c, int(x), order=order, model=m, prepared=pr) for x in bits])
+    gbar = a / np.abs(a) ** 2
+    n_gates = len(c.param_gates)
+    gates = sorted(set(np.linspace(0, n_gates - 1, 24).round().astype(int).tolist()))
+    out = []
+    for p in gates:
+        for which in (0, 1):
+            da = np.array([vec.amplitude_derivative(c, int(x), p, which, order=order, model=m, prepared=pr)
+                           for x in bits])
+            out.append({"param": 2 * p + which, "gate": int(c.param_gates[p]),
+                        "dL": float(2 * np.real(np.sum(np.conj(gbar) * da)))})
+        print(p, out[-2:], flush=True)
+    doc = {"circuit": "grid 6x6, depth 20, seed 0, parametrised (theta, phi per RXY gate)",
+           "bitstrings": "qgm_inputs.bitstrings(36, 256, 0), all of them",
+           "loss": "sum_x log |a_x|^2", "n_params": 2 * n_gates,
+           "source": "oracle/ve.c by derivative insertion (oracle.vec.amplitude_derivative), min-fill order",
+           "sum_log_p": float(np.sum(np.log(np.abs(a) ** 2))), "grad": out}
+    with open(os.path.join(HERE, "grad_grid6x6_d20.json"), "w") as f:
+        json.dump(doc, f, indent=1)
+
+
 def main():
     what = sys.argv[1:] or ["moments", "circuits"]
     if "moments" in what:
@@ -108,6 +141,8 @@ def main():
         circuits()
     if "amps6x6" in what:
         amps(6, 6, 25, 32, 0, "amps_grid6x6_d25.json")
+    if "grad6x6" in what:
+        grad6x6()
     if "amps5x9" in what:
         amps(5, 9, 40, 4, 30, "amps_grid5x9_d40.json")
 

@@ -77,26 +77,86 @@ def test_gradient_matches_finite_differences(q):
     assert ok, worst
 
 
-def test_grid6x6_d20_b256_param_sampled(q):
-    # 6x6 grid, depth 20, parametrised angles, 256 bitstrings: the loss is
-    # sum log|a|^2 over two of them (weights zero elsewhere); 8 sampled
-    # parameters against the oracle's derivative insertion
+def test_grid6x6_d20_b256_full_loss_vs_oracle(q):
+    # 6x6 grid, depth 20, parametrised angles, all 256 bitstrings: the
+    # gradient of L = sum_x log |a_x|^2 (App. B's log-probability loss)
+    # through the torch.autograd wrapper, against the oracle's gradient for 48
+    # of the 362 angles (tests/golden/grad_grid6x6_d20.json: derivative
+    # insertion with the plain-C elimination)
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "grad_grid6x6_d20.json")) as f:
+        gold = json.load(f)
     c = qi.grid_circuit(6, 6, 20, 0, param=True)
     bits = qi.bitstrings(c.n, 256, 0)
-    sel = [3, 200]
-    a_ref = ve.amplitudes(c, bits[sel])
-    weights = np.zeros(256, dtype=complex)
-    weights[sel] = a_ref / np.abs(a_ref) ** 2
-    g, a = gpu_grad(q, c, bits, weights)
-    assert np.max(np.abs(a[sel] - a_ref)) * 2 ** (c.n / 2) < 1e-5
-    rng = np.random.default_rng(0)
-    picks = rng.choice(len(g), 8, replace=False)
-    ref_all = np.zeros(len(g))
-    for qi_ in picks:
-        p, w = divmod(int(qi_), 2)
-        da = np.array([OG.amplitude_derivative_ve(c, int(bits[s]), p, w) for s in sel])
-        ref_all[qi_] = 2 * np.real(np.sum(np.conj(weights[sel]) * da))
-    ok, worst = close(g[picks], ref_all[picks])
+    plan = q.Plan(q.Model(q.Circuit.grid(6, 6, 20, 0, True)), batch=256, gradients=True).bind()
+    th, ph = OG.params(c)
+    params = torch.tensor(np.stack([th, ph], axis=1).reshape(-1), dtype=torch.float64, requires_grad=True)
+    assert params.numel() == gold["n_params"]
+    d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
+    a = q.autograd.amplitudes(plan, params, d_bits)
+    L = torch.sum(torch.log(torch.abs(a) ** 2))
+    assert abs(L.item() - gold["sum_log_p"]) < 1e-4 * abs(gold["sum_log_p"])
+    L.backward()
+    assert plan.status() == 0
+    g = params.grad.numpy()
+    idx = [e["param"] for e in gold["grad"]]
+    ref = np.array([e["dL"] for e in gold["grad"]])
+    ok, worst = close(g[idx], ref)
+    print(f"[grad] 6x6 d20, 256 bitstrings, {len(idx)} angles: worst scaled error {worst:.2e}")
+    assert ok, worst
+
+
+def test_autograd_small_and_new_angles(q):
+    # the autograd wrapper on 3x3 depth 12: L = sum log|a|^2 against the
+    # oracle's derivative insertion; then new angles through the same plan
+    # (qgm_plan_set_params, no re-planning) give the other circuit's
+    # amplitudes and gradient
+    c = qi.grid_circuit(3, 3, 12, 4, param=True)
+    bits = qi.bitstrings(c.n, 16, 4)
+    plan = q.Plan(q.Model(q.Circuit.grid(3, 3, 12, 4, True)), batch=16, gradients=True).bind()
+    d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
+    th, ph = OG.params(c)
+    for shift in (0.0, 0.3):
+        c2 = c.with_angles(th + shift, ph - shift)
+        params = torch.tensor(np.stack([th + shift, ph - shift], axis=1).reshape(-1), dtype=torch.float64,
+                              requires_grad=True)
+        a = q.autograd.amplitudes(plan, params, d_bits)
+        assert np.max(np.abs(a.detach().cpu().numpy() - sv.amplitudes(c2, bits))) * 2 ** (c.n / 2) < 1e-5
+        torch.sum(torch.log(torch.abs(a) ** 2)).backward()
+        ok, worst = close(params.grad.numpy(), OG.grad_exact(c2, bits))
+        assert ok, (shift, worst)
+
+
+def test_sliced_gradient_equals_unsliced(q):
+    # a sliced gradient plan recomputes each slice's forward intermediates
+    # before its adjoint pass and adds the slices' shares
+    c = qi.grid_circuit(4, 5, 20, 2, param=True)
+    bits = qi.bitstrings(c.n, 8, 2)
+    m = q.Model(q.Circuit.grid(4, 5, 20, 2, True))
+    full = q.Plan(m, batch=8, gradients=True, executor=1)
+    sliced = q.Plan(m, batch=8, gradients=True, executor=1, mem_budget_bytes=full.info.arena_bytes // 3)
+    assert full.info.n_slices == 1 and 2 <= sliced.info.n_slices <= 64
+    a_ref = sv.amplitudes(c, bits)
+    w = a_ref / np.abs(a_ref) ** 2
+    ww = np.zeros(16)
+    ww[0::2], ww[1::2] = w.real, w.imag
+    d_w = torch.from_numpy(ww).cuda()
+    d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
+    out = []
+    for plan in (full, sliced):
+        plan.bind()
+        d_grad = torch.zeros(2 * len(c.param_gates), dtype=torch.float64, device="cuda")
+        d_amp = torch.zeros(16, dtype=torch.float64, device="cuda")
+        plan.amplitude_grad(d_bits, d_w, d_grad, d_amp)
+        torch.cuda.synchronize()
+        assert plan.status() == 0
+        o = d_amp.cpu().numpy()
+        assert np.max(np.abs(o[0::2] + 1j * o[1::2] - a_ref)) * 2 ** (c.n / 2) < 1e-5
+        out.append(d_grad.cpu().numpy())
+    ok, worst = close(out[1], out[0])
+    assert ok, worst
+    ok, worst = close(out[1], OG.grad_exact(c, bits))
     assert ok, worst
 
 

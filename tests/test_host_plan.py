@@ -309,3 +309,32 @@ def test_contraction_trees_keep_every_tensor(rows, cols, depth, batch, kw):
     st = p.steps()
     assert st["k"].sum() == p.info.n_free
     assert st["out_rank"][-1] == 0
+
+
+def test_set_params_checks_its_arguments():
+    # new angles keep the plan's structure; the count must match 2 per RXY gate
+    c = Q.Circuit.grid(3, 3, 10, 1, True)
+    p = Q.Plan(Q.Model(c), batch=4, gradients=True)
+    n = 2 * len(c.param_gates())
+    p.set_params(np.linspace(0.1, 3.0, n))
+    with pytest.raises(Q.QgmError):
+        p.set_params(np.zeros(n + 2))
+    # a sliced gradient plan is accepted (each slice recomputed in turn)
+    m = Q.Model(Q.Circuit.grid(4, 5, 20, 2, True))
+    full = Q.Plan(m, batch=8, gradients=True, executor=Q.EXEC_STEPWISE)
+    s = Q.Plan(m, batch=8, gradients=True, executor=Q.EXEC_STEPWISE, mem_budget_bytes=full.info.arena_bytes // 3)
+    assert s.info.n_slices > 1
+
+
+def test_torch_complex_gradient_convention():
+    # the autograd wrapper relies on torch passing G = 2 dL/d(conj a) for a
+    # complex output and expecting dL/dp = Re sum conj(G) da/dp: for
+    # L = |a|^2 with a = (1 + 2i) p at p = 1, dL/dp = 2 |1 + 2i|^2 = 10
+    torch = pytest.importorskip("torch")
+    p = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    z = torch.tensor(1 + 2j, dtype=torch.complex128, requires_grad=True)
+    (z * z.conj()).real.backward()
+    assert complex(z.grad) == 2 * (1 + 2j)        # G = 2 dL/dconj(z) = 2 z
+    a = (1 + 2j) * p.to(torch.complex128)
+    (a * a.conj()).real.backward()
+    assert abs(p.grad.item() - 10.0) < 1e-12
