@@ -209,6 +209,14 @@ typedef struct {
                                  term products above 2^-24 (24 MMAs);
                                  -1: every GEMM step on the FP32 cores (plain
                                  complex64) */
+  int32_t n_keep;             /* QGM_OUT_BATCH: variables (model ids, not
+                                 inputs) kept open like open outputs: the
+                                 result then has 2^(k + n_keep) entries per
+                                 bitstring, keep_vars[j] being bit j of the
+                                 low n_keep bits of the entry index (e.g. an
+                                 intermediate table of App. D, see
+                                 qgm_eliminate_fixed) */
+  const int32_t *keep_vars;   /* n_keep variable ids (copied at plan time) */
 } qgm_plan_opts;
 
 enum {
@@ -319,7 +327,42 @@ int qgm_amplitudes_host(qgm_plan *p, const uint64_t *h_bitstrings, int64_t B,
  * (entry x has bit j = qubit j): Eq. psi_x with the output deltas omitted. */
 int qgm_eliminate(qgm_plan *p, double *d_out, void *stream);
 
-/* Timing pass for reports: runs slice 0 of qgm_amplitudes kernel by kernel
+/* One contraction for a fixed output assignment (Eq. psi_x with the output
+ * deltas fixed to fixed_assign[q], host uint8 of n_qubits values 0/1, qubit q
+ * at index q): the final tensor as the elimination leaves it, before its
+ * power-of-two exponent is applied.  d_out (device double[2 * 2^k], k =
+ * popcount(open_mask) + n_keep) receives c * F[r], c the plan's constant
+ * (scope-free factors, 2^{-1/2} per fixed gate pulled out), and *exp_out
+ * (host) the exponent e: the value is d_out[r] * 2^e, which stays finite
+ * where the product itself would leave FP64's range.  With kept variables
+ * (qgm_plan_opts.keep_vars) it returns an intermediate table of App. A's
+ * elimination, e.g. App. D's tau_2.  Runs the stepwise kernels whatever the
+ * bound executor (the final tensor must be in the workspace); a sliced plan
+ * returns the FP64 sum of its slices with *exp_out = 0.  Synchronises.
+ * Errors: QGM_ERR_ARG (plan kind, values), QGM_ERR_CUDA. */
+int qgm_eliminate_fixed(qgm_plan *p, const uint8_t *fixed_assign, double *d_out, int64_t *exp_out,
+                        void *stream);
+
+/* Report of one qgm_amplitudes call: the device status word (read and
+ * cleared), the executor, milliseconds (CUDA events on the stream around
+ * the call), the slices, the algorithmic bytes and flops of the plan's steps
+ * over all slices (qgm_plan_info) and the kernel launches issued. */
+typedef struct {
+  int32_t status;
+  int32_t executor;
+  float ms;
+  double bytes;
+  double flops;
+  int64_t slices;
+  int64_t launches;
+} qgm_report;
+
+/* qgm_amplitudes with a report (synchronises `stream`); returns the device
+ * status as an error when it is not QGM_OK. */
+int qgm_amplitudes_report(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out, qgm_report *rep,
+                          void *stream);
+
+/* Timing pass for reports:/* Timing pass for reports: runs slice 0 of qgm_amplitudes kernel by kernel
  * (no graph) with CUDA events around each launch on `stream` and stores the
  * milliseconds in ms[0] (leaf build), ms[1 + s] (step s), ms[n_steps + 1]
  * (accumulation); ms must hold n_steps + 2 floats (host).  Synchronises. */

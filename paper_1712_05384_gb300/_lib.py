@@ -40,12 +40,18 @@ class qgm_plan_opts(C.Structure):
                 ("order", C.POINTER(C.c_int32)), ("executor", C.c_int32),
                 ("no_gemm", C.c_int32), ("gradients", C.c_int32), ("trees", C.c_int32),
                 ("open_mask", C.c_uint64),
-                ("resident_chunk", C.c_int32), ("autotune", C.c_int32), ("gemm_precision", C.c_int32)]
+                ("resident_chunk", C.c_int32), ("autotune", C.c_int32), ("gemm_precision", C.c_int32),
+                ("n_keep", C.c_int32), ("keep_vars", C.POINTER(C.c_int32))]
 
 
 class qgm_xeb_result(C.Structure):
     _fields_ = [("cross_entropy", C.c_double), ("alpha", C.c_double), ("mean_Np", C.c_double),
                 ("second_moment", C.c_double)]
+
+
+class qgm_report(C.Structure):
+    _fields_ = [("status", C.c_int32), ("executor", C.c_int32), ("ms", C.c_float), ("bytes", C.c_double),
+                ("flops", C.c_double), ("slices", C.c_int64), ("launches", C.c_int64)]
 
 
 class qgm_plan_info(C.Structure):
@@ -99,6 +105,8 @@ _SIGS = {
     "qgm_amplitudes": [_P, _P, C.c_int64, _P, _P],
     "qgm_amplitudes_host": [_P, _P, C.c_int64, _P, _P],
     "qgm_eliminate": [_P, _P, _P],
+    "qgm_eliminate_fixed": [_P, C.POINTER(C.c_uint8), _P, _I64P, _P],
+    "qgm_amplitudes_report": [_P, _P, C.c_int64, _P, C.POINTER(qgm_report), _P],
     "qgm_status": [_P, _P],
     "qgm_plan_get_executor": [_P, _I32P, _I32P, _I64P],
     "qgm_amplitudes_static": [_P, _P, C.c_int64, _P, _P],
@@ -249,7 +257,7 @@ class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
                  resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=None,
-                 split_bf16=None, precision=None, autotune=False):
+                 split_bf16=None, precision=None, autotune=False, keep_vars=None):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -270,8 +278,15 @@ class Plan:
             precision = "bf16" if split_bf16 else "fp32"
         o.gemm_precision = {None: 0, "fp16": 2, "bf16": 1, "fp32": -1}[precision]
         o.autotune = 1 if autotune else 0
-        # amplitudes per bitstring: its open qubits run over all 2^k values
-        self.n_open = bin(open_mask).count("1") if output_mode == OUT_BATCH else 0
+        self._keep_buf = None
+        if keep_vars is not None and len(keep_vars):
+            self._keep_buf = np.ascontiguousarray(keep_vars, dtype=np.int32)
+            o.keep_vars = self._keep_buf.ctypes.data_as(_I32P)
+            o.n_keep = len(self._keep_buf)
+        # amplitudes per bitstring: its open qubits (and kept variables) run
+        # over all their values
+        self.n_open = (bin(open_mask).count("1") + (0 if self._keep_buf is None else len(self._keep_buf))
+                       if output_mode == OUT_BATCH else 0)
         self._order_buf = None
         if order is not None:
             self._order_buf = np.ascontiguousarray(order, dtype=np.int32)
@@ -390,6 +405,26 @@ class Plan:
     def eliminate(self, d_out, stream=None):
         check(lib().qgm_eliminate(self._h, _ptr(d_out), _stream(stream)))
         return d_out
+
+    def eliminate_fixed(self, x_bits, stream=None):
+        """(raw final tensor times the constant, as complex128 of 2^k entries,
+        exponent e): the values are raw * 2^e for the output bits x_bits
+        (sequence of n 0/1 values, qubit q first)."""
+        import torch
+        fa = np.ascontiguousarray(x_bits, dtype=np.uint8)
+        out = torch.zeros(2 << self.n_open, dtype=torch.float64, device="cuda")
+        e = C.c_int64()
+        check(lib().qgm_eliminate_fixed(self._h, fa.ctypes.data_as(C.POINTER(C.c_uint8)), _ptr(out), C.byref(e),
+                                        _stream(stream)))
+        o = out.cpu().numpy()
+        return o[0::2] + 1j * o[1::2], e.value
+
+    def amplitudes_report(self, d_bits, d_out, B=None, stream=None):
+        """qgm_amplitudes with its report (a dict)."""
+        B = d_bits.numel() if B is None else B
+        r = qgm_report()
+        check(lib().qgm_amplitudes_report(self._h, _ptr(d_bits), B, _ptr(d_out), C.byref(r), _stream(stream)))
+        return {k: getattr(r, k) for k, _ in r._fields_}
 
     def profile(self, d_bits, d_out, B=None, stream=None):
         """Per-kernel milliseconds of one slice: [leaves, step 0..n-1, accumulate]."""

@@ -1156,6 +1156,20 @@ __global__ void k_accumulate(const char *ws, int64_t final_off, int final_meta, 
   }
 }
 
+// The final tensor of batch entry 0 as it stands (its exponent left apart),
+// times the constant c, in FP64: out[r] for the 2^rows_log open entries.
+__global__ void k_raw_final(const char *ws, int64_t final_off, int final_batched, int rows_log, int Bp,
+                            double c_re, double c_im, double2 *out, const Meta *meta, int final_meta,
+                            int64_t *exp_out) {
+  const float2 *F = reinterpret_cast<const float2 *>(ws + final_off);
+  const int64_t rows = (int64_t)1 << rows_log;
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = F[final_batched ? r * Bp : r];
+    out[r] = make_double2((double)v.x * c_re - (double)v.y * c_im, (double)v.x * c_im + (double)v.y * c_re);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *exp_out = final_meta >= 0 ? (int64_t)meta[final_meta].exp : 0;
+}
+
 // Adjoint seed: d(final)/d(final) = 1 for every batch entry, exponent 0.
 __global__ void k_seed(float2 *seed, int Bp, Meta *meta, int slot) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < Bp; t += gridDim.x * blockDim.x)
@@ -2266,6 +2280,97 @@ int qgm_eliminate(qgm_plan *p, double *d_out, void *stream) {
   uint64_t *d_bits = reinterpret_cast<uint64_t *>(p->exec->ws + p->off_bits);
   return run(p, d_bits, 1, reinterpret_cast<double2 *>(d_out), p->final_entries,
              static_cast<cudaStream_t>(stream));
+}
+
+int qgm_eliminate_fixed(qgm_plan *p, const uint8_t *fixed_assign, double *d_out, int64_t *exp_out, void *stream) {
+  int rc = check_bound(p, "qgm_eliminate_fixed");
+  if (rc) return rc;
+  if (p->output_mode != QGM_OUT_BATCH || !fixed_assign || !d_out || !exp_out) {
+    set_error("qgm_eliminate_fixed: needs a batch plan and non-null arguments");
+    return QGM_ERR_ARG;
+  }
+  uint64_t x = 0;
+  for (int q = 0; q < p->model.n; ++q) {
+    if (fixed_assign[q] > 1) {
+      set_error("qgm_eliminate_fixed: output value of qubit %d is %d, not 0 or 1", q, (int)fixed_assign[q]);
+      return QGM_ERR_ARG;
+    }
+    x |= (uint64_t)fixed_assign[q] << q;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  qgm_exec_state *xs = p->exec;
+  uint64_t *d_bits = reinterpret_cast<uint64_t *>(xs->ws + p->off_bits);
+  double2 *out = reinterpret_cast<double2 *>(d_out);
+  const int64_t n_out = (int64_t)1 << p->open_in_batch;
+  CK(cudaMemcpyAsync(d_bits, &x, sizeof x, cudaMemcpyHostToDevice, st));
+  if (!p->slice_vars.empty()) {
+    // slices carry exponents of their own: their FP64 sum, exponent 0
+    rc = run(p, d_bits, 1, out, n_out, st);
+    if (rc) return rc;
+    *exp_out = 0;
+    CK(cudaStreamSynchronize(st));
+    return QGM_OK;
+  }
+  // the stepwise launches (whatever executor is bound: the final tensor must
+  // be in the workspace), then the raw final tensor and its exponent
+  Header *hdr = reinterpret_cast<Header *>(xs->ws + p->off_header);
+  k_init<<<1, 32, 0, st>>>(out, 0, hdr);
+  launch_leaves(p, d_bits, 1, st);
+  for (const StepDesc &d : p->steps) launch_step(p, d, st);
+  int64_t *d_exp = reinterpret_cast<int64_t *>(xs->ws + p->off_outstage);
+  const cd c = p->constant * std::pow(2.0, -0.5 * p->half_pow_total);
+  k_raw_final<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>((n_out + 255) / 256, 1024)), 256, 0, st>>>(
+      xs->ws, p->final_off, p->final_batched, p->open_in_batch, p->Bp, c.real(), c.imag(), out,
+      reinterpret_cast<const Meta *>(xs->ws + p->off_meta), p->final_meta, d_exp);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(exp_out, d_exp, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return QGM_OK;
+}
+
+int qgm_amplitudes_report(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out, qgm_report *rep,
+                          void *stream) {
+  if (!rep) {
+    set_error("qgm_amplitudes_report: null report");
+    return QGM_ERR_ARG;
+  }
+  std::memset(rep, 0, sizeof *rep);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  CK(cudaEventRecord(a, st));
+  int rc = qgm_amplitudes(p, d_bitstrings, B, d_out, stream);
+  if (rc) {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    rep->status = rc;
+    return rc;
+  }
+  CK(cudaEventRecord(b, st));
+  CK(cudaEventSynchronize(b));
+  CK(cudaEventElapsedTime(&rep->ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  const qgm_exec_state *x = p->exec;
+  rep->executor = x->kind;
+  rep->slices = (int64_t)1 << p->slice_vars.size();
+  rep->bytes = p->sim.bytes * (double)rep->slices;
+  rep->flops = p->sim.flops * (double)rep->slices;
+  if (x->kind == QGM_EXEC_STEPWISE) {
+    int64_t per = (int64_t)p->steps.size() + 2;
+    for (const StepDesc &d : p->steps)
+      if (d.gemm >= 0 && p->gemm_tc && tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes).ok) per += 2;
+    rep->launches = per * rep->slices + 1;
+  } else {
+    rep->launches = x->jit_pre ? 2 : 1;
+  }
+  rep->status = qgm_status(p, stream);
+  if (rep->status < 0) {
+    set_error("qgm_amplitudes_report: device status %d", rep->status);
+    return rep->status;
+  }
+  return QGM_OK;
 }
 
 int qgm_plan_profile(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, double *d_out, float *ms,

@@ -1302,6 +1302,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   p->model = m;
   p->opts = o;
   p->opts.order = nullptr;
+  p->opts.keep_vars = nullptr;
   p->output_mode = o.output_mode;
   if (o.output_mode != QGM_OUT_BATCH && o.output_mode != QGM_OUT_OPEN) {
     set_error("qgm_plan_order: bad output_mode %d", o.output_mode);
@@ -1359,6 +1360,22 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
       set_error("qgm_plan_order: qubit %d has no non-diagonal gate (every qubit needs one)", q);
       return QGM_ERR_ARG;
     }
+  // variables kept open on request (a batch plan): never eliminated, like
+  // open outputs; keep_vars[j] is bit j of the low part of the entry index
+  if (o.n_keep < 0 || (o.n_keep > 0 && (!o.keep_vars || o.output_mode != QGM_OUT_BATCH))) {
+    set_error("qgm_plan_order: keep_vars needs a batch plan and a list");
+    return QGM_ERR_ARG;
+  }
+  for (int j = o.n_keep - 1; j >= 0; --j) {
+    const int v = o.keep_vars[j];
+    if (v < 0 || v >= m.n_vars || p->var_role[v] == 1 || p->var_role[v] == 3) {
+      set_error("qgm_plan_order: keep_vars holds %d (an input, an open output, repeated or unknown)", v);
+      return QGM_ERR_ARG;
+    }
+    p->var_role[v] = 3;
+    p->open_vars.push_back(v);
+    p->open_in_batch += 1;
+  }
   std::vector<char> in_graph(m.n_vars, 0), elim(m.n_vars, 0), keep(m.n_vars, 0);
   for (int v = 0; v < m.n_vars; ++v) {
     in_graph[v] = p->var_role[v] == 0 || p->var_role[v] == 3;

@@ -451,3 +451,44 @@ def test_narrow_gemm_tiles_with_wide_batch():
     assert rel < 2 * REL_TOL and ab < 2 * ABS_TOL, (rel, ab)
     rel, ab = errors(a[:4], ve.amplitudes(c, bits[:4]), c.n)
     assert rel < REL_TOL and ab < ABS_TOL, (rel, ab)
+
+
+def test_eliminate_fixed_app_d_tables(app_d):
+    # App. D: with the inputs and outputs fixed to 0, eliminating b_1^1
+    # leaves tau_2(b_0^1) = (1/2, 0) and summing b_0^1 gives <00|C|00> = 1/2.
+    # qgm_eliminate_fixed returns the raw final tensor (times the plan's
+    # constant) and its power-of-two exponent
+    q = Q()
+    c = q.Circuit.from_gates(app_d.n, app_d.gates)
+    m = q.Model(c)
+    qubit, k = m.vars()
+    b01 = [v for v in range(len(qubit)) if qubit[v] == 0 and k[v] == 1][0]
+    for executor in EXECS:
+        p = q.Plan(m, batch=1, executor=executor)
+        p.bind()
+        raw, e = p.eliminate_fixed([0, 0])
+        assert abs(raw[0] * 2.0 ** e - 0.5) < 1e-7
+        pk = q.Plan(m, batch=1, keep_vars=[b01], executor=1).bind()
+        raw, e = pk.eliminate_fixed([0, 0])
+        assert np.allclose(raw * 2.0 ** e, [0.5, 0.0], atol=1e-7)
+        # other outputs: <x|C|00> = (1/2, 1/2, 1/2, -1/2) by the state vector
+        for x, ref in [((1, 0), 0.5), ((0, 1), 0.5), ((1, 1), -0.5)]:
+            raw, e = p.eliminate_fixed(x)
+            assert abs(raw[0] * 2.0 ** e - ref) < 1e-7
+
+
+def test_amplitudes_report(app_d):
+    q = Q()
+    c = qi.grid_circuit(4, 4, 12, 0)
+    bits = qi.bitstrings(16, 32, 0)
+    for executor in EXECS:
+        p = q.Plan(q.Model(q.Circuit.grid(4, 4, 12, 0)), batch=32, executor=executor).bind()
+        d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
+        d_out = torch.empty(64, dtype=torch.float64, device="cuda")
+        r = p.amplitudes_report(d_bits, d_out)
+        assert r["status"] == 0 and r["executor"] == executor and r["ms"] > 0
+        assert r["slices"] == 1 and r["launches"] >= 1
+        assert r["flops"] == p.info.flops_per_slice and r["bytes"] == p.info.bytes_per_slice
+        o = d_out.cpu().numpy()
+        rel, ab = errors(o[0::2] + 1j * o[1::2], sv.amplitudes(c, bits), 16)
+        assert rel < REL_TOL and ab < ABS_TOL
