@@ -299,7 +299,8 @@ def main():
     pk = peaks()
 
     def make_plan(precision):
-        return q.Plan(model, batch=P, executor=args.executor, precision=precision,
+        # the autotuner picks per-step launch parameters at bind (untimed)
+        return q.Plan(model, batch=P, executor=args.executor, precision=precision, autotune=True,
                       order_kind=q.ORDER_MINFILL if P < B else q.ORDER_AUTO).bind()
 
     def run_pass(plan, i):

@@ -366,14 +366,16 @@ class Plan:
 
     def gemm_shapes(self):
         """GEMM-shaped steps: list of dicts (step, nm, nn, nk, ns, a_bat,
-        b_bat, o_bat, tc) -- 2^nm x 2^nn outputs, 2^nk summed entries, for
-        each of the 2^ns shared indices (and batch entry when batched)."""
+        b_bat, o_bat, tc, o_bout, in_bout) -- 2^nm x 2^nn outputs, 2^nk
+        summed entries, for each of the 2^ns shared indices (and batch entry
+        when batched); o_bout / in_bout: output / an operand stored with the
+        batch entry outermost."""
         n = C.c_int64()
         check(lib().qgm_plan_get_gemm(self._h, None, 0, C.byref(n)))
-        a = np.zeros(9 * max(n.value, 1), dtype=np.int32)
+        a = np.zeros(11 * max(n.value, 1), dtype=np.int32)
         check(lib().qgm_plan_get_gemm(self._h, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
-        keys = ("step", "nm", "nn", "nk", "ns", "a_bat", "b_bat", "o_bat", "tc")
-        return [dict(zip(keys, map(int, a[9 * c: 9 * c + 9]))) for c in range(n.value)]
+        keys = ("step", "nm", "nn", "nk", "ns", "a_bat", "b_bat", "o_bat", "tc", "o_bout", "in_bout")
+        return [dict(zip(keys, map(int, a[11 * c: 11 * c + 11]))) for c in range(n.value)]
 
     # ------------------------------------------------------------ device
     def bind(self, workspace=None, stream=None):

@@ -835,6 +835,7 @@ struct SplitArgs {
   int32_t tr;                // rows per tile (128 for the M side, NT for N)
   int64_t rows, rtiles, kc;  // rows per instance, row tiles, chunks of 16
   int32_t fp16;              // 1: FP16 terms (4 planes), 0: BF16 (6 planes)
+  int32_t bout, rank;        // batch entry outermost: entry beta at beta * 2^rank complex64
   uint8_t rX[GMAXB], kX[GMAXB], sX[GMAXB];
 };
 
@@ -851,7 +852,8 @@ __global__ void __launch_bounds__(256) k_split(char *ws, const __grid_constant__
   const int64_t nb = a.perbeta ? a.Bp : 1;
   const int64_t RP = a.rtiles * a.tr, KG = a.kc * 2;
   const int64_t n_items = ((int64_t)1 << a.ns) * KG * RP * nb;
-  const int64_t u = a.batched ? (int64_t)a.Bp * 8 : 8;
+  const int64_t u = a.batched && !a.bout ? (int64_t)a.Bp * 8 : 8;
+  const int64_t ustride = a.bout ? ((int64_t)8 << a.rank) : 8;  // bytes between batch entries
   const int64_t pbytes = (int64_t)a.tr * 32;
   for (int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; it < n_items;
        it += (int64_t)gridDim.x * blockDim.x) {
@@ -868,7 +870,7 @@ __global__ void __launch_bounds__(256) k_split(char *ws, const __grid_constant__
       const int64_t beta = a.fold ? rho % a.Bp : b;
       const int64_t base = a.src_off + (lin_bits((uint64_t)s, a.sX, a.ns) + lin_bits((uint64_t)m, a.rX, a.nr) +
                                         lin_bits((uint64_t)(kg * 8), a.kX, a.nk)) * u +
-                           (a.batched ? beta * 8 : 0);
+                           (a.batched ? beta * ustride : 0);
       if (klow == 3) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
@@ -927,10 +929,15 @@ struct TcArgs {
   int64_t pm_off, pn_off, o_off;  // plane regions of the M and N sides; output
   int32_t a_meta, b_meta, o_meta; // M side, N side, output
   int32_t o_bat, fold, perbeta, Bp;
+  int32_t o_bout, o_rank;         // output batch entry outermost (2^o_rank complex64 per entry)
   int32_t nM, nN, ns;
   int64_t mrows, mtiles, ntiles, kc;
   float out_scale;                // undoes the terms' scale: 2^-30 (FP16) or 1
   uint8_t mO[GMAXB], nO[GMAXB], sO[GMAXB];
+  // k_gemm_tc_conv: the M side read as complex64 from the operand itself
+  int64_t a_src_off;
+  int32_t a_batched, a_bout, a_rank, nk;
+  uint8_t mA[GMAXB], kA[GMAXB], sA[GMAXB];
 };
 
 __host__ __device__ constexpr int tc_plane_bytes(int rows) { return rows * 32; }
@@ -973,7 +980,8 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(char *ws, const __grid_const
   const int64_t tm = bid % a.mtiles;
   const int64_t sidx = bid / a.mtiles;
   const int64_t inst = a.perbeta ? sidx * a.Bp + beta : sidx;
-  const int64_t uO = a.o_bat ? (int64_t)a.Bp * 8 : 8;
+  const int64_t uO = a.o_bat && !a.o_bout ? (int64_t)a.Bp * 8 : 8;
+  const int64_t bstrideO = a.o_bout ? ((int64_t)8 << a.o_rank) : 8;  // bytes between batch entries
   for (int j = tid; j < NT; j += 128) colO[j] = lin_bits((uint64_t)(tn * NT + j), a.nO, a.nN) * uO;
   if (tid == 0) abort_flag = 0;
   float sa, sb;
@@ -1097,8 +1105,264 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(char *ws, const __grid_const
       b2 = rho % a.Bp;
     }
     char *orow = ws + a.o_off + (lin_bits((uint64_t)sidx, a.sO, a.ns) + lin_bits((uint64_t)(valid ? m : 0), a.mO, a.nM)) * uO +
-                 (a.o_bat ? b2 * 8 : 0);
+                 (a.o_bat ? b2 * bstrideO : 0);
     const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+    for (int c0 = 0; c0 < NT; c0 += 16) {
+      uint32_t re[16], im[16];
+      tc_ld16(tl + c0, re);
+      tc_ld16(tl + NT + c0, im);
+      if (valid) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const float2 v = make_float2(__uint_as_float(re[j]) * a.out_scale, __uint_as_float(im[j]) * a.out_scale);
+          *reinterpret_cast<float2 *>(orow + colO[c0 + j]) = v;
+          lmax = fmax_nan(lmax, absmax2(v));
+        }
+      }
+    }
+  }
+  if (!valid_run && tid == 0 && hdr) atomicCAS(&hdr->status, 0, QGM_ERR_TIMEOUT);
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(COLS));
+  record_max(lmax, meta, a.o_meta);
+}
+
+// The folded tensor-core step with the M side converted in the kernel.  When
+// the batch entries fold into the M side (one operand without a batch axis),
+// that side is the large operand streamed once; splitting it in a separate
+// pass would read and write it once more.  Here 8 warps: warp 0 streams the
+// N side's planes (bulk copies, as k_gemm_tc), warp 1 issues the MMAs, warps
+// 4-7 convert: thread r gathers row r of each chunk (16 complex64 values
+// through the operand's bit maps, two chunks ahead in registers), scales and
+// splits them into the 16-bit planes of the stage (the layout k_split
+// writes), makes the stores visible to the tensor cores (fence.proxy.async)
+// and arrives on the stage's "full" mbarrier, which completes when the 128
+// converters and the N side's bytes are in.  Warps 4-7 then read the
+// accumulators back (TMEM lane quadrant = warp % 4).  Waits are bounded as
+// in k_gemm_tc.
+template <int P>
+__device__ __forceinline__ void conv_put(uint8_t *stage, int r, const float2 (&v)[16]) {
+  const int pb = tc_plane_bytes(TC_M);
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    uint8_t *base = stage + (r >> 3) * 256 + half * 128 + (r & 7) * 16;
+    if (P == 4) {
+      uint32_t rh[4], rl[4], ih[4], il[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split2h(v[half * 8 + 2 * q].x, v[half * 8 + 2 * q + 1].x, rh[q], rl[q]);
+        split2h(v[half * 8 + 2 * q].y, v[half * 8 + 2 * q + 1].y, ih[q], il[q]);
+      }
+      *reinterpret_cast<uint4 *>(base) = make_uint4(rh[0], rh[1], rh[2], rh[3]);
+      *reinterpret_cast<uint4 *>(base + pb) = make_uint4(rl[0], rl[1], rl[2], rl[3]);
+      *reinterpret_cast<uint4 *>(base + 2 * pb) = make_uint4(ih[0], ih[1], ih[2], ih[3]);
+      *reinterpret_cast<uint4 *>(base + 3 * pb) = make_uint4(il[0], il[1], il[2], il[3]);
+    } else {
+      uint32_t re[3][4], im[3][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        split3(v[half * 8 + 2 * q].x, v[half * 8 + 2 * q + 1].x, re[0][q], re[1][q], re[2][q]);
+        split3(v[half * 8 + 2 * q].y, v[half * 8 + 2 * q + 1].y, im[0][q], im[1][q], im[2][q]);
+      }
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        *reinterpret_cast<uint4 *>(base + t * pb) = make_uint4(re[t][0], re[t][1], re[t][2], re[t][3]);
+        *reinterpret_cast<uint4 *>(base + (3 + t) * pb) = make_uint4(im[t][0], im[t][1], im[t][2], im[t][3]);
+      }
+    }
+  }
+}
+
+template <int NT, int P>
+__global__ void __launch_bounds__(256, 1) k_gemm_tc_conv(char *ws, const __grid_constant__ TcArgs a, Meta *meta,
+                                                         Header *hdr) {
+  constexpr int S = tc_stages(NT, P);
+  constexpr int ABYTES = P * tc_plane_bytes(TC_M), BBYTES = P * tc_plane_bytes(NT);
+  constexpr int SBYTES = ABYTES + BBYTES;
+  constexpr uint32_t COLS = 2 * NT < 32 ? 32 : 2 * NT;
+  static_assert(S >= 2, "at least two stages");
+  extern __shared__ __align__(1024) uint8_t tsm[];
+  __shared__ __align__(8) uint64_t bar_full[S], bar_empty[S], bar_done;
+  __shared__ uint32_t tbase;
+  __shared__ int abort_flag;
+  __shared__ int64_t colO[NT];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int64_t bid = blockIdx.x;
+  const int64_t tn = bid % a.ntiles;
+  bid /= a.ntiles;
+  const int64_t tm = bid % a.mtiles;
+  const int64_t sidx = bid / a.mtiles;
+  const int64_t uO = a.o_bat && !a.o_bout ? (int64_t)a.Bp * 8 : 8;
+  const int64_t bstrideO = a.o_bout ? ((int64_t)8 << a.o_rank) : 8;
+  for (int j = tid; j < NT; j += 256) colO[j] = lin_bits((uint64_t)(tn * NT + j), a.nO, a.nN) * uO;
+  if (tid == 0) abort_flag = 0;
+  float sa, sb;
+  int ea, eb;
+  operand_scale(meta, a.a_meta, hdr, &sa, &ea);
+  operand_scale(meta, a.b_meta, hdr, &sb, &eb);
+  if (blockIdx.x == 0 && tid == 0)
+    meta[a.o_meta].exp = ea + eb + (a.a_meta >= 0 ? meta[a.a_meta].exp : 0) + (a.b_meta >= 0 ? meta[a.b_meta].exp : 0);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tbase)),
+                 "r"(COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < S; ++i) {
+      // the N side's bulk copy (one arrival with its bytes) and 128 converters
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar_full[i])), "r"(1 + TC_M));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_empty[i])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_done)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tbase;
+  const uint32_t s0 = smem_u32(tsm);
+  const int64_t kc = a.kc;
+  if (warp == 0) {
+    if (lane == 0) {
+      const char *srcB = ws + a.pn_off + (sidx * a.ntiles + tn) * kc * BBYTES;
+      for (int64_t k = 0; k < kc; ++k) {
+        const int st = (int)(k % S);
+        if (k >= S && !tc_wait(smem_u32(&bar_empty[st]), (uint32_t)((k / S) - 1) & 1u)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        if (*(volatile int *)&abort_flag) break;
+        const uint32_t fb = smem_u32(&bar_full[st]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(fb), "r"(BBYTES) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                s0 + st * SBYTES + ABYTES),
+            "l"(srcB + k * BBYTES), "r"(BBYTES), "r"(fb)
+            : "memory");
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t fmt = P == 4 ? 0u : 1u;
+      constexpr uint32_t idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(NT >> 3) << 17) |
+                                 ((uint32_t)(TC_M >> 4) << 24);
+      constexpr uint32_t idesc_neg = idesc | (1u << 13);
+      for (int64_t k = 0; k < kc; ++k) {
+        const int st = (int)(k % S);
+        if (!tc_wait(smem_u32(&bar_full[st]), (uint32_t)(k / S) & 1u)) {
+          atomicExch(&abort_flag, 1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sA = s0 + st * SBYTES, sB = sA + ABYTES;
+        uint32_t acc = k > 0 ? 1u : 0u;
+        if (P == 4) {
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            const int i = t == 2 ? 1 : 0, j = t == 1 ? 1 : 0;
+            const uint64_t ar = tc_desc(sA + i * tc_plane_bytes(TC_M)), ai = tc_desc(sA + (2 + i) * tc_plane_bytes(TC_M));
+            const uint64_t br = tc_desc(sB + j * tc_plane_bytes(NT)), bi = tc_desc(sB + (2 + j) * tc_plane_bytes(NT));
+            tc_mma(tmem, ar, br, idesc, acc);
+            tc_mma(tmem, ai, bi, idesc_neg, 1u);
+            tc_mma(tmem + NT, ar, bi, idesc, acc);
+            tc_mma(tmem + NT, ai, br, idesc, 1u);
+            acc = 1u;
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < 6; ++t) {
+            const int i = t == 2 || t == 4 ? 1 : t == 5 ? 2 : 0;
+            const int j = t == 1 || t == 4 ? 1 : t == 3 ? 2 : 0;
+            const uint64_t ar = tc_desc(sA + i * tc_plane_bytes(TC_M)), ai = tc_desc(sA + (3 + i) * tc_plane_bytes(TC_M));
+            const uint64_t br = tc_desc(sB + j * tc_plane_bytes(NT)), bi = tc_desc(sB + (3 + j) * tc_plane_bytes(NT));
+            tc_mma(tmem, ar, br, idesc, acc);
+            tc_mma(tmem, ai, bi, idesc_neg, 1u);
+            tc_mma(tmem + NT, ar, bi, idesc, acc);
+            tc_mma(tmem + NT, ai, br, idesc, 1u);
+            acc = 1u;
+          }
+        }
+        tc_commit(smem_u32(&bar_empty[st]));
+      }
+      tc_commit(smem_u32(&bar_done));
+    }
+    __syncwarp();
+  } else if (warp >= 4) {
+    // converters: row r of the M tile
+    const int r = tid - 128;
+    const int64_t rho = tm * TC_M + r;
+    const bool live = rho < a.mrows;
+    const int64_t m = a.fold ? rho / a.Bp : rho, beta = a.fold ? rho % a.Bp : 0;
+    const int64_t uA = a.a_batched && !a.a_bout ? (int64_t)a.Bp * 8 : 8;
+    const int64_t bstrideA = a.a_bout ? ((int64_t)8 << a.a_rank) : 8;
+    const char *rowA = ws + a.a_src_off +
+                       (lin_bits((uint64_t)sidx, a.sA, a.ns) + lin_bits((uint64_t)(live ? m : 0), a.mA, a.nM)) * uA +
+                       (a.a_batched ? beta * bstrideA : 0);
+    const float sc = P == 4 ? sa * 32768.f : sa;
+    const int klow = a.nk < 4 ? a.nk : 4;  // summed variables inside a chunk of 16
+    const int64_t K = (int64_t)1 << a.nk;
+    int64_t klo[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) klo[q] = q < (1 << klow) ? lin_bits((uint64_t)q, a.kA, klow) * uA : 0;
+    auto gather = [&](int64_t k, float2 (&v)[16]) {
+      const char *h = rowA + lin_bits((uint64_t)(k * 16), a.kA, a.nk) * uA;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        if (live && q < K) {
+          const float2 x = __ldg(reinterpret_cast<const float2 *>(h + klo[q]));
+          v[q] = make_float2(x.x * sc, x.y * sc);
+        } else {
+          v[q] = make_float2(0.f, 0.f);
+        }
+      }
+    };
+    bool ok = true;
+    auto put = [&](int64_t k, const float2 (&v)[16]) {
+      const int st = (int)(k % S);
+      if (k >= S && !tc_wait(smem_u32(&bar_empty[st]), (uint32_t)((k / S) - 1) & 1u)) {
+        atomicExch(&abort_flag, 1);
+        ok = false;
+        return;
+      }
+      conv_put<P>(tsm + st * SBYTES, r, v);
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_full[st])) : "memory");
+    };
+    float2 v0[16], v1[16];
+    gather(0, v0);
+    if (kc > 1) gather(1, v1);
+    for (int64_t k = 0; k < kc && ok; k += 2) {
+      put(k, v0);
+      if (!ok) break;
+      if (k + 2 < kc) gather(k + 2, v0);
+      if (k + 1 < kc) {
+        put(k + 1, v1);
+        if (!ok) break;
+        if (k + 3 < kc) gather(k + 3, v1);
+      }
+    }
+  }
+  // epilogue: warps 4-7, thread tid - 128 = tile row = tensor-memory lane
+  bool ok = tc_wait(smem_u32(&bar_done), 0u);
+  if (!ok) ok = tc_wait(smem_u32(&bar_done), 0u);
+  const bool valid_run = ok && !*(volatile int *)&abort_flag;
+  float lmax = 0.f;
+  if (ok && warp >= 4) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int64_t rho = tm * TC_M + (tid - 128);
+    const bool valid = valid_run && rho < a.mrows;
+    int64_t m = rho, b2 = 0;
+    if (a.fold) {
+      m = rho / a.Bp;
+      b2 = rho % a.Bp;
+    }
+    char *orow = ws + a.o_off +
+                 (lin_bits((uint64_t)sidx, a.sO, a.ns) + lin_bits((uint64_t)(valid ? m : 0), a.mO, a.nM)) * uO +
+                 (a.o_bat ? b2 * bstrideO : 0);
+    const uint32_t tl = tmem + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll 1
     for (int c0 = 0; c0 < NT; c0 += 16) {
       uint32_t re[16], im[16];
@@ -1625,11 +1889,14 @@ static void launch_leaves(qgm_plan *p, const uint64_t *d_bits, int64_t B, cudaSt
 static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c, int64_t planes_off, int P,
                            Meta *meta, Header *hdr, cudaStream_t st, cudaEvent_t mid = nullptr) {
   if (c.swap) gemm_swap_roles(g);
-  for (int side = 0; side < 2; ++side) {
+  // folded steps convert the M side inside the product kernel: only the N
+  // side is split (and its planes start the region)
+  const int64_t pn_off = planes_off + (c.fold ? 0 : c.bytesM);
+  for (int side = c.fold ? 1 : 0; side < 2; ++side) {
     const bool ms = side == 0;
     SplitArgs s{};
     s.src_off = ms ? g.a_off : g.b_off;
-    s.dst_off = planes_off + (ms ? 0 : c.bytesM);
+    s.dst_off = ms ? planes_off : pn_off;
     s.meta = ms ? g.a_meta : g.b_meta;
     s.batched = ms ? g.a_bat : g.b_bat;
     s.fold = ms && c.fold;
@@ -1643,6 +1910,8 @@ static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c
     s.rtiles = ms ? c.mtiles : c.ntiles;
     s.kc = c.kc;
     s.fp16 = P == 4;
+    s.bout = ms ? g.a_bout : g.b_bout;
+    s.rank = (ms ? g.nm : g.nn) + g.nk + g.ns;
     std::memcpy(s.rX, ms ? g.mA : g.nB, GMAXB);
     std::memcpy(s.kX, ms ? g.kA : g.kB, GMAXB);
     std::memcpy(s.sX, ms ? g.sA : g.sB, GMAXB);
@@ -1654,7 +1923,7 @@ static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c
   if (mid) cudaEventRecord(mid, st);
   TcArgs a{};
   a.pm_off = planes_off;
-  a.pn_off = planes_off + c.bytesM;
+  a.pn_off = pn_off;
   a.o_off = g.o_off;
   a.a_meta = g.a_meta;
   a.b_meta = g.b_meta;
@@ -1663,6 +1932,8 @@ static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c
   a.fold = c.fold;
   a.perbeta = c.perbeta;
   a.Bp = Bp;
+  a.o_bout = g.o_bout;
+  a.o_rank = g.nm + g.nn + g.ns;
   a.nM = g.nm;
   a.nN = g.nn;
   a.ns = g.ns;
@@ -1674,7 +1945,32 @@ static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c
   std::memcpy(a.mO, g.mO, GMAXB);
   std::memcpy(a.nO, g.nO, GMAXB);
   std::memcpy(a.sO, g.sO, GMAXB);
+  a.a_src_off = g.a_off;
+  a.a_batched = g.a_bat;
+  a.a_bout = g.a_bout;
+  a.a_rank = g.nm + g.nk + g.ns;
+  a.nk = g.nk;
+  std::memcpy(a.mA, g.mA, GMAXB);
+  std::memcpy(a.kA, g.kA, GMAXB);
+  std::memcpy(a.sA, g.sA, GMAXB);
   const unsigned grid = (unsigned)(c.inst * c.mtiles * c.ntiles);
+  if (c.fold) {
+#define QGM_TC_CONV(NT_, P_) \
+  k_gemm_tc_conv<NT_, P_><<<grid, 256, tc_smem_bytes(NT_, P_), st>>>(ws, a, meta, hdr)
+    if (P == 4) {
+      if (c.nt == 256) QGM_TC_CONV(256, 4);
+      else if (c.nt == 128) QGM_TC_CONV(128, 4);
+      else if (c.nt == 64) QGM_TC_CONV(64, 4);
+      else QGM_TC_CONV(32, 4);
+    } else {
+      if (c.nt == 256) QGM_TC_CONV(256, 6);
+      else if (c.nt == 128) QGM_TC_CONV(128, 6);
+      else if (c.nt == 64) QGM_TC_CONV(64, 6);
+      else QGM_TC_CONV(32, 6);
+    }
+#undef QGM_TC_CONV
+    return;
+  }
 #define QGM_TC_LAUNCH(NT_, P_) \
   k_gemm_tc<NT_, P_><<<grid, 128, tc_smem_bytes(NT_, P_), st>>>(ws, a, meta, hdr)
   if (P == 4) {
@@ -1697,6 +1993,19 @@ static cudaError_t tc_set_smem() {
 #define QGM_TC_ATTR(NT_, P_)                                                                                  \
   if (e == cudaSuccess)                                                                                       \
   e = cudaFuncSetAttribute(k_gemm_tc<NT_, P_>, cudaFuncAttributeMaxDynamicSharedMemorySize, tc_smem_bytes(NT_, P_))
+  QGM_TC_ATTR(256, 4);
+  QGM_TC_ATTR(128, 4);
+  QGM_TC_ATTR(64, 4);
+  QGM_TC_ATTR(32, 4);
+  QGM_TC_ATTR(256, 6);
+  QGM_TC_ATTR(128, 6);
+  QGM_TC_ATTR(64, 6);
+  QGM_TC_ATTR(32, 6);
+#undef QGM_TC_ATTR
+#define QGM_TC_ATTR(NT_, P_)                                                                                  \
+  if (e == cudaSuccess)                                                                                       \
+  e = cudaFuncSetAttribute(k_gemm_tc_conv<NT_, P_>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
+                           tc_smem_bytes(NT_, P_))
   QGM_TC_ATTR(256, 4);
   QGM_TC_ATTR(128, 4);
   QGM_TC_ATTR(64, 4);
@@ -2717,6 +3026,12 @@ extern "C" int qgm_amplitudes_static(qgm_plan *p, const uint64_t *d_bitstrings, 
     set_error("qgm_amplitudes_static: needs a batch plan and 1 <= B <= %lld", (long long)p->batch);
     return QGM_ERR_ARG;
   }
+  for (const GemmDesc &g : p->gemms)
+    if (g.a_bout || g.b_bout || g.o_bout) {
+      set_error("qgm_amplitudes_static: the plan keeps batch-outer intermediates for its tensor-core steps "
+                "(larger than the static scratch); use qgm_plan_bind");
+      return QGM_ERR_OOM;
+    }
   if (p->ws_fwd_bytes > (int64_t)QGM_STATIC_SCRATCH_BYTES) {
     set_error("qgm_amplitudes_static: the plan needs %lld bytes of scratch, more than the %llu-byte "
               "static scratch; use qgm_plan_bind with a caller-allocated workspace",

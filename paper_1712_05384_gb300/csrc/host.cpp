@@ -1726,6 +1726,32 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     }
     p->steps.push_back(d);
   }
+  // batch-outer intermediates: the output of a tensor-core product per batch
+  // entry whose only reader is another tensor-core step's operand split (each
+  // entry's stores are then contiguous instead of 8 bytes in every 32-byte
+  // sector); large tensors only, none in a gradient layout (its product-sum
+  // kernels read batch-inner rows)
+  if (p->gemm_tc && !p->grad) {
+    std::vector<int> consumer(S.tensors.size(), -1);
+    for (size_t si = 0; si < S.steps.size(); ++si)
+      for (int id : S.steps[si].inputs) consumer[id] = (int)si;
+    for (size_t si = 0; si < S.steps.size(); ++si) {
+      const StepDesc &d = p->steps[si];
+      if (d.gemm < 0) continue;
+      GemmDesc &g = p->gemms[d.gemm];
+      const TcCfg c = tc_config(g, (int)Bp, p->tc_planes);
+      const int out = S.steps[si].out;
+      if (!c.ok || !c.perbeta || S.tensors[out].entries < ((int64_t)1 << 24)) continue;
+      const int cs = consumer[out];
+      if (cs < 0 || p->steps[cs].gemm < 0) continue;
+      GemmDesc &h = p->gemms[p->steps[cs].gemm];
+      if (!tc_config(h, (int)Bp, p->tc_planes).ok) continue;
+      if (h.a_off == g.o_off) h.a_bout = 1;
+      else if (h.b_off == g.o_off) h.b_bout = 1;
+      else continue;
+      g.o_bout = 1;
+    }
+  }
   p->tune.assign(p->steps.size(), StepTune{});
   // the split operand planes of the largest tensor-core step, after the arena
   p->ws_fwd_bytes = p->ws_bytes;
@@ -1733,7 +1759,8 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   if (p->gemm_tc)
     for (const GemmDesc &g : p->gemms) {
       const TcCfg c = tc_config(g, (int)Bp, p->tc_planes);
-      if (c.ok) p->planes_bytes = std::max(p->planes_bytes, c.bytesM + c.bytesN);
+      // a folded step converts its M side in the product kernel: N planes only
+      if (c.ok) p->planes_bytes = std::max(p->planes_bytes, (c.fold ? 0 : c.bytesM) + c.bytesN);
     }
   p->off_planes = p->ws_bytes - 256;
   p->ws_bytes = p->off_planes + p->planes_bytes + 256;
@@ -2324,7 +2351,7 @@ int qgm_plan_get_gemm(const qgm_plan *p, int32_t *rec, int64_t cap, int64_t *n) 
     if (d.gemm < 0) continue;
     if (rec && c < cap) {
       const GemmDesc &g = p->gemms[d.gemm];
-      int32_t *r = rec + 9 * c;
+      int32_t *r = rec + 11 * c;
       r[0] = (int32_t)s;
       r[1] = g.nm;
       r[2] = g.nn;
@@ -2334,6 +2361,8 @@ int qgm_plan_get_gemm(const qgm_plan *p, int32_t *rec, int64_t cap, int64_t *n) 
       r[6] = g.b_bat;
       r[7] = g.o_bat;
       r[8] = p->gemm_tc && gemm_tc_eligible(g, p->Bp) ? 1 : 0;
+      r[9] = g.o_bout;
+      r[10] = g.a_bout | g.b_bout;
     }
     ++c;
   }

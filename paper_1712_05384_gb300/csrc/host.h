@@ -90,6 +90,10 @@ struct GemmDesc {
   int32_t a_meta, b_meta, o_meta;
   int32_t a_bat, b_bat, o_bat;
   int32_t nm, nn, nk, ns;
+  // batch entry outermost (a tensor written by one tensor-core product per
+  // entry and read only by another tensor-core step): entry beta's values
+  // are a whole tensor of 2^rank complex64 at beta * 2^rank * 8 bytes
+  int32_t a_bout, b_bout, o_bout;
   uint8_t mA[GMAXB], mO[GMAXB], nB[GMAXB], nO[GMAXB];
   uint8_t kA[GMAXB], kB[GMAXB], sA[GMAXB], sB[GMAXB], sO[GMAXB];
 };
@@ -100,6 +104,7 @@ inline void gemm_swap_roles(GemmDesc &g) {
   std::swap(g.a_off, g.b_off);
   std::swap(g.a_meta, g.b_meta);
   std::swap(g.a_bat, g.b_bat);
+  std::swap(g.a_bout, g.b_bout);
   std::swap(g.nm, g.nn);
   for (int b = 0; b < GMAXB; ++b) {
     std::swap(g.mA[b], g.nB[b]);

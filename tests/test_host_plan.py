@@ -338,3 +338,21 @@ def test_torch_complex_gradient_convention():
     a = (1 + 2j) * p.to(torch.complex128)
     (a * a.conj()).real.backward()
     assert abs(p.grad.item() - 10.0) < 1e-12
+
+
+def test_batch_outer_intermediates():
+    # a product per batch entry on the tensor cores whose output only another
+    # tensor-core step reads keeps the batch entry outermost: on 5x9 depth 40
+    # (4 bitstrings) the two large per-entry products feed folded GEMMs
+    m = Q.Model(Q.Circuit.grid(5, 9, 40, 0))
+    gs = Q.Plan(m, order_kind=1, batch=4, executor=Q.EXEC_STEPWISE).gemm_shapes()
+    prod = [g for g in gs if g["o_bout"]]
+    cons = [g for g in gs if g["in_bout"]]
+    assert len(prod) == len(cons) == 2
+    for g in prod:
+        assert g["tc"] and g["a_bat"] and g["b_bat"]
+    # never with the FP32-core GEMM (no tensor-core steps) or a gradient layout
+    for kw in ({"precision": "fp32"}, {"gradients": True, "batch": 2}):
+        kw = dict({"batch": 4}, **kw)
+        p = Q.Plan(Q.Model(Q.Circuit.grid(4, 6, 30, 0)), order_kind=1, executor=Q.EXEC_STEPWISE, **kw)
+        assert not any(g["o_bout"] or g["in_bout"] for g in p.gemm_shapes())
