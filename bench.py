@@ -187,7 +187,8 @@ def cpu_oracle_sample(workload, c, bits):
     entries on every host core) on a bounded sample: (amplitudes/s, sample
     description, cores).  5x9 depth 40: one of the 2^7 conditioned parts of
     one bitstring (the oracle slices it to fit host memory), scaled to a
-    whole amplitude; smaller circuits: whole amplitudes for about 10 s."""
+    whole amplitude; smaller circuits: whole amplitudes for about 10 s on a
+    pool of threads over bitstrings."""
     from oracle import order as O
     from oracle import ugm, vec
     cores = os.cpu_count() or 1
@@ -209,11 +210,12 @@ def cpu_oracle_sample(workload, c, bits):
     t0 = time.perf_counter()
     done = 0
     while done < len(bits) and time.perf_counter() - t0 < 10.0:
-        vec.amplitude(c, int(bits[done]), order=order, model=m, prepared=pr)
-        done += 1
+        chunk = bits[done:done + 4 * cores]
+        vec.amplitudes_parallel(c, chunk, order=order, model=m, prepared=pr, workers=cores)
+        done += len(chunk)
     dt = time.perf_counter() - t0
     return done / dt, (f"{done} bitstrings in {dt:.1f} s; oracle/ve.c FP64 bucket elimination, min-fill "
-                       f"order, {cores} threads"), cores
+                       f"order, a pool of {cores} host threads over bitstrings"), cores
 
 
 def _one_slice(m, pr, order, slice_vars, x):

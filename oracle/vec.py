@@ -132,3 +132,19 @@ def amplitude_derivative(circuit, x, p, which, order=None, model=None, prepared=
         return amplitude(circuit, x, order=order, model=m, prepared=pr, threads=threads)
     finally:
         pr.tables[:] = saved
+
+
+def amplitudes_parallel(circuit, xs, order=None, model=None, prepared=None, workers=0):
+    """<x|C|0^n> for every x of ``xs``, one elimination per bitstring on a
+    pool of ``workers`` host threads (default: every core), each elimination
+    single-threaded (the C call releases the GIL)."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    m = model or ugm.build(circuit)
+    pr = prepared or Prepared(m)
+    if order is None:
+        order, _ = O.min_fill(free_graph(m))
+    workers = workers or os.cpu_count() or 1
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return np.array(list(ex.map(lambda x: amplitude(circuit, int(x), order=order, model=m, prepared=pr,
+                                                        threads=1), xs)))
