@@ -190,7 +190,10 @@ typedef struct {
   int32_t autotune;           /* 1: qgm_plan_bind times the candidate launch
                                  parameters of every step that has several (the
                                  tensor-core GEMM's N tile: 256, 128 or 64
-                                 columns; the batched product-sum kernel's term
+                                 columns, and for a folded step whether its
+                                 streamed operand is split in a pass of its own
+                                 or inside the product kernel; the batched
+                                 product-sum kernel's term
                                  groups: 1, 2 or 4) on the bound device, on
                                  tensors from one pass over an all-zero batch,
                                  and keeps the fastest; 0: fixed rules */
@@ -217,6 +220,11 @@ typedef struct {
                                  intermediate table of App. D, see
                                  qgm_eliminate_fixed) */
   const int32_t *keep_vars;   /* n_keep variable ids (copied at plan time) */
+  int32_t tc_convert;         /* tensor-core steps whose batch entries are rows
+                                 of M (one operand batch-free): 1 converts the
+                                 batched operand to its 16-bit terms inside the
+                                 product kernel, 0 (default) in a split pass of
+                                 its own; with autotune on, the faster per step */
 } qgm_plan_opts;
 
 enum {
@@ -281,7 +289,9 @@ int qgm_plan_get_step_inputs(const qgm_plan *p, int32_t step, int32_t *rec, int6
 
 /* Autotuner choices (qgm_plan_opts.autotune, after qgm_plan_bind): for the
  * c-th tuned step, rec[4c .. 4c+3] = step index, tensor-core N tile cap (0:
- * not a tensor-core step), product-sum term groups (0: not tuned), and
+ * not a tensor-core step), product-sum term groups (0: not tuned), 1 when a
+ * folded tensor-core step converts its streamed operand inside the product
+ * kernel (instead of a separate split pass), and
  * ms[2c], ms[2c+1] = milliseconds with the fixed rules and with the choice.
  * *n = the number of tuned steps; rec/ms may be NULL to query it. */
 int qgm_plan_get_tuning(const qgm_plan *p, int32_t *rec, float *ms, int64_t cap, int64_t *n);

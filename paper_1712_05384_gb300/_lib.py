@@ -41,7 +41,7 @@ class qgm_plan_opts(C.Structure):
                 ("no_gemm", C.c_int32), ("gradients", C.c_int32), ("trees", C.c_int32),
                 ("open_mask", C.c_uint64),
                 ("resident_chunk", C.c_int32), ("autotune", C.c_int32), ("gemm_precision", C.c_int32),
-                ("n_keep", C.c_int32), ("keep_vars", C.POINTER(C.c_int32))]
+                ("n_keep", C.c_int32), ("keep_vars", C.POINTER(C.c_int32)), ("tc_convert", C.c_int32)]
 
 
 class qgm_xeb_result(C.Structure):
@@ -257,7 +257,7 @@ class Plan:
     def __init__(self, model: Model, order_kind=ORDER_AUTO, output_mode=OUT_BATCH, batch=1,
                  mem_budget_bytes=0, max_fuse=0, order=None, executor=EXEC_AUTO,
                  resident_chunk=0, gradients=False, gemm=True, open_mask=0, trees=None,
-                 split_bf16=None, precision=None, autotune=False, keep_vars=None):
+                 split_bf16=None, precision=None, autotune=False, keep_vars=None, tc_convert=False):
         self.model = model
         o = qgm_plan_opts()
         o.order_kind = order_kind
@@ -278,6 +278,9 @@ class Plan:
             precision = "bf16" if split_bf16 else "fp32"
         o.gemm_precision = {None: 0, "fp16": 2, "bf16": 1, "fp32": -1}[precision]
         o.autotune = 1 if autotune else 0
+        # folded tensor-core steps convert their batched operand inside the
+        # product kernel (else in a split pass of their own)
+        o.tc_convert = 1 if tc_convert else 0
         self._keep_buf = None
         if keep_vars is not None and len(keep_vars):
             self._keep_buf = np.ascontiguousarray(keep_vars, dtype=np.int32)
@@ -353,7 +356,7 @@ class Plan:
         return U, k, ins
 
     def tuning(self):
-        """Autotuner choices after bind: list of dicts (step, nt_cap, T,
+        """Autotuner choices after bind: list of dicts (step, nt_cap, T, conv,
         ms_rule, ms_best)."""
         n = C.c_int64()
         check(lib().qgm_plan_get_tuning(self._h, None, None, 0, C.byref(n)))
@@ -362,7 +365,8 @@ class Plan:
         check(lib().qgm_plan_get_tuning(self._h, r.ctypes.data_as(_I32P), m.ctypes.data_as(C.POINTER(C.c_float)),
                                         n.value, C.byref(n)))
         return [{"step": int(r[4 * c]), "nt_cap": int(r[4 * c + 1]), "T": int(r[4 * c + 2]),
-                 "ms_rule": float(m[2 * c]), "ms_best": float(m[2 * c + 1])} for c in range(n.value)]
+                 "conv": int(r[4 * c + 3]), "ms_rule": float(m[2 * c]), "ms_best": float(m[2 * c + 1])}
+                for c in range(n.value)]
 
     def gemm_shapes(self):
         """GEMM-shaped steps: list of dicts (step, nm, nn, nk, ns, a_bat,

@@ -1887,12 +1887,13 @@ static void launch_leaves(qgm_plan *p, const uint64_t *d_bits, int64_t B, cudaSt
 // Tensor-core form of a GEMM-shaped step: split both operands into planes,
 // then the product (see k_split and k_gemm_tc).
 static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c, int64_t planes_off, int P,
-                           Meta *meta, Header *hdr, cudaStream_t st, cudaEvent_t mid = nullptr) {
+                           Meta *meta, Header *hdr, cudaStream_t st, cudaEvent_t mid = nullptr, bool conv = false) {
   if (c.swap) gemm_swap_roles(g);
-  // folded steps convert the M side inside the product kernel: only the N
-  // side is split (and its planes start the region)
-  const int64_t pn_off = planes_off + (c.fold ? 0 : c.bytesM);
-  for (int side = c.fold ? 1 : 0; side < 2; ++side) {
+  // a folded step may convert its M side inside the product kernel (then
+  // only the N side is split)
+  conv = conv && c.fold;
+  const int64_t pn_off = planes_off + c.bytesM;
+  for (int side = conv ? 1 : 0; side < 2; ++side) {
     const bool ms = side == 0;
     SplitArgs s{};
     s.src_off = ms ? g.a_off : g.b_off;
@@ -1954,7 +1955,7 @@ static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c
   std::memcpy(a.kA, g.kA, GMAXB);
   std::memcpy(a.sA, g.sA, GMAXB);
   const unsigned grid = (unsigned)(c.inst * c.mtiles * c.ntiles);
-  if (c.fold) {
+  if (conv) {
 #define QGM_TC_CONV(NT_, P_) \
   k_gemm_tc_conv<NT_, P_><<<grid, 256, tc_smem_bytes(NT_, P_), st>>>(ws, a, meta, hdr)
     if (P == 4) {
@@ -2025,7 +2026,7 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
   if (d.gemm >= 0 && gemms && tc) {
     const TcCfg c = tc_config(gemms[d.gemm], Bp, planes, tn && tn->nt_cap ? tn->nt_cap : 256);
     if (c.ok) {
-      launch_gemm_tc(ws, sms, Bp, gemms[d.gemm], c, planes_off, planes, meta, hdr, st, mid);
+      launch_gemm_tc(ws, sms, Bp, gemms[d.gemm], c, planes_off, planes, meta, hdr, st, mid, tn && tn->conv);
       return;
     }
   }
@@ -2103,7 +2104,9 @@ static void launch_step(qgm_plan *p, const StepDesc &d, cudaStream_t st, cudaEve
                  tune_of(p, d));
 }
 
-// Autotuner (qgm_plan_opts.autotune): one pass over an all-zero batch puts
+// Autotuner (qgm_plan_opts.autotune; candidates: the tensor-core N tile, for
+// folded steps in-kernel conversion of the M side, the product-sum term
+// groups): one pass over an all-zero batch puts
 // real tensors in the workspace; then, step by step in order, every
 // candidate launch configuration of a step with several is run once to
 // warm up and three times under CUDA events, and the fastest is kept (the
@@ -2137,13 +2140,15 @@ static int autotune(qgm_plan *p, cudaStream_t st) {
     StepTune &tn = p->tune[si];
     std::vector<StepTune> cand;
     if (d.gemm >= 0 && p->gemm_tc && tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes).ok) {
-      const int wide = tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes).nt;
-      for (int cap : {256, 128, 64})
-        if (cap <= wide) {
-          StepTune t;
-          t.nt_cap = cap;
-          cand.push_back(t);
-        }
+      const TcCfg tcc = tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes);
+      for (int conv = 0; conv <= (tcc.fold ? 1 : 0); ++conv)
+        for (int cap : {256, 128, 64})
+          if (cap <= tcc.nt) {
+            StepTune t;
+            t.nt_cap = cap;
+            t.conv = conv;
+            cand.push_back(t);
+          }
     } else if (d.gemm < 0 && d.batched_out && d.tile_t == 0) {
       for (int T : {1, 2, 4})
         if (T <= (1 << std::min(d.k, 4))) {
@@ -2154,11 +2159,13 @@ static int autotune(qgm_plan *p, cudaStream_t st) {
     }
     if (cand.size() < 2) continue;
     float ms_rule = 0.f;
-    tn = StepTune{};
+    StepTune rule{};
+    rule.conv = p->opts.tc_convert ? 1 : 0;
+    tn = rule;
     int rc = time_step(d, &ms_rule);
     if (rc) return rc;
     if (ms_rule < 0.05f) continue;
-    StepTune best{};
+    StepTune best = rule;
     float best_ms = ms_rule;
     for (const StepTune &c : cand) {
       tn = c;
@@ -2374,7 +2381,10 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
   // chunk size by fewest waves x chunk
   x->kind = QGM_EXEC_STEPWISE;
   x->layout = -1;
-  for (StepTune &t : p->tune) t = StepTune{};
+  for (StepTune &t : p->tune) {
+    t = StepTune{};
+    t.conv = p->opts.tc_convert ? 1 : 0;
+  }
   if (p->executor_pref == QGM_EXEC_STEPWISE || p->resident.empty()) {
     if (p->executor_pref == QGM_EXEC_RESIDENT || p->executor_pref == QGM_EXEC_COMPILED) {
       set_error("qgm_plan_bind: this plan has no resident layout (one slice, batch outputs only)");

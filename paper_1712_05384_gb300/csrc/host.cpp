@@ -1759,8 +1759,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
   if (p->gemm_tc)
     for (const GemmDesc &g : p->gemms) {
       const TcCfg c = tc_config(g, (int)Bp, p->tc_planes);
-      // a folded step converts its M side in the product kernel: N planes only
-      if (c.ok) p->planes_bytes = std::max(p->planes_bytes, (c.fold ? 0 : c.bytesM) + c.bytesN);
+      if (c.ok) p->planes_bytes = std::max(p->planes_bytes, c.bytesM + c.bytesN);
     }
   p->off_planes = p->ws_bytes - 256;
   p->ws_bytes = p->off_planes + p->planes_bytes + 256;
@@ -2327,7 +2326,7 @@ int qgm_plan_get_tuning(const qgm_plan *p, int32_t *rec, float *ms, int64_t cap,
         rec[4 * c] = (int32_t)s;
         rec[4 * c + 1] = t.nt_cap;
         rec[4 * c + 2] = t.T;
-        rec[4 * c + 3] = 0;
+        rec[4 * c + 3] = t.conv;
       }
       if (ms) {
         ms[2 * c] = t.ms_rule;

@@ -104,6 +104,27 @@ def test_split_narrow_tiles_with_wide_batch(precision):
     assert rel < SPLIT_TOL and ab < SPLIT_TOL, (rel, ab)
 
 
+@pytest.mark.parametrize("precision", PRECISIONS)
+def test_in_kernel_conversion_matches_split_pass(precision):
+    # folded steps (batch entries as rows of M): converting the batched
+    # operand inside the product kernel gives the same terms as the split
+    # pass, so the same bits; 4x6 d34 against the oracle, 4x8 d40 pairwise
+    q = Q()
+    c = qi.grid_circuit(4, 6, 34, 0)
+    bits = qi.bitstrings(c.n, 6, 0)
+    m = q.Model(q.Circuit.grid(4, 6, 34, 0))
+    a = q.Plan(m, order_kind=1, batch=6, executor=1, precision=precision, tc_convert=True).bind()
+    b = q.Plan(m, order_kind=1, batch=6, executor=1, precision=precision).bind()
+    assert np.array_equal(a.amplitudes_host(bits), b.amplitudes_host(bits))
+    rel, ab = errors(a.amplitudes_host(bits), sv.amplitudes(c, bits), c.n)
+    assert rel < SPLIT_TOL and ab < SPLIT_TOL, (rel, ab)
+    m = q.Model(q.Circuit.grid(4, 8, 40, 0))
+    bits = qi.bitstrings(32, 4, 0)
+    a = q.Plan(m, order_kind=1, batch=4, precision=precision, tc_convert=True).bind().amplitudes_host(bits)
+    b = q.Plan(m, order_kind=1, batch=4, precision=precision).bind().amplitudes_host(bits)
+    assert np.array_equal(a, b)
+
+
 def test_repeat_calls_are_identical():
     # the planes are rewritten on every call: two calls give the same bits
     q = Q()
