@@ -402,6 +402,14 @@ int qgm_plan_step_stats(qgm_plan *p, uint32_t *maxbits, int32_t *exps, int64_t c
  * which kernels bound by FP32 arithmetic are reported.  Synchronises. */
 int qgm_measure_fp32_peak(double *tflops, void *stream);
 
+/* Failure-detection self-test (no counterpart in the paper): runs the
+ * bounded mbarrier wait every tensor-core kernel uses, on one barrier with an
+ * arrival count of 1.  arrive = 0: nothing arrives, the wait gives up after
+ * limit_ns (1 us .. 2 s, else QGM_ERR_ARG) and *status_out = QGM_ERR_TIMEOUT;
+ * arrive = 1: the waiting thread arrives first and *status_out = QGM_OK.  The
+ * context stays usable either way.  Host int32 out; synchronises. */
+int qgm_selftest_wait_timeout(int64_t limit_ns, int32_t arrive, int32_t *status_out, void *stream);
+
 /* Executor chosen at bind time:/* Executor chosen at bind time: *kind (QGM_EXEC_STEPWISE, _RESIDENT or
  * _COMPILED), the bitstrings per CTA *chunk and the dynamic shared memory per
  * CTA (resident and compiled). */

@@ -99,6 +99,7 @@ _SIGS = {
     "qgm_plan_profile": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), _P],
     "qgm_plan_profile_gemm": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), C.POINTER(C.c_float), _P],
     "qgm_measure_fp32_peak": [C.POINTER(C.c_double), _P],
+    "qgm_selftest_wait_timeout": [C.c_int64, C.c_int32, _I32P, _P],
     "qgm_plan_step_stats": [_P, C.POINTER(C.c_uint32), _I32P, C.c_int64, _P],
     "qgm_plan_free": [_P],
     "qgm_plan_bind": [_P, _P, C.c_size_t, _P],

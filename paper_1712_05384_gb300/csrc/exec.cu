@@ -772,7 +772,7 @@ __device__ __forceinline__ uint64_t gtimer() {
 
 // Wait (about one second at most) for the completion of the mbarrier phase
 // of the given parity; false when the limit ran out.
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
+__device__ __forceinline__ bool tc_wait_ns(uint32_t bar, uint32_t parity, uint64_t limit_ns) {
   const uint64_t t0 = gtimer();
   while (true) {
     uint32_t done;
@@ -783,9 +783,11 @@ __device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
-    if (gtimer() - t0 > 1000000000ull) return false;
+    if (gtimer() - t0 > limit_ns) return false;
   }
 }
+
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) { return tc_wait_ns(bar, parity, 1000000000ull); }
 
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
@@ -930,6 +932,7 @@ struct TcArgs {
   int32_t a_meta, b_meta, o_meta; // M side, N side, output
   int32_t o_bat, fold, perbeta, Bp;
   int32_t o_bout, o_rank;         // output batch entry outermost (2^o_rank complex64 per entry)
+  int32_t s_fast;                 // shared index fastest in the grid (its bits share output sectors)
   int32_t nM, nN, ns;
   int64_t mrows, mtiles, ntiles, kc;
   float out_scale;                // undoes the terms' scale: 2^-30 (FP16) or 1
@@ -951,6 +954,24 @@ __host__ __device__ constexpr int tc_stages(int nt, int planes) {
 __host__ __device__ constexpr int tc_smem_bytes(int nt, int planes) {
   return tc_stages(nt, planes) * planes * (tc_plane_bytes(TC_M) + tc_plane_bytes(nt));
 }
+// k_gemm_tc_conv: two plane stages (the converters write one while the MMAs
+// read the other), and as many stages of the raw ring (the M side's
+// complex64 rows of one chunk, 128 bytes per row) as fit in 220 KB, up to 8:
+// the copies run that many chunks ahead of the conversion, several
+// microseconds of MMA time, which covers the DRAM latency under load
+__host__ __device__ constexpr int tcc_stages(int nt, int planes) { return 2; }
+__host__ __device__ constexpr int tcc_raw_stages(int nt, int planes) {
+  return (220 * 1024 - tcc_stages(nt, planes) * planes * (tc_plane_bytes(TC_M) + tc_plane_bytes(nt))) /
+                     (TC_M * 128) < 8
+             ? (220 * 1024 - tcc_stages(nt, planes) * planes * (tc_plane_bytes(TC_M) + tc_plane_bytes(nt))) /
+                   (TC_M * 128)
+             : 8;
+}
+__host__ __device__ constexpr int tcc_smem_bytes(int nt, int planes) {
+  return tcc_stages(nt, planes) * planes * (tc_plane_bytes(TC_M) + tc_plane_bytes(nt)) +
+         tcc_raw_stages(nt, planes) * TC_M * 128;
+}
+static_assert(tcc_smem_bytes(256, 4) <= 220 * 1024 && tcc_smem_bytes(256, 6) <= 220 * 1024, "conv ring");
 
 template <int NT, int P>
 __global__ void __launch_bounds__(128, 1) k_gemm_tc(char *ws, const __grid_constant__ TcArgs a, Meta *meta,
@@ -970,7 +991,13 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(char *ws, const __grid_const
   // tile write the same output sectors, which then merge in L2), then the N
   // tile, the M tile and the shared index
   int64_t bid = blockIdx.x;
-  int64_t beta = 0;
+  int64_t beta = 0, sidx = 0;
+  if (a.s_fast) {
+    // the output's lowest index bits include a shared variable: the tiles of
+    // neighbouring instances fill the same sectors, so they run together
+    sidx = bid & ((1ll << a.ns) - 1);
+    bid >>= a.ns;
+  }
   if (a.perbeta) {
     beta = bid % a.Bp;
     bid /= a.Bp;
@@ -978,7 +1005,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(char *ws, const __grid_const
   const int64_t tn = bid % a.ntiles;
   bid /= a.ntiles;
   const int64_t tm = bid % a.mtiles;
-  const int64_t sidx = bid / a.mtiles;
+  if (!a.s_fast) sidx = bid / a.mtiles;
   const int64_t inst = a.perbeta ? sidx * a.Bp + beta : sidx;
   const int64_t uO = a.o_bat && !a.o_bout ? (int64_t)a.Bp * 8 : 8;
   const int64_t bstrideO = a.o_bout ? ((int64_t)8 << a.o_rank) : 8;  // bytes between batch entries
@@ -1134,14 +1161,14 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(char *ws, const __grid_const
 // that side is the large operand streamed once; splitting it in a separate
 // pass would read and write it once more.  Here 8 warps: warp 0 streams the
 // N side's planes (bulk copies, as k_gemm_tc), warp 1 issues the MMAs, warps
-// 4-7 convert: thread r gathers row r of each chunk (16 complex64 values
-// through the operand's bit maps, two chunks ahead in registers), scales and
-// splits them into the 16-bit planes of the stage (the layout k_split
-// writes), makes the stores visible to the tensor cores (fence.proxy.async)
-// and arrives on the stage's "full" mbarrier, which completes when the 128
-// converters and the N side's bytes are in.  Warps 4-7 then read the
-// accumulators back (TMEM lane quadrant = warp % 4).  Waits are bounded as
-// in k_gemm_tc.
+// 4-7 convert: thread r copies row r of each chunk (16 complex64 values
+// through the operand's bit maps) into a raw ring in shared memory with
+// cp.async, RS - 1 chunks ahead, then scales and splits it into the 16-bit
+// planes of the stage (the layout k_split writes), makes the stores visible
+// to the tensor cores (fence.proxy.async) and arrives on the stage's "full"
+// mbarrier, which completes when the 128 converters and the N side's bytes
+// are in.  Warps 4-7 then read the accumulators back (TMEM lane quadrant =
+// warp % 4).  Waits are bounded as in k_gemm_tc.
 template <int P>
 __device__ __forceinline__ void conv_put(uint8_t *stage, int r, const float2 (&v)[16]) {
   const int pb = tc_plane_bytes(TC_M);
@@ -1178,7 +1205,8 @@ __device__ __forceinline__ void conv_put(uint8_t *stage, int r, const float2 (&v
 template <int NT, int P>
 __global__ void __launch_bounds__(256, 1) k_gemm_tc_conv(char *ws, const __grid_constant__ TcArgs a, Meta *meta,
                                                          Header *hdr) {
-  constexpr int S = tc_stages(NT, P);
+  constexpr int S = tcc_stages(NT, P), RS = tcc_raw_stages(NT, P);
+  static_assert(RS >= 3, "raw ring");
   constexpr int ABYTES = P * tc_plane_bytes(TC_M), BBYTES = P * tc_plane_bytes(NT);
   constexpr int SBYTES = ABYTES + BBYTES;
   constexpr uint32_t COLS = 2 * NT < 32 ? 32 : 2 * NT;
@@ -1190,10 +1218,15 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc_conv(char *ws, const __grid_
   __shared__ int64_t colO[NT];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   int64_t bid = blockIdx.x;
+  int64_t sidx = 0;
+  if (a.s_fast) {
+    sidx = bid & ((1ll << a.ns) - 1);
+    bid >>= a.ns;
+  }
   const int64_t tn = bid % a.ntiles;
   bid /= a.ntiles;
   const int64_t tm = bid % a.mtiles;
-  const int64_t sidx = bid / a.mtiles;
+  if (!a.s_fast) sidx = bid / a.mtiles;
   const int64_t uO = a.o_bat && !a.o_bout ? (int64_t)a.Bp * 8 : 8;
   const int64_t bstrideO = a.o_bout ? ((int64_t)8 << a.o_rank) : 8;
   for (int j = tid; j < NT; j += 256) colO[j] = lin_bits((uint64_t)(tn * NT + j), a.nO, a.nN) * uO;
@@ -1291,7 +1324,11 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc_conv(char *ws, const __grid_
     }
     __syncwarp();
   } else if (warp >= 4) {
-    // converters: row r of the M tile
+    // converters: row r of the M tile.  The raw ring holds, per stage, the
+    // 16 complex64 values of each row for one chunk (128 bytes per row, its
+    // 16-byte pieces rotated by r mod 8 so a quarter-warp's reads hit
+    // distinct banks); each thread fills its own row with 8-byte cp.async
+    // copies RS - 1 chunks ahead, so only its own copy groups are waited on.
     const int r = tid - 128;
     const int64_t rho = tm * TC_M + r;
     const bool live = rho < a.mrows;
@@ -1307,43 +1344,51 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc_conv(char *ws, const __grid_
     int64_t klo[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) klo[q] = q < (1 << klow) ? lin_bits((uint64_t)q, a.kA, klow) * uA : 0;
-    auto gather = [&](int64_t k, float2 (&v)[16]) {
+    uint8_t *raw = tsm + S * SBYTES + r * 128;
+    const uint32_t raw_s = smem_u32(raw);
+    const int rot = r & 7;
+    auto issue = [&](int64_t k) {
+      const int rs = (int)(k % RS);
       const char *h = rowA + lin_bits((uint64_t)(k * 16), a.kA, a.nk) * uA;
 #pragma unroll
       for (int q = 0; q < 16; ++q) {
+        const int slot = rs * TC_M * 128 + (((q >> 1) ^ rot) << 4) + ((q & 1) << 3);
         if (live && q < K) {
-          const float2 x = __ldg(reinterpret_cast<const float2 *>(h + klo[q]));
-          v[q] = make_float2(x.x * sc, x.y * sc);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(raw_s + slot), "l"(h + klo[q]) : "memory");
         } else {
-          v[q] = make_float2(0.f, 0.f);
+          *reinterpret_cast<float2 *>(raw + slot) = make_float2(0.f, 0.f);
         }
       }
+      asm volatile("cp.async.commit_group;" ::: "memory");
     };
-    bool ok = true;
-    auto put = [&](int64_t k, const float2 (&v)[16]) {
+    for (int64_t k = 0; k < RS - 1; ++k) {
+      if (k < kc) issue(k);
+      else asm volatile("cp.async.commit_group;" ::: "memory");
+    }
+    for (int64_t k = 0; k < kc; ++k) {
+      if (k + RS - 1 < kc) issue(k + RS - 1);
+      else asm volatile("cp.async.commit_group;" ::: "memory");
+      // every group but the newest RS - 1 has landed: chunk k's row is in
+      asm volatile("cp.async.wait_group %0;" ::"n"(RS - 1) : "memory");
+      const int rs = (int)(k % RS);
+      float2 v[16];
+#pragma unroll
+      for (int q2 = 0; q2 < 8; ++q2) {
+        const float4 w = *reinterpret_cast<const float4 *>(raw + rs * TC_M * 128 + ((q2 ^ rot) << 4));
+        v[2 * q2] = make_float2(w.x * sc, w.y * sc);
+        v[2 * q2 + 1] = make_float2(w.z * sc, w.w * sc);
+      }
       const int st = (int)(k % S);
       if (k >= S && !tc_wait(smem_u32(&bar_empty[st]), (uint32_t)((k / S) - 1) & 1u)) {
         atomicExch(&abort_flag, 1);
-        ok = false;
-        return;
+        break;
       }
       conv_put<P>(tsm + st * SBYTES, r, v);
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar_full[st])) : "memory");
-    };
-    float2 v0[16], v1[16];
-    gather(0, v0);
-    if (kc > 1) gather(1, v1);
-    for (int64_t k = 0; k < kc && ok; k += 2) {
-      put(k, v0);
-      if (!ok) break;
-      if (k + 2 < kc) gather(k + 2, v0);
-      if (k + 1 < kc) {
-        put(k + 1, v1);
-        if (!ok) break;
-        if (k + 3 < kc) gather(k + 3, v1);
-      }
     }
+    // no copy of this thread is left in flight when the CTA ends
+    asm volatile("cp.async.wait_all;" ::: "memory");
   }
   // epilogue: warps 4-7, thread tid - 128 = tile row = tensor-memory lane
   bool ok = tc_wait(smem_u32(&bar_done), 0u);
@@ -1934,6 +1979,12 @@ static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c
   a.perbeta = c.perbeta;
   a.Bp = Bp;
   a.o_bout = g.o_bout;
+  // a shared variable among the output's two lowest index bits (one 32-byte
+  // sector of complex64) when no batch axis lies below them: instances fastest
+  a.s_fast = 0;
+  if (g.ns > 0 && !(g.o_bat && !g.o_bout))
+    for (int b = 0; b < g.ns; ++b)
+      if (g.sO[b] < 2) a.s_fast = 1;
   a.o_rank = g.nm + g.nn + g.ns;
   a.nM = g.nm;
   a.nN = g.nn;
@@ -1957,7 +2008,7 @@ static void launch_gemm_tc(char *ws, int sms, int Bp, GemmDesc g, const TcCfg &c
   const unsigned grid = (unsigned)(c.inst * c.mtiles * c.ntiles);
   if (conv) {
 #define QGM_TC_CONV(NT_, P_) \
-  k_gemm_tc_conv<NT_, P_><<<grid, 256, tc_smem_bytes(NT_, P_), st>>>(ws, a, meta, hdr)
+  k_gemm_tc_conv<NT_, P_><<<grid, 256, tcc_smem_bytes(NT_, P_), st>>>(ws, a, meta, hdr)
     if (P == 4) {
       if (c.nt == 256) QGM_TC_CONV(256, 4);
       else if (c.nt == 128) QGM_TC_CONV(128, 4);
@@ -2006,7 +2057,7 @@ static cudaError_t tc_set_smem() {
 #define QGM_TC_ATTR(NT_, P_)                                                                                  \
   if (e == cudaSuccess)                                                                                       \
   e = cudaFuncSetAttribute(k_gemm_tc_conv<NT_, P_>, cudaFuncAttributeMaxDynamicSharedMemorySize,              \
-                           tc_smem_bytes(NT_, P_))
+                           tcc_smem_bytes(NT_, P_))
   QGM_TC_ATTR(256, 4);
   QGM_TC_ATTR(128, 4);
   QGM_TC_ATTR(64, 4);
@@ -2334,6 +2385,25 @@ static int upload_image(qgm_plan *p, const ResidentLayout &L, int smem, cudaStre
   CK(cudaMemcpyAsync(p->exec->ws + p->off_image, img.data(), img.size() * 4, cudaMemcpyHostToDevice, st));
   CK(cudaStreamSynchronize(st));
   return QGM_OK;
+}
+
+// Self-test of the bounded wait (qgm_selftest_wait_timeout): one mbarrier
+// with an arrival count of 1; with arrive = 0 nothing arrives, so the wait
+// for its first phase runs out after limit_ns and the kernel writes
+// QGM_ERR_TIMEOUT; with arrive = 1 the thread arrives first and the wait
+// succeeds at once.
+__device__ int32_t g_selftest_status;
+__global__ void k_selftest_wait(uint64_t limit_ns, int arrive) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar)));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+    g_selftest_status = tc_wait_ns(smem_u32(&bar), 0u, limit_ns) ? QGM_OK : QGM_ERR_TIMEOUT;
+  }
 }
 
 extern "C" {
@@ -2799,6 +2869,21 @@ int qgm_plan_step_stats(qgm_plan *p, uint32_t *maxbits, int32_t *exps, int64_t c
     maxbits[s] = slot >= 0 && slot < p->n_meta ? m[slot].maxbits : 0u;
     exps[s] = slot >= 0 && slot < p->n_meta ? m[slot].exp : 0;
   }
+  return QGM_OK;
+}
+
+int qgm_selftest_wait_timeout(int64_t limit_ns, int32_t arrive, int32_t *status_out, void *stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!status_out || limit_ns < 1000 || limit_ns > 2000000000ll) {
+    set_error("qgm_selftest_wait_timeout: need status_out and 1 us <= limit_ns <= 2 s");
+    return QGM_ERR_ARG;
+  }
+  const int32_t unset = 1;
+  CK(cudaMemcpyToSymbolAsync(g_selftest_status, &unset, sizeof(int32_t), 0, cudaMemcpyHostToDevice, st));
+  k_selftest_wait<<<1, 32, 0, st>>>((uint64_t)limit_ns, arrive ? 1 : 0);
+  CK(cudaGetLastError());
+  CK(cudaMemcpyFromSymbolAsync(status_out, g_selftest_status, sizeof(int32_t), 0, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
   return QGM_OK;
 }
 
