@@ -298,12 +298,15 @@ int qgm_plan_get_tuning(const qgm_plan *p, int32_t *rec, float *ms, int64_t cap,
 
 /* Shapes of the GEMM-shaped steps (Sec. IV, Eq. par_sum with two large
  * operands sharing every summed variable): for the c-th such step, c < cap,
- * rec[11c .. 11c+10] = step index, nm, nn, nk, ns (variables private to A, to
+ * rec[12c .. 12c+11] = step index, nm, nn, nk, ns (variables private to A, to
  * B, summed, shared and kept), A batched, B batched, output batched, 1 when
  * the step runs on the tensor cores, 1 when its output is stored with the
  * batch entry outermost, 1 when an operand is (both for tensor-core steps
- * only: a product per batch entry read by another tensor-core step).  *n = the number of GEMM steps; rec may
- * be NULL to query it.  Host only. */
+ * only: a product per batch entry read by another tensor-core step), and 1
+ * when the tensor-core step folds its batch entries into M, so that the
+ * product kernel can convert its batched operand itself
+ * (qgm_plan_opts.tc_convert).  *n = the number of GEMM steps; rec may be
+ * NULL to query it.  Host only. */
 int qgm_plan_get_gemm(const qgm_plan *p, int32_t *rec, int64_t cap, int64_t *n);
 void qgm_plan_free(qgm_plan *p);
 

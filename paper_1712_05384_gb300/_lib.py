@@ -371,16 +371,17 @@ class Plan:
 
     def gemm_shapes(self):
         """GEMM-shaped steps: list of dicts (step, nm, nn, nk, ns, a_bat,
-        b_bat, o_bat, tc, o_bout, in_bout) -- 2^nm x 2^nn outputs, 2^nk
-        summed entries, for each of the 2^ns shared indices (and batch entry
-        when batched); o_bout / in_bout: output / an operand stored with the
-        batch entry outermost."""
+        b_bat, o_bat, tc, o_bout, in_bout, conv_ok) -- 2^nm x 2^nn outputs,
+        2^nk summed entries, for each of the 2^ns shared indices (and batch
+        entry when batched); o_bout / in_bout: output / an operand stored with
+        the batch entry outermost; conv_ok: a folded tensor-core step (its
+        product kernel can convert the batched operand itself)."""
         n = C.c_int64()
         check(lib().qgm_plan_get_gemm(self._h, None, 0, C.byref(n)))
-        a = np.zeros(11 * max(n.value, 1), dtype=np.int32)
+        a = np.zeros(12 * max(n.value, 1), dtype=np.int32)
         check(lib().qgm_plan_get_gemm(self._h, a.ctypes.data_as(_I32P), n.value, C.byref(n)))
-        keys = ("step", "nm", "nn", "nk", "ns", "a_bat", "b_bat", "o_bat", "tc", "o_bout", "in_bout")
-        return [dict(zip(keys, map(int, a[11 * c: 11 * c + 11]))) for c in range(n.value)]
+        keys = ("step", "nm", "nn", "nk", "ns", "a_bat", "b_bat", "o_bat", "tc", "o_bout", "in_bout", "conv_ok")
+        return [dict(zip(keys, map(int, a[12 * c: 12 * c + 12]))) for c in range(n.value)]
 
     # ------------------------------------------------------------ device
     def bind(self, workspace=None, stream=None):
@@ -499,6 +500,15 @@ def measure_fp32_peak(stream=None):
     t = C.c_double()
     check(lib().qgm_measure_fp32_peak(C.byref(t), _stream(stream)))
     return t.value
+
+
+def selftest_wait_timeout(limit_ns, arrive=False, stream=None):
+    """Run the kernels' bounded mbarrier wait on a barrier nothing (arrive =
+    False) or the waiting thread itself (True) arrives at; returns the status
+    the kernel wrote (QGM_ERR_TIMEOUT or 0)."""
+    st = C.c_int32(1)
+    check(lib().qgm_selftest_wait_timeout(int(limit_ns), 1 if arrive else 0, C.byref(st), _stream(stream)))
+    return st.value
 
 
 # ---------------------------------------------------------------- App. B, C

@@ -1120,6 +1120,7 @@ __global__ void __launch_bounds__(128, 1) k_gemm_tc(char *ws, const __grid_const
   // epilogue: thread r = tile row r = tensor-memory lane r
   bool ok = tc_wait(smem_u32(&bar_done), 0u);
   if (!ok) ok = tc_wait(smem_u32(&bar_done), 0u);  // MMAs read only loaded stages: they finish
+  ok = __all_sync(0xffffffffu, ok);                 // tcgen05.ld below is warp-collective
   const bool valid_run = ok && !*(volatile int *)&abort_flag;
   float lmax = 0.f;
   if (ok) {
@@ -1393,6 +1394,7 @@ __global__ void __launch_bounds__(256, 1) k_gemm_tc_conv(char *ws, const __grid_
   // epilogue: warps 4-7, thread tid - 128 = tile row = tensor-memory lane
   bool ok = tc_wait(smem_u32(&bar_done), 0u);
   if (!ok) ok = tc_wait(smem_u32(&bar_done), 0u);
+  ok = __all_sync(0xffffffffu, ok);  // tcgen05.ld below is warp-collective
   const bool valid_run = ok && !*(volatile int *)&abort_flag;
   float lmax = 0.f;
   if (ok && warp >= 4) {
@@ -2837,8 +2839,8 @@ int qgm_plan_profile_gemm(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, 
     for (auto &x : e) CK(cudaEventCreate(&x));
     CK(cudaEventRecord(e[0], st));
     const bool tc = p->gemm_tc && tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes).ok;
+    if (!tc) CK(cudaEventRecord(e[1], st));  // no split pass: all of it is the product
     launch_step(p, d, st, tc ? e[1] : nullptr);
-    if (!tc) CK(cudaEventRecord(e[1], st));
     CK(cudaEventRecord(e[2], st));
     for (auto &x : e) ev.push_back(x);
   }

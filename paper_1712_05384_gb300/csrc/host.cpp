@@ -2350,7 +2350,7 @@ int qgm_plan_get_gemm(const qgm_plan *p, int32_t *rec, int64_t cap, int64_t *n) 
     if (d.gemm < 0) continue;
     if (rec && c < cap) {
       const GemmDesc &g = p->gemms[d.gemm];
-      int32_t *r = rec + 11 * c;
+      int32_t *r = rec + 12 * c;
       r[0] = (int32_t)s;
       r[1] = g.nm;
       r[2] = g.nn;
@@ -2362,6 +2362,7 @@ int qgm_plan_get_gemm(const qgm_plan *p, int32_t *rec, int64_t cap, int64_t *n) 
       r[8] = p->gemm_tc && gemm_tc_eligible(g, p->Bp) ? 1 : 0;
       r[9] = g.o_bout;
       r[10] = g.a_bout | g.b_bout;
+      r[11] = r[8] && tc_config(g, p->Bp, p->tc_planes).fold ? 1 : 0;
     }
     ++c;
   }

@@ -273,6 +273,26 @@ def test_errors_are_reported():
                executor=2)
 
 
+def test_bounded_wait_gives_timeout_status():
+    # failure detection without a fault: the tensor-core kernels' bounded
+    # mbarrier wait on a barrier nothing arrives at gives up after its limit
+    # and reports QGM_ERR_TIMEOUT; the context stays usable afterwards
+    import time
+    q = Q()
+    from paper_1712_05384_gb300 import _lib
+    t0 = time.perf_counter()
+    assert _lib.selftest_wait_timeout(200_000_000) == -4
+    assert time.perf_counter() - t0 >= 0.2
+    assert _lib.selftest_wait_timeout(200_000_000, arrive=True) == 0
+    with pytest.raises(q.QgmError):
+        _lib.selftest_wait_timeout(10)                 # limit out of range
+    c = qi.grid_circuit(3, 3, 8, 0)
+    bits = qi.bitstrings(c.n, 8, 0)
+    a = q.Plan(q.Model(q.Circuit.grid(3, 3, 8, 0)), batch=8, executor=1).bind().amplitudes_host(bits)
+    rel, ab = errors(a, sv.amplitudes(c, bits), c.n)
+    assert rel < REL_TOL and ab < ABS_TOL
+
+
 @pytest.mark.parametrize("executor", [2, 3])
 @pytest.mark.parametrize("chunk", [1, 2, 4, 8])
 def test_resident_chunks_agree(chunk, executor):

@@ -113,14 +113,18 @@ def test_in_kernel_conversion_matches_split_pass(precision):
     c = qi.grid_circuit(4, 6, 34, 0)
     bits = qi.bitstrings(c.n, 6, 0)
     m = q.Model(q.Circuit.grid(4, 6, 34, 0))
-    a = q.Plan(m, order_kind=1, batch=6, executor=1, precision=precision, tc_convert=True).bind()
+    a = q.Plan(m, order_kind=1, batch=6, executor=1, precision=precision, tc_convert=True)
+    assert any(g["conv_ok"] for g in a.gemm_shapes())
+    a = a.bind()
     b = q.Plan(m, order_kind=1, batch=6, executor=1, precision=precision).bind()
     assert np.array_equal(a.amplitudes_host(bits), b.amplitudes_host(bits))
     rel, ab = errors(a.amplitudes_host(bits), sv.amplitudes(c, bits), c.n)
     assert rel < SPLIT_TOL and ab < SPLIT_TOL, (rel, ab)
     m = q.Model(q.Circuit.grid(4, 8, 40, 0))
     bits = qi.bitstrings(32, 4, 0)
-    a = q.Plan(m, order_kind=1, batch=4, precision=precision, tc_convert=True).bind().amplitudes_host(bits)
+    pa = q.Plan(m, order_kind=1, batch=4, precision=precision, tc_convert=True)
+    assert any(g["conv_ok"] for g in pa.gemm_shapes())
+    a = pa.bind().amplitudes_host(bits)
     b = q.Plan(m, order_kind=1, batch=4, precision=precision).bind().amplitudes_host(bits)
     assert np.array_equal(a, b)
 
