@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precisions", action="store_true", help="time the headline precision only")
     ap.add_argument("--executor", type=int, default=0, help="0 auto, 1 stepwise, 2 resident, 3 compiled resident")
+    ap.add_argument("--no-autotune", action="store_true", help="fixed launch rules instead of the autotuner")
+    ap.add_argument("--tc-convert", action="store_true",
+                    help="folded tensor-core steps convert their batched operand in the product kernel")
     ap.add_argument("--custom", default=None, metavar="RxC,DEPTH,BATCH",
                     help="a smaller seed-0 grid circuit instead of a workload (profiling captures), e.g. 4x8,40,4")
     a = ap.parse_args()
@@ -302,7 +305,8 @@ def main():
 
     def make_plan(precision):
         # the autotuner picks per-step launch parameters at bind (untimed)
-        return q.Plan(model, batch=P, executor=args.executor, precision=precision, autotune=True,
+        return q.Plan(model, batch=P, executor=args.executor, precision=precision, autotune=not args.no_autotune,
+                      tc_convert=args.tc_convert,
                       order_kind=q.ORDER_MINFILL if P < B else q.ORDER_AUTO).bind()
 
     def run_pass(plan, i):
@@ -486,7 +490,8 @@ def main():
                    "workspace_gb": info.workspace_bytes / 1e9, "parallelism": f"replicas{world}",
                    "executor": {1: "stepwise", 2: "resident", 3: "compiled resident"}.get(ex_kind), "chunk": ex_chunk,
                    "gemm_steps": info.n_gemm_steps, "gemm_steps_tensor_core": info.n_gemm_tc_steps,
-                   "gemm_precision": args.precision,
+                   "gemm_precision": args.precision, "autotune": not args.no_autotune,
+                   "tc_convert": bool(args.tc_convert),
                    "l2": "flushed between timed steps (264 MB write, untimed); the pass's tensors exceed L2"},
         "error": err,
         "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 8 * amps_per_step,

@@ -95,6 +95,7 @@ _SIGS = {
     "qgm_plan_get_step_cost": [_P, C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int64],
     "qgm_plan_get_gemm": [_P, _I32P, C.c_int64, _I64P],
     "qgm_plan_get_tuning": [_P, _I32P, C.POINTER(C.c_float), C.c_int64, _I64P],
+    "qgm_plan_set_tuning": [_P, _I32P, C.c_int64],
     "qgm_plan_get_step_inputs": [_P, C.c_int32, _I32P, C.c_int64, _I64P],
     "qgm_plan_profile": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), _P],
     "qgm_plan_profile_gemm": [_P, _P, C.c_int64, _P, C.POINTER(C.c_float), C.POINTER(C.c_float), _P],
@@ -358,16 +359,26 @@ class Plan:
 
     def tuning(self):
         """Autotuner choices after bind: list of dicts (step, nt_cap, T, conv,
-        ms_rule, ms_best)."""
+        U, ms_rule, ms_best)."""
         n = C.c_int64()
         check(lib().qgm_plan_get_tuning(self._h, None, None, 0, C.byref(n)))
-        r = np.zeros(4 * max(n.value, 1), dtype=np.int32)
+        r = np.zeros(5 * max(n.value, 1), dtype=np.int32)
         m = np.zeros(2 * max(n.value, 1), dtype=np.float32)
         check(lib().qgm_plan_get_tuning(self._h, r.ctypes.data_as(_I32P), m.ctypes.data_as(C.POINTER(C.c_float)),
                                         n.value, C.byref(n)))
-        return [{"step": int(r[4 * c]), "nt_cap": int(r[4 * c + 1]), "T": int(r[4 * c + 2]),
-                 "conv": int(r[4 * c + 3]), "ms_rule": float(m[2 * c]), "ms_best": float(m[2 * c + 1])}
+        return [{"step": int(r[5 * c]), "nt_cap": int(r[5 * c + 1]), "T": int(r[5 * c + 2]),
+                 "conv": int(r[5 * c + 3]), "U": int(r[5 * c + 4]), "ms_rule": float(m[2 * c]),
+                 "ms_best": float(m[2 * c + 1])}
                 for c in range(n.value)]
+
+    def set_tuning(self, choices):
+        """Set launch parameters by hand: dicts with step and any of nt_cap,
+        T, conv, U (as tuning() returns them)."""
+        r = np.zeros(5 * max(len(choices), 1), dtype=np.int32)
+        for c, t in enumerate(choices):
+            r[5 * c:5 * c + 5] = [t["step"], t.get("nt_cap", 0), t.get("T", 0), t.get("conv", 0), t.get("U", 0)]
+        check(lib().qgm_plan_set_tuning(self._h, r.ctypes.data_as(_I32P), len(choices)))
+        return self
 
     def gemm_shapes(self):
         """GEMM-shaped steps: list of dicts (step, nm, nn, nk, ns, a_bat,

@@ -191,7 +191,7 @@ __device__ void build_tables(const StepDesc &d, int r0, int lt, int Bp, int64_t 
 // Product-sum step, batched output: thread (x, y) = (pair of batch entries,
 // term group).  Rows are walked at stride gridDim.y (a power of two), terms
 // at stride blockDim.y (a power of two); addresses advance by table lookups.
-template <int M>
+template <int M, int U>
 __global__ void __launch_bounds__(512)
     k_step_batched(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp, int logP) {
   __shared__ float4 part[512];
@@ -275,6 +275,51 @@ __global__ void __launch_bounds__(512)
         }
         a0 = p0;
         a1 = p1;
+      } else if (U == 4 && tcount >= 4) {
+        // four terms per iteration (their loads in flight together): terms
+        // jt .. jt + 3 differ in the two lowest term bits, at eb + 0, e0,
+        // e0 + e1 and 2 e0 + e1 (e_t: the carry-table steps)
+        for (int jt = 0; jt < tcount; jt += 4) {
+          float2 p[4][2];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) p[u][0] = p[u][1] = make_float2(1.f, 0.f);
+#pragma unroll
+          for (int i = 0; i < M; ++i) {
+            const int64_t e0 = etab[i][0], e1 = etab[i][1];
+            const char *a = ws + rowb[i] + eb[i];
+            const int64_t off[4] = {0, e0, e0 + e1, 2 * e0 + e1};
+            if (d.in[i].batched) {
+              float4 v[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4 *>(a + off[u]));
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                p[u][0] = cmul(p[u][0], make_float2(v[u].x * scale[i], v[u].y * scale[i]));
+                p[u][1] = cmul(p[u][1], make_float2(v[u].z * scale[i], v[u].w * scale[i]));
+              }
+            } else {
+              float2 v[4];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float2 *>(a + off[u]));
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                const float2 sv = make_float2(v[u].x * scale[i], v[u].y * scale[i]);
+                p[u][0] = cmul(p[u][0], sv);
+                p[u][1] = cmul(p[u][1], sv);
+              }
+            }
+          }
+          a0.x += (p[0][0].x + p[1][0].x) + (p[2][0].x + p[3][0].x);
+          a0.y += (p[0][0].y + p[1][0].y) + (p[2][0].y + p[3][0].y);
+          a1.x += (p[0][1].x + p[1][1].x) + (p[2][1].x + p[3][1].x);
+          a1.y += (p[0][1].y + p[1][1].y) + (p[2][1].y + p[3][1].y);
+          if (jt + 4 < tcount) {
+            const int t = __ffs(jt + 4) - 1;
+#pragma unroll
+            for (int i = 0; i < M; ++i)
+              eb[i] += 2 * etab[i][0] + etab[i][1] + etab[i][t];
+          }
+        }
       } else {
         // two terms per iteration (their loads in flight together): term jt
         // at eb, term jt + 1 one carry into bit 0 away
@@ -2127,16 +2172,22 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
     }
     const uint64_t gy = pow2_floor(std::min<uint64_t>(row_blocks, std::min<uint64_t>(cap, 32768)));
     const dim3 g2(bx, (unsigned)gy), b2(STEP_THREADS, T);
+    // four terms in flight per thread where the tuner measured that faster
+    const bool u4 = tn && tn->U == 4 && d.k >= 2 && (d.k - (31 - __builtin_clz((unsigned)T))) >= 2;
+#define QGM_SB(M_)                                                                      \
+  if (u4) k_step_batched<M_, 4><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP);         \
+  else k_step_batched<M_, 2><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP);
     switch (d.m) {
-      case 1: k_step_batched<1><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
-      case 2: k_step_batched<2><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
-      case 3: k_step_batched<3><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
-      case 4: k_step_batched<4><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
-      case 5: k_step_batched<5><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
-      case 6: k_step_batched<6><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
-      case 7: k_step_batched<7><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
-      default: k_step_batched<8><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      case 1: QGM_SB(1) break;
+      case 2: QGM_SB(2) break;
+      case 3: QGM_SB(3) break;
+      case 4: QGM_SB(4) break;
+      case 5: QGM_SB(5) break;
+      case 6: QGM_SB(6) break;
+      case 7: QGM_SB(7) break;
+      default: QGM_SB(8) break;
     }
+#undef QGM_SB
   } else {
     const uint64_t blocks = pow2_floor(std::max<uint64_t>(1, std::min<uint64_t>((rows + 255) / 256, (uint64_t)sms * 8)));
     k_step_plain<<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr);
@@ -2203,12 +2254,14 @@ static int autotune(qgm_plan *p, cudaStream_t st) {
             cand.push_back(t);
           }
     } else if (d.gemm < 0 && d.batched_out && d.tile_t == 0) {
-      for (int T : {1, 2, 4})
-        if (T <= (1 << std::min(d.k, 4))) {
-          StepTune t;
-          t.T = T;
-          cand.push_back(t);
-        }
+      for (int U : {2, 4})
+        for (int T : {1, 2, 4})
+          if (T <= (1 << std::min(d.k, 4)) && (U == 2 || (1 << d.k) >= 4 * T)) {
+            StepTune t;
+            t.T = T;
+            t.U = U;
+            cand.push_back(t);
+          }
     }
     if (cand.size() < 2) continue;
     float ms_rule = 0.f;
@@ -2870,6 +2923,47 @@ int qgm_plan_step_stats(qgm_plan *p, uint32_t *maxbits, int32_t *exps, int64_t c
     const int slot = p->steps[s].out_meta;
     maxbits[s] = slot >= 0 && slot < p->n_meta ? m[slot].maxbits : 0u;
     exps[s] = slot >= 0 && slot < p->n_meta ? m[slot].exp : 0;
+  }
+  return QGM_OK;
+}
+
+int qgm_plan_set_tuning(qgm_plan *p, const int32_t *rec, int64_t n) {
+  int rc = check_bound(p, "qgm_plan_set_tuning");
+  if (rc) return rc;
+  if (n < 0 || (n > 0 && !rec)) {
+    set_error("qgm_plan_set_tuning: bad record count or null records");
+    return QGM_ERR_ARG;
+  }
+  for (int64_t c = 0; c < n; ++c) {
+    const int32_t *r = rec + 5 * c;
+    const bool ok = r[0] >= 0 && r[0] < (int32_t)p->steps.size() &&
+                    (r[1] == 0 || r[1] == 64 || r[1] == 128 || r[1] == 256) &&
+                    (r[2] == 0 || r[2] == 1 || r[2] == 2 || r[2] == 4) && (r[3] == 0 || r[3] == 1) &&
+                    (r[4] == 0 || r[4] == 2 || r[4] == 4);
+    if (!ok) {
+      set_error("qgm_plan_set_tuning: bad record %lld (step %d, N tile %d, T %d, conv %d, U %d)", (long long)c,
+                r[0], r[1], r[2], r[3], r[4]);
+      return QGM_ERR_ARG;
+    }
+  }
+  for (int64_t c = 0; c < n; ++c) {
+    const int32_t *r = rec + 5 * c;
+    StepTune &t = p->tune[r[0]];
+    t.nt_cap = r[1];
+    t.T = r[2];
+    t.conv = r[3];
+    t.U = r[4];
+    t.ms_rule = t.ms_best = 0.f;
+  }
+  // the captured passes hold the old launch parameters
+  qgm_exec_state *x = p->exec;
+  if (x->graph) {
+    cudaGraphExecDestroy(x->graph);
+    x->graph = nullptr;
+  }
+  if (x->ggraph) {
+    cudaGraphExecDestroy(x->ggraph);
+    x->ggraph = nullptr;
   }
   return QGM_OK;
 }

@@ -140,3 +140,35 @@ def test_repeat_calls_are_identical():
     c = p.amplitudes_host(bits)
     assert np.array_equal(a, c)
     assert np.max(np.abs(a - b[::-1])) <= 1e-12 * np.max(np.abs(a))
+
+
+@pytest.mark.parametrize("rows,cols,depth,B,trees", [(4, 6, 34, 6, None), (4, 6, 30, 64, True)])
+def test_every_tuning_candidate_gives_the_same_amplitudes(rows, cols, depth, B, trees):
+    # the autotuner's candidates (tensor-core N tile, in-kernel conversion,
+    # product-sum term groups and terms in flight) compute the same products:
+    # each setting, applied to every step by hand, matches the fixed rules
+    # and the oracle
+    q = Q()
+    c = qi.grid_circuit(rows, cols, depth, 0)
+    bits = qi.bitstrings(c.n, B, 0)
+    m = q.Model(q.Circuit.grid(rows, cols, depth, 0))
+    p = q.Plan(m, order_kind=1, batch=B, executor=1, trees=trees).bind()
+    base = p.amplitudes_host(bits)
+    from oracle import ve
+    ref = ve.amplitudes(c, bits[:4])
+    n_steps = p.info.n_steps
+    with pytest.raises(q.QgmError):
+        p.set_tuning([{"step": 0, "nt_cap": 100}])
+    for nt in (64, 128, 256):
+        for conv in (0, 1):
+            for T in (1, 2, 4):
+                for U in (2, 4):
+                    p.set_tuning([{"step": s, "nt_cap": nt, "conv": conv, "T": T, "U": U} for s in range(n_steps)])
+                    a = p.amplitudes_host(bits)
+                    assert p.status() == 0
+                    scale = np.max(np.abs(base))
+                    assert np.max(np.abs(a - base)) <= 1e-5 * scale, (nt, conv, T, U)
+                    rel, ab = errmeasure.measures(a[:4], ref, c.n)["rel"], errmeasure.measures(a[:4], ref, c.n)["abs"]
+                    assert rel < SPLIT_TOL and ab < SPLIT_TOL, (nt, conv, T, U, rel, ab)
+    got = p.tuning()
+    assert len(got) == n_steps and all(t["U"] == 4 and t["T"] == 4 for t in got)
