@@ -195,7 +195,8 @@ typedef struct {
                                  or inside the product kernel; the batched
                                  product-sum kernel's term
                                  groups: 1, 2 or 4, and terms in flight per
-                                 thread: 2 or 4) on the bound device, on
+                                 thread: 2 or 4; a GEMM-shaped step may run
+                                 as a product-sum) on the bound device, on
                                  tensors from one pass over an all-zero batch,
                                  and keeps the fastest; 0: fixed rules */
   int32_t gemm_precision;     /* GEMM-shaped steps whose tensor-core form exists
@@ -289,19 +290,22 @@ int qgm_plan_get_step_cost(const qgm_plan *p, double *bytes, double *flops, int6
 int qgm_plan_get_step_inputs(const qgm_plan *p, int32_t step, int32_t *rec, int64_t cap, int64_t *n);
 
 /* Autotuner choices (qgm_plan_opts.autotune, after qgm_plan_bind): for the
- * c-th tuned step, rec[5c .. 5c+4] = step index, tensor-core N tile cap (0:
+ * c-th tuned step, rec[6c .. 6c+5] = step index, tensor-core N tile cap (0:
  * not a tensor-core step), product-sum term groups (0: not tuned), 1 when a
  * folded tensor-core step converts its streamed operand inside the product
  * kernel (instead of a separate split pass), product-sum terms in flight
- * per thread (4, or 0/2 for two), and
+ * per thread (4, or 0/2 for two), 1 when a GEMM-shaped step runs with the
+ * product-sum kernels instead of a GEMM kernel, and
  * ms[2c], ms[2c+1] = milliseconds with the fixed rules and with the choice.
  * *n = the number of tuned steps; rec/ms may be NULL to query it. */
 int qgm_plan_get_tuning(const qgm_plan *p, int32_t *rec, float *ms, int64_t cap, int64_t *n);
 
 /* Sets launch parameters of steps by hand, in the records qgm_plan_get_tuning
- * returns (5 ints per step: step index, N tile cap 0/64/128/256, term groups
- * 0/1/2/4, in-kernel conversion 0/1, terms in flight 0/2/4; a parameter
- * that does not apply to the step is ignored), e.g. to reuse a tuning saved
+ * returns (6 ints per step: step index, N tile cap 0/64/128/256, term groups
+ * 0/1/2/4, in-kernel conversion 0/1, terms in flight 0/2/4, product-sum
+ * form of a GEMM-shaped step 0/1 (only where no tensor of the step keeps its
+ * batch entry outermost); a parameter that does not apply to the step is
+ * ignored), e.g. to reuse a tuning saved
  * from an earlier bind without timing again.  After qgm_plan_bind (which
  * resets them); the next call re-captures its pass.  QGM_ERR_ARG on a bad
  * record (nothing changed). */

@@ -359,24 +359,25 @@ class Plan:
 
     def tuning(self):
         """Autotuner choices after bind: list of dicts (step, nt_cap, T, conv,
-        U, ms_rule, ms_best)."""
+        U, ps, ms_rule, ms_best)."""
         n = C.c_int64()
         check(lib().qgm_plan_get_tuning(self._h, None, None, 0, C.byref(n)))
-        r = np.zeros(5 * max(n.value, 1), dtype=np.int32)
+        r = np.zeros(6 * max(n.value, 1), dtype=np.int32)
         m = np.zeros(2 * max(n.value, 1), dtype=np.float32)
         check(lib().qgm_plan_get_tuning(self._h, r.ctypes.data_as(_I32P), m.ctypes.data_as(C.POINTER(C.c_float)),
                                         n.value, C.byref(n)))
-        return [{"step": int(r[5 * c]), "nt_cap": int(r[5 * c + 1]), "T": int(r[5 * c + 2]),
-                 "conv": int(r[5 * c + 3]), "U": int(r[5 * c + 4]), "ms_rule": float(m[2 * c]),
-                 "ms_best": float(m[2 * c + 1])}
+        return [{"step": int(r[6 * c]), "nt_cap": int(r[6 * c + 1]), "T": int(r[6 * c + 2]),
+                 "conv": int(r[6 * c + 3]), "U": int(r[6 * c + 4]), "ps": int(r[6 * c + 5]),
+                 "ms_rule": float(m[2 * c]), "ms_best": float(m[2 * c + 1])}
                 for c in range(n.value)]
 
     def set_tuning(self, choices):
         """Set launch parameters by hand: dicts with step and any of nt_cap,
-        T, conv, U (as tuning() returns them)."""
-        r = np.zeros(5 * max(len(choices), 1), dtype=np.int32)
+        T, conv, U, ps (as tuning() returns them)."""
+        r = np.zeros(6 * max(len(choices), 1), dtype=np.int32)
         for c, t in enumerate(choices):
-            r[5 * c:5 * c + 5] = [t["step"], t.get("nt_cap", 0), t.get("T", 0), t.get("conv", 0), t.get("U", 0)]
+            r[6 * c:6 * c + 6] = [t["step"], t.get("nt_cap", 0), t.get("T", 0), t.get("conv", 0), t.get("U", 0),
+                                  t.get("ps", 0)]
         check(lib().qgm_plan_set_tuning(self._h, r.ctypes.data_as(_I32P), len(choices)))
         return self
 

@@ -2121,14 +2121,15 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
                            Header *hdr, cudaStream_t st, bool tc = false, int64_t planes_off = 0,
                            int planes = 4, cudaEvent_t mid = nullptr, const StepTune *tn = nullptr) {
   const uint64_t rows = 1ull << d.w_out;
-  if (d.gemm >= 0 && gemms && tc) {
+  const bool as_ps = tn && tn->ps;  // a GEMM-shaped step the tuner runs as a product-sum
+  if (d.gemm >= 0 && gemms && tc && !as_ps) {
     const TcCfg c = tc_config(gemms[d.gemm], Bp, planes, tn && tn->nt_cap ? tn->nt_cap : 256);
     if (c.ok) {
       launch_gemm_tc(ws, sms, Bp, gemms[d.gemm], c, planes_off, planes, meta, hdr, st, mid, tn && tn->conv);
       return;
     }
   }
-  if (d.gemm >= 0 && gemms && gemm_fp32_ok(gemms[d.gemm])) {
+  if (d.gemm >= 0 && gemms && gemm_fp32_ok(gemms[d.gemm]) && !as_ps) {
     const GemmDesc &g = gemms[d.gemm];
     const dim3 grid(1u << ((g.nm - 6) + (g.nn - (g.nn >= 6 ? 6 : 5))), g.o_bat ? Bp : 1, 1u << g.ns);
     if (g.nn >= 6) {
@@ -2253,6 +2254,18 @@ static int autotune(qgm_plan *p, cudaStream_t st) {
             t.conv = conv;
             cand.push_back(t);
           }
+    }
+    if (d.gemm >= 0 && d.batched_out && d.tile_t == 0) {
+      // a GEMM-shaped step may also run as a product-sum (batch axis
+      // innermost everywhere: coalesced across batch entries)
+      const GemmDesc &g = p->gemms[d.gemm];
+      if (!g.a_bout && !g.b_bout && !g.o_bout)
+        for (int U : {2, 4}) {
+          StepTune t;
+          t.ps = 1;
+          t.U = U;
+          cand.push_back(t);
+        }
     } else if (d.gemm < 0 && d.batched_out && d.tile_t == 0) {
       for (int U : {2, 4})
         for (int T : {1, 2, 4})
@@ -2935,24 +2948,30 @@ int qgm_plan_set_tuning(qgm_plan *p, const int32_t *rec, int64_t n) {
     return QGM_ERR_ARG;
   }
   for (int64_t c = 0; c < n; ++c) {
-    const int32_t *r = rec + 5 * c;
-    const bool ok = r[0] >= 0 && r[0] < (int32_t)p->steps.size() &&
-                    (r[1] == 0 || r[1] == 64 || r[1] == 128 || r[1] == 256) &&
-                    (r[2] == 0 || r[2] == 1 || r[2] == 2 || r[2] == 4) && (r[3] == 0 || r[3] == 1) &&
-                    (r[4] == 0 || r[4] == 2 || r[4] == 4);
+    const int32_t *r = rec + 6 * c;
+    bool ok = r[0] >= 0 && r[0] < (int32_t)p->steps.size() &&
+              (r[1] == 0 || r[1] == 64 || r[1] == 128 || r[1] == 256) &&
+              (r[2] == 0 || r[2] == 1 || r[2] == 2 || r[2] == 4) && (r[3] == 0 || r[3] == 1) &&
+              (r[4] == 0 || r[4] == 2 || r[4] == 4) && (r[5] == 0 || r[5] == 1);
+    if (ok && r[5]) {
+      // a product-sum needs the batch axis innermost on every tensor of the step
+      const StepDesc &d = p->steps[r[0]];
+      ok = d.gemm >= 0 && !p->gemms[d.gemm].a_bout && !p->gemms[d.gemm].b_bout && !p->gemms[d.gemm].o_bout;
+    }
     if (!ok) {
-      set_error("qgm_plan_set_tuning: bad record %lld (step %d, N tile %d, T %d, conv %d, U %d)", (long long)c,
-                r[0], r[1], r[2], r[3], r[4]);
+      set_error("qgm_plan_set_tuning: bad record %lld (step %d, N tile %d, T %d, conv %d, U %d, ps %d)",
+                (long long)c, r[0], r[1], r[2], r[3], r[4], r[5]);
       return QGM_ERR_ARG;
     }
   }
   for (int64_t c = 0; c < n; ++c) {
-    const int32_t *r = rec + 5 * c;
+    const int32_t *r = rec + 6 * c;
     StepTune &t = p->tune[r[0]];
     t.nt_cap = r[1];
     t.T = r[2];
     t.conv = r[3];
     t.U = r[4];
+    t.ps = r[5];
     t.ms_rule = t.ms_best = 0.f;
   }
   // the captured passes hold the old launch parameters

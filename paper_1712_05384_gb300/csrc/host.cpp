@@ -2320,14 +2320,15 @@ int qgm_plan_get_tuning(const qgm_plan *p, int32_t *rec, float *ms, int64_t cap,
   int64_t c = 0;
   for (size_t s = 0; s < p->tune.size(); ++s) {
     const StepTune &t = p->tune[s];
-    if (t.ms_rule <= 0.f && !t.nt_cap && !t.T && !t.conv && !t.U) continue;
+    if (t.ms_rule <= 0.f && !t.nt_cap && !t.T && !t.conv && !t.U && !t.ps) continue;
     if (c < cap) {
       if (rec) {
-        rec[5 * c] = (int32_t)s;
-        rec[5 * c + 1] = t.nt_cap;
-        rec[5 * c + 2] = t.T;
-        rec[5 * c + 3] = t.conv;
-        rec[5 * c + 4] = t.U;
+        rec[6 * c] = (int32_t)s;
+        rec[6 * c + 1] = t.nt_cap;
+        rec[6 * c + 2] = t.T;
+        rec[6 * c + 3] = t.conv;
+        rec[6 * c + 4] = t.U;
+        rec[6 * c + 5] = t.ps;
       }
       if (ms) {
         ms[2 * c] = t.ms_rule;

@@ -172,3 +172,17 @@ def test_every_tuning_candidate_gives_the_same_amplitudes(rows, cols, depth, B, 
                     assert rel < SPLIT_TOL and ab < SPLIT_TOL, (nt, conv, T, U, rel, ab)
     got = p.tuning()
     assert len(got) == n_steps and all(t["U"] == 4 and t["T"] == 4 for t in got)
+    # GEMM-shaped steps as product-sums (where no tensor keeps its batch
+    # entry outermost; the others refuse)
+    shapes = p.gemm_shapes()
+    ok = [g["step"] for g in shapes if not g["o_bout"] and not g["in_bout"]]
+    assert ok
+    for U in (2, 4):
+        p.set_tuning([{"step": s, "ps": 1, "U": U} for s in ok])
+        a = p.amplitudes_host(bits)
+        assert p.status() == 0
+        assert np.max(np.abs(a - base)) <= 1e-5 * np.max(np.abs(base)), U
+    bout = [g["step"] for g in shapes if g["o_bout"] or g["in_bout"]]
+    if bout:
+        with pytest.raises(q.QgmError):
+            p.set_tuning([{"step": bout[0], "ps": 1}])
