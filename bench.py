@@ -53,8 +53,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="grid5x9_d40_b1000", choices=sorted(
-        k for k, v in qi.WORKLOADS.items() if v[3] > 0))
+    ap.add_argument("--workload", default="grid5x9_d40_b1000", choices=sorted(qi.WORKLOADS))
+    ap.add_argument("--grad", action="store_true",
+                    help="parametrised workload: time amplitudes plus the gradient of sum log|a|^2")
     ap.add_argument("--precision", default="fp16", choices=["fp16", "bf16", "fp32"],
                     help="GEMM steps of the headline value: split FP16, split BF16 or FP32 cores")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -265,11 +266,97 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def run_secondary(args):
+    """Secondary lines on one GPU: all 2^n amplitudes of a small circuit
+    (open outputs, qgm_eliminate), or amplitudes plus the gradient of
+    L = sum log|a|^2 (qgm_amplitudes, then qgm_amplitude_grad, as the
+    torch.autograd wrapper runs them).  Parity of both is in the GPU tests."""
+    import torch
+    import paper_1712_05384_gb300 as q
+    from paper_1712_05384_gb300 import build
+    build.build()
+    q.lib()
+    rows, cols, depth, B, param = qi.WORKLOADS[args.workload]
+    model = q.Model(q.Circuit.grid(rows, cols, depth, 0, param))
+    n = rows * cols
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    if B == 0:
+        plan = q.Plan(model, output_mode=q.OUT_OPEN).bind()
+        d_out = torch.empty(2 << n, dtype=torch.float64, device="cuda")
+        step = lambda: plan.eliminate(d_out, stream=stream)
+        amps, what = 1 << n, "all 2^n amplitudes (open outputs)"
+        h_out = torch.empty(2 << n, dtype=torch.float64).pin_memory()
+        e2e_step = lambda: (step(), h_out.copy_(d_out, non_blocking=True))
+        hb, db = 0, 16 << n
+    else:
+        bits = qi.bitstrings(n, B, 0)
+        plan = q.Plan(model, batch=B, gradients=bool(args.grad)).bind()
+        d_bits = torch.from_numpy(bits.astype(np.int64)).cuda()
+        d_out = torch.empty(2 * B, dtype=torch.float64, device="cuda")
+        d_g = torch.empty(2 * B, dtype=torch.float64, device="cuda")
+        n_par = 2 * len(q.Circuit.grid(rows, cols, depth, 0, param).param_gates()) if param else 0
+        d_grad = torch.empty(max(n_par, 1), dtype=torch.float64, device="cuda")
+
+        def step():
+            plan.amplitudes(d_bits, d_out, stream=stream)
+            if args.grad:
+                a = torch.view_as_complex(d_out.view(B, 2))
+                d_g.copy_(torch.view_as_real(a / (a.abs() ** 2)).reshape(-1))  # g = dL/d(conj a)
+                plan.amplitude_grad(d_bits, d_g, d_grad, stream=stream)
+        amps, what = B, ("amplitudes and the gradient of sum log|a|^2 (%d angles)" % n_par if args.grad
+                         else "amplitudes")
+        h_bits = torch.from_numpy(bits.astype(np.int64)).pin_memory()
+        h_grad = torch.empty_like(d_grad, device="cpu").pin_memory()
+
+        def e2e_step():
+            d_bits.copy_(h_bits, non_blocking=True)
+            step()
+            (h_grad.copy_(d_grad, non_blocking=True) if args.grad else h_out_b.copy_(d_out, non_blocking=True))
+        h_out_b = torch.empty(2 * B, dtype=torch.float64).pin_memory()
+        hb, db = 8 * B, (8 * n_par if args.grad else 16 * B)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with Clocks(0) as clk:
+        for i in range(args.steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+    if plan.status(stream) != 0:
+        raise RuntimeError("device status not OK in the timed region")
+    t_ms = sum(a.elapsed_time(b) for a, b in evs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    print(json.dumps({
+        "metric": METRIC, "value": amps * args.steps / (t_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": args.workload, "grid": f"{rows}x{cols}", "depth": depth, "batch": B, "seed": 0,
+                   "what": what, "executor": {1: "stepwise", 2: "resident", 3: "compiled resident"}.get(
+                       plan.executor()[0]),
+                   "l2": "flushed between timed steps (264 MB write, untimed)"},
+        "e2e": {"value": amps * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": hb, "d2h_bytes_per_step": db},
+        "clocks": clk.summary() if hasattr(clk, "summary") else None,
+    }), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if qi.WORKLOADS[args.workload][3] == 0 or args.grad:
+        if rank == 0:
+            run_secondary(args)
         return
     import torch
     import torch.distributed as dist
@@ -402,7 +489,11 @@ def main():
             flush.fill_(1.0)
             ms += plan.profile(d_pass, d_out, B=P, stream=stream)
             flush.fill_(1.0)
-            a, b = plan.profile_gemm(d_pass, d_out, B=P, stream=stream)
+            try:
+                a, b = plan.profile_gemm(d_pass, d_out, B=P, stream=stream)
+            except q.QgmError as e:  # event timing is unavailable under a kernel profiler
+                print(f"profile_gemm: {e}", file=sys.stderr)
+                a, b = np.zeros(len(gemms)), np.zeros(len(gemms))
             ms_split += a
             ms_prod += b
         ms /= reps
