@@ -385,6 +385,7 @@ __global__ void __launch_bounds__(512)
 // lacks those bits serves all 2^t outputs.  Rows are counted over the other
 // output bits ("outer" bits) and walked by table increments as in
 // k_step_batched; one thread = one pair of batch entries (no term split).
+template <int M>
 __global__ void __launch_bounds__(STEP_THREADS)
     k_step_tile(char *ws, const StepDesc d, Meta *meta, Header *hdr, int Bp, int logP) {
   __shared__ int64_t rowtab[MAXIN][ROWTAB];
@@ -458,9 +459,9 @@ __global__ void __launch_bounds__(STEP_THREADS)
   }
   const int bp = logP < 0 ? (blockIdx.x * STEP_THREADS + tx) * 2 : (tx & ((1 << logP) - 1)) * 2;
   const bool active = bp < Bp;
-  float scale[MAXIN];
+  float scale[M];
   int esum = 0;
-  int64_t rowb[MAXIN];
+  int64_t rowb[M];
   const uint64_t j0 = logP < 0 ? blockIdx.y : ((uint64_t)blockIdx.y << rpb_log) + (tx >> logP);
   __syncthreads();
   int64_t orow = 0;
@@ -468,7 +469,7 @@ __global__ void __launch_bounds__(STEP_THREADS)
     if ((j0 >> b) & 1) orow += ((int64_t)1 << obits[b]) * (int64_t)Bp * 8;
   orow += (int64_t)bp * 8;
 #pragma unroll
-  for (int i = 0; i < MAXIN; ++i) {
+  for (int i = 0; i < M; ++i) {
     scale[i] = 1.f;
     rowb[i] = 0;
     if (i < d.m) {
@@ -495,7 +496,7 @@ __global__ void __launch_bounds__(STEP_THREADS)
     if (it) {
       const int tb = __ffsll((long long)it) - 1;
 #pragma unroll
-      for (int i = 0; i < MAXIN; ++i)
+      for (int i = 0; i < M; ++i)
         if (i < d.m) rowb[i] += rowtab[i][tb];
       orow += outtab[tb];
     }
@@ -503,20 +504,20 @@ __global__ void __launch_bounds__(STEP_THREADS)
     float4 acc[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = make_float4(0.f, 0.f, 0.f, 0.f);
-    int64_t eb[MAXIN];
+    int64_t eb[M];
 #pragma unroll
-    for (int i = 0; i < MAXIN; ++i) eb[i] = 0;
+    for (int i = 0; i < M; ++i) eb[i] = 0;
     for (int jt = 0; jt < tcount; ++jt) {
       if (jt) {
         const int tb = __ffs(jt) - 1;
 #pragma unroll
-        for (int i = 0; i < MAXIN; ++i)
+        for (int i = 0; i < M; ++i)
           if (i < d.m) eb[i] += etab[i][tb];
       }
       // product of the inputs that hold no tile bit (shared by all outputs)
       float2 s0 = make_float2(1.f, 0.f), s1 = s0;
 #pragma unroll
-      for (int i = 0; i < MAXIN; ++i) {
+      for (int i = 0; i < M; ++i) {
         if (i < d.m && !tile_in[i]) {
           const char *a = ws + rowb[i] + eb[i];
           if (d.in[i].batched) {
@@ -536,7 +537,7 @@ __global__ void __launch_bounds__(STEP_THREADS)
         if (c < ncomb) {
           float2 p0 = s0, p1 = s1;
 #pragma unroll
-          for (int i = 0; i < MAXIN; ++i) {
+          for (int i = 0; i < M; ++i) {
             if (i < d.m && tile_in[i]) {
               const char *a = ws + rowb[i] + eb[i] + toff[i][c];
               if (d.in[i].batched) {
@@ -2168,7 +2169,14 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
       const uint64_t orows = rows >> d.tile_t;
       const uint64_t oblocks = (orows + rpb - 1) / rpb;
       const uint64_t gy = pow2_floor(std::min<uint64_t>(oblocks, std::min<uint64_t>(cap, 32768)));
-      k_step_tile<<<dim3(bx, (unsigned)gy), STEP_THREADS, 0, st>>>(ws, d, meta, hdr, Bp, logP);
+      const dim3 gt(bx, (unsigned)gy);
+      switch (d.m) {
+        case 1: k_step_tile<1><<<gt, STEP_THREADS, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+        case 2: k_step_tile<2><<<gt, STEP_THREADS, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+        case 3: k_step_tile<3><<<gt, STEP_THREADS, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+        case 4: k_step_tile<4><<<gt, STEP_THREADS, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+        default: k_step_tile<MAXIN><<<gt, STEP_THREADS, 0, st>>>(ws, d, meta, hdr, Bp, logP); break;
+      }
       return;
     }
     const uint64_t gy = pow2_floor(std::min<uint64_t>(row_blocks, std::min<uint64_t>(cap, 32768)));
