@@ -573,6 +573,7 @@ __global__ void __launch_bounds__(STEP_THREADS)
 
 // Product-sum step without a batch axis: thread = output entry j, rows walked
 // at stride gridDim.x * blockDim.x (a power of two) with table increments.
+template <int M>
 __global__ void __launch_bounds__(256)
     k_step_plain(char *ws, const StepDesc d, Meta *meta, Header *hdr) {
   __shared__ int64_t rowtab[MAXIN][ROWTAB];
@@ -580,12 +581,12 @@ __global__ void __launch_bounds__(256)
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const int r0 = __ffsll((long long)stride) - 1;
   build_tables(d, r0, 0, 1, rowtab, etab, threadIdx.x, blockDim.x);
-  float scale[MAXIN];
+  float scale[M];
   int esum = 0;
-  int64_t rowb[MAXIN];
+  int64_t rowb[M];
   const uint64_t j0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
 #pragma unroll
-  for (int i = 0; i < MAXIN; ++i) {
+  for (int i = 0; i < M; ++i) {
     scale[i] = 1.f;
     rowb[i] = 0;
     if (i < d.m) {
@@ -610,23 +611,23 @@ __global__ void __launch_bounds__(256)
     if (it) {
       const int t = __ffsll((long long)it) - 1;
 #pragma unroll
-      for (int i = 0; i < MAXIN; ++i)
+      for (int i = 0; i < M; ++i)
         if (i < d.m) rowb[i] += rowtab[i][t];
     }
     float2 a = make_float2(0.f, 0.f);
-    int64_t eb[MAXIN];
+    int64_t eb[M];
 #pragma unroll
-    for (int i = 0; i < MAXIN; ++i) eb[i] = 0;
+    for (int i = 0; i < M; ++i) eb[i] = 0;
     for (int jt = 0; jt < tcount; ++jt) {
       if (jt) {
         const int t = __ffs(jt) - 1;
 #pragma unroll
-        for (int i = 0; i < MAXIN; ++i)
+        for (int i = 0; i < M; ++i)
           if (i < d.m) eb[i] += etab[i][t];
       }
       float2 pr = make_float2(1.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < MAXIN; ++i) {
+      for (int i = 0; i < M; ++i) {
         if (i < d.m) {
           const float2 v = __ldg(reinterpret_cast<const float2 *>(ws + rowb[i] + eb[i]));
           pr = cmul(pr, make_float2(v.x * scale[i], v.y * scale[i]));
@@ -2199,7 +2200,13 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
 #undef QGM_SB
   } else {
     const uint64_t blocks = pow2_floor(std::max<uint64_t>(1, std::min<uint64_t>((rows + 255) / 256, (uint64_t)sms * 8)));
-    k_step_plain<<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr);
+    switch (d.m) {
+      case 1: k_step_plain<1><<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr); break;
+      case 2: k_step_plain<2><<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr); break;
+      case 3: k_step_plain<3><<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr); break;
+      case 4: k_step_plain<4><<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr); break;
+      default: k_step_plain<MAXIN><<<(unsigned)blocks, 256, 0, st>>>(ws, d, meta, hdr); break;
+    }
   }
 }
 
