@@ -642,6 +642,101 @@ __global__ void __launch_bounds__(256)
   record_max(lmax, meta, d.out_meta);
 }
 
+// A run of small product-sum steps without a batch axis in one launch of one
+// CTA: the steps run in plan order, each as in k_step_plain over a stride of
+// 256 rows, separated by block barriers (which make each step's outputs and
+// exponent visible to the next).  Tensors written inside the launch are read
+// with ordinary loads (not the read-only path); the recorded maximum of each
+// output is stored by thread 0 after a block reduction, and the metadata is
+// read through volatile loads, so no stale copy is used.
+__global__ void __launch_bounds__(256)
+    k_step_plain_group(char *ws, const StepDesc *descs, int first, int count, Meta *meta, Header *hdr) {
+  __shared__ int64_t rowtab[MAXIN][ROWTAB];
+  __shared__ int64_t etab[MAXIN][ETAB];
+  __shared__ float red[8];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  volatile Meta *vm = meta;
+  for (int si = first; si < first + count; ++si) {
+    const StepDesc &d = descs[si];
+    build_tables(d, 8, 0, 1, rowtab, etab, tid, 256);
+    float scale[MAXIN];
+    int esum = 0;
+    int64_t rowb[MAXIN];
+#pragma unroll
+    for (int i = 0; i < MAXIN; ++i) {
+      scale[i] = 1.f;
+      rowb[i] = 0;
+      if (i < d.m) {
+        const InDesc &in = d.in[i];
+        int e = 0;
+        if (in.meta >= 0) {
+          const uint32_t bits = vm[in.meta].maxbits;
+          const int E = (int)((bits >> 23) & 0xff);
+          if (E == 0xff) {
+            if (hdr && tid == 0) atomicCAS(&hdr->status, 0, QGM_ERR_NONFINITE);
+          } else if (E != 0) {
+            e = E - 126 > 126 ? 126 : E - 126;
+            scale[i] = __int_as_float((127 - e) << 23);
+          }
+          esum += e + vm[in.meta].exp;
+        }
+        int64_t ri = 0;
+        for (int b = 0; b < 8 && b < d.w_out; ++b)
+          if ((tid >> b) & 1) ri += run_bit(in, b);
+        rowb[i] = in.off + ri * 8;
+      }
+    }
+    if (tid == 0) vm[d.out_meta].exp = esum;
+    __syncthreads();
+    const uint64_t rows = 1ull << d.w_out;
+    const int tcount = 1 << d.k;
+    float lmax = 0.f;
+    float2 *out = reinterpret_cast<float2 *>(ws + d.out_off);
+    uint64_t it = 0;
+    for (uint64_t j = tid; j < rows; j += 256, ++it) {
+      if (it) {
+        const int t = __ffsll((long long)it) - 1;
+#pragma unroll
+        for (int i = 0; i < MAXIN; ++i)
+          if (i < d.m) rowb[i] += rowtab[i][t];
+      }
+      float2 a = make_float2(0.f, 0.f);
+      int64_t eb[MAXIN];
+#pragma unroll
+      for (int i = 0; i < MAXIN; ++i) eb[i] = 0;
+      for (int jt = 0; jt < tcount; ++jt) {
+        if (jt) {
+          const int t = __ffs(jt) - 1;
+#pragma unroll
+          for (int i = 0; i < MAXIN; ++i)
+            if (i < d.m) eb[i] += etab[i][t];
+        }
+        float2 pr = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < MAXIN; ++i) {
+          if (i < d.m) {
+            const float2 v = *reinterpret_cast<const float2 *>(ws + rowb[i] + eb[i]);
+            pr = cmul(pr, make_float2(v.x * scale[i], v.y * scale[i]));
+          }
+        }
+        a.x += pr.x;
+        a.y += pr.y;
+      }
+      out[j] = a;
+      lmax = fmax_nan(lmax, absmax2(a));
+    }
+    for (int o = 16; o > 0; o >>= 1) lmax = fmax_nan(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+    if (lane == 0) red[wid] = lmax;
+    __syncthreads();
+    if (tid == 0) {
+      float v = red[0];
+      for (int w = 1; w < 8; ++w) v = fmax_nan(v, red[w]);
+      if (v > 0.f || v != v) vm[d.out_meta].maxbits = __float_as_uint(v);
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // GEMM-shaped step: out[s, m, n] = sum_k A[s, m, k] B[s, n, k] for each
 // shared kept index s and batch entry (grid z and y), 64 x 64 output tiles
@@ -2338,7 +2433,20 @@ static void launch_accumulate(qgm_plan *p, double2 *d_out, int64_t n_out, cudaSt
 static int enqueue_slice(qgm_plan *p, const uint64_t *d_bits, int64_t B, double2 *d_out,
                          int64_t n_out, cudaStream_t st) {
   launch_leaves(p, d_bits, B, st);
-  for (const StepDesc &d : p->steps) launch_step(p, d, st);
+  char *ws = p->exec->ws;
+  for (size_t s = 0; s < p->steps.size();) {
+    const int32_t g = s < p->plain_group.size() ? p->plain_group[s] : 0;
+    if (g >= 2) {
+      // a run of small batch-free steps: one launch of one CTA
+      k_step_plain_group<<<1, 256, 0, st>>>(ws, reinterpret_cast<const StepDesc *>(ws + p->off_sdesc), (int)s, g,
+                                            reinterpret_cast<Meta *>(ws + p->off_meta),
+                                            reinterpret_cast<Header *>(ws + p->off_header));
+      s += (size_t)g;
+    } else {
+      launch_step(p, p->steps[s], st);
+      ++s;
+    }
+  }
   launch_accumulate(p, d_out, n_out, st);
   return QGM_OK;
 }
@@ -2525,6 +2633,9 @@ int qgm_plan_bind(qgm_plan *p, void *d_workspace, size_t ws_bytes, void *stream)
                        cudaMemcpyHostToDevice, st));
   if (!p->leafdesc.empty())
     CK(cudaMemcpyAsync(x->ws + p->off_leafdesc, p->leafdesc.data(), p->leafdesc.size() * sizeof(LeafDesc),
+                       cudaMemcpyHostToDevice, st));
+  if (!p->steps.empty())
+    CK(cudaMemcpyAsync(x->ws + p->off_sdesc, p->steps.data(), p->steps.size() * sizeof(StepDesc),
                        cudaMemcpyHostToDevice, st));
   if (p->grad && !p->gparams.empty())
     CK(cudaMemcpyAsync(x->ws + p->off_gparams, p->gparams.data(), p->gparams.size() * sizeof(GradParam),

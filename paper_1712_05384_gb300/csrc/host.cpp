@@ -1614,6 +1614,7 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
                          (int64_t)(p->leaves.size() + 1) * sizeof(RLeaf) + (njobs + 1) * sizeof(RJob) +
                          ((int64_t)S.steps.size() * RES_WARPS + RES_WARPS + 8) * 4);
   }
+  p->off_sdesc = take((int64_t)(S.steps.size() + 1) * (int64_t)sizeof(StepDesc));
   p->off_arena = take(0);
   for (SymTensor &t : S.tensors)
     if (t.leaf < 0) t.off += p->off_arena;
@@ -1753,6 +1754,20 @@ int build_plan(const Model &m, const qgm_plan_opts &o, qgm_plan *p) {
     }
   }
   p->tune.assign(p->steps.size(), StepTune{});
+  // runs of at least two consecutive small batch-free product-sum steps (at
+  // most 2^12 outputs and 2^16 products each): a launch of their own would
+  // cost more than the work
+  p->plain_group.assign(p->steps.size(), 0);
+  for (size_t s0 = 0; s0 < p->steps.size();) {
+    auto small = [&](size_t s) {
+      const StepDesc &d = p->steps[s];
+      return d.gemm < 0 && !d.batched_out && d.w_out <= 12 && d.w_out + d.k <= 16;
+    };
+    size_t s1 = s0;
+    while (s1 < p->steps.size() && small(s1)) ++s1;
+    if (s1 - s0 >= 2) p->plain_group[s0] = (int32_t)(s1 - s0);
+    s0 = s1 > s0 ? s1 : s0 + 1;
+  }
   // the split operand planes of the largest tensor-core step, after the arena
   p->ws_fwd_bytes = p->ws_bytes;
   p->planes_bytes = 0;

@@ -411,6 +411,11 @@ struct qgm_plan {
   int64_t planes_bytes = 0; // its size (the largest tensor-core step's two operands)
   int64_t ws_fwd_bytes = 0; // workspace the forward pass needs without that region
   std::vector<qgm::StepTune> tune;  // per step of `steps` (autotuner choices)
+  // runs of consecutive small steps without a batch axis, run by one CTA in
+  // one launch: plain_group[s] = steps in the run starting at s (0: none);
+  // their descriptors are copied to the workspace at off_sdesc
+  std::vector<int32_t> plain_group;
+  int64_t off_sdesc = 0;
   // per leaf: table layout (internal | slice | output variables), offset of
   // its base table and of its derivative tables (floats), its RXY member
   std::vector<std::vector<int>> leaf_layout;
