@@ -552,7 +552,9 @@ def main():
                          for i, g in enumerate(gemms)],
             "tuning": [t for t in plan.tuning()],
         }
-        launches = args.steps * int(info.n_slices * (info.n_steps + 2 + 2 * len(tc)) + 1)
+        # the library's own count of its launches per call (grouped small
+        # steps, split passes), times the timed calls
+        launches = args.steps * int(plan.amplitudes_report(d_pass, d_out, B=P, stream=stream)["launches"])
     else:
         ms = np.zeros(info.n_steps + 2)
         for _ in range(reps):

@@ -2941,9 +2941,27 @@ int qgm_amplitudes_report(qgm_plan *p, const uint64_t *d_bitstrings, int64_t B, 
   rep->bytes = p->sim.bytes * (double)rep->slices;
   rep->flops = p->sim.flops * (double)rep->slices;
   if (x->kind == QGM_EXEC_STEPWISE) {
-    int64_t per = (int64_t)p->steps.size() + 2;
-    for (const StepDesc &d : p->steps)
-      if (d.gemm >= 0 && p->gemm_tc && tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes).ok) per += 2;
+    // per slice: leaves, accumulation, and per step one launch (a run of
+    // small batch-free steps: one for the run), a tensor-core step adding
+    // its split passes (one when its streamed operand is converted in the
+    // product kernel, else two)
+    int64_t per = 2;
+    for (size_t si = 0; si < p->steps.size();) {
+      const int32_t g = si < p->plain_group.size() ? p->plain_group[si] : 0;
+      if (g >= 2) {
+        per += 1;
+        si += (size_t)g;
+        continue;
+      }
+      const StepDesc &d = p->steps[si];
+      const StepTune *tn = si < p->tune.size() ? &p->tune[si] : nullptr;
+      per += 1;
+      if (d.gemm >= 0 && p->gemm_tc && !(tn && tn->ps)) {
+        const TcCfg c = tc_config(p->gemms[d.gemm], p->Bp, p->tc_planes, tn && tn->nt_cap ? tn->nt_cap : 256);
+        if (c.ok) per += tn && tn->conv && c.fold ? 1 : 2;
+      }
+      ++si;
+    }
     rep->launches = per * rep->slices + 1;
   } else {
     rep->launches = x->jit_pre ? 2 : 1;
