@@ -277,7 +277,8 @@ int qgm_plan_get_steps(const qgm_plan *p, int32_t *out_rank, int32_t *k, int32_t
                        int32_t *batched, int64_t cap);
 /* Kernel that runs step s in the stepwise executor: 0 product-sum without a
  * batch axis, 1 batched product-sum, 2 batched with a register tile, 3 tiled
- * GEMM. */
+ * GEMM, 4 a small step without a batch axis run with its neighbours of the
+ * same kind in one single-CTA launch. */
 int qgm_plan_get_step_kernels(const qgm_plan *p, int32_t *kind, int64_t cap);
 
 /* Algorithmic cost of step s: bytes[s] (inputs read once + output written,

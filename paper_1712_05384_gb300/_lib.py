@@ -328,7 +328,8 @@ class Plan:
         return {k: a[:n] for k, a in zip(("out_rank", "k", "n_in", "batched"), arrs)}
 
     def step_kernels(self):
-        """Per step: 0 plain, 1 batched, 2 batched with register tile, 3 GEMM."""
+        """Per step: 0 plain, 1 batched, 2 batched with register tile, 3 GEMM,
+        4 plain inside a single-CTA run of small steps."""
         n = self.info.n_steps
         a = np.zeros(max(n, 1), dtype=np.int32)
         check(lib().qgm_plan_get_step_kernels(self._h, a.ctypes.data_as(_I32P), n))

@@ -52,14 +52,6 @@ struct Meta {
 
 constexpr int STEP_THREADS = 128;
 
-__device__ __forceinline__ uint64_t pext_runs(uint64_t f, const InDesc &d) {
-  uint64_t r = 0;
-#pragma unroll 1
-  for (int q = 0; q < d.nruns; ++q)
-    r |= ((f >> d.src[q]) & ((1ull << d.len[q]) - 1ull)) << d.dst[q];
-  return r;
-}
-
 // Power-of-two rescale of an operand from its recorded maximum.  For a normal
 // maximum with biased exponent E, max in [2^(E-127), 2^(E-126)), so
 // e = E - 126 puts the scaled maximum in [0.5, 1).
@@ -1790,18 +1782,6 @@ __global__ void k_init(double2 *out, int64_t n_out, Header *hdr) {
 // global write is the chunk's FP64 amplitudes.  Steps are separated by
 // __syncthreads only: no grid-wide barrier, no launch per step.
 constexpr int RES_THREADS = 256;
-
-// pext of the summed-variable index e by a k-bit mask (bits kept in order)
-__device__ __forceinline__ uint32_t pext_small(uint32_t e, uint32_t mask) {
-  uint32_t r = 0;
-  int o = 0;
-  while (mask) {
-    const int b = __ffs(mask) - 1;
-    r |= ((e >> b) & 1u) << o++;
-    mask &= mask - 1;
-  }
-  return r;
-}
 
 // Product of the M inputs at one term; with PER_LOAD each value is scaled as
 // it is loaded, otherwise the caller applies one combined scale per entry.

@@ -2301,6 +2301,9 @@ int qgm_plan_get_step_kernels(const qgm_plan *p, int32_t *kind, int64_t cap) {
     const StepDesc &d = p->steps[s];
     kind[s] = d.gemm >= 0 ? 3 : (d.tile_t > 0 ? 2 : (d.batched_out ? 1 : 0));
   }
+  // steps inside a run of small batch-free steps share one single-CTA launch
+  for (size_t s = 0; s < p->plain_group.size(); ++s)
+    for (int32_t j = 0; j < p->plain_group[s] && (int64_t)(s + j) < cap; ++j) kind[s + j] = 4;
   return QGM_OK;
 }
 

@@ -356,3 +356,19 @@ def test_batch_outer_intermediates():
         kw = dict({"batch": 4}, **kw)
         p = Q.Plan(Q.Model(Q.Circuit.grid(4, 6, 30, 0)), order_kind=1, executor=Q.EXEC_STEPWISE, **kw)
         assert not any(g["o_bout"] or g["in_bout"] for g in p.gemm_shapes())
+
+
+def test_small_batch_free_steps_run_in_groups():
+    # runs of two or more consecutive small steps without a batch axis (at
+    # most 2^12 outputs and 2^16 products) share one single-CTA launch
+    # (kind 4); every grouped step is such a step, and such a step outside a
+    # group has a non-small or batched neighbour on both sides
+    p = Q.Plan(Q.Model(Q.Circuit.grid(5, 9, 40, 0)), batch=4, order_kind=Q.ORDER_MINFILL,
+               executor=Q.EXEC_STEPWISE)
+    kinds = p.step_kernels()
+    st = p.steps()
+    small = (st["batched"] == 0) & (st["out_rank"] <= 12) & (st["out_rank"] + st["k"] <= 16) & (kinds != 3)
+    assert (kinds == 4).sum() > 100
+    assert np.all(small[kinds == 4])
+    for s in np.nonzero(small & (kinds != 4))[0]:
+        assert not (s > 0 and small[s - 1]) and not (s + 1 < len(kinds) and small[s + 1])
