@@ -247,16 +247,17 @@ def run_reference(args, rank, world):
     cores = os.cpu_count() or 1
     ts, dts = [], []
     sample = ""
-    for s in range(args.warmup + args.steps):
+    warm = max(args.warmup, 3)
+    for s in range(warm + args.steps):
         t0 = time.perf_counter()
         rate, sample, cores = cpu_oracle_sample(args.workload, c, bits[s % len(bits):])
-        if s >= args.warmup:
+        if s >= warm:
             ts.append(rate)
             dts.append(time.perf_counter() - t0)
     v = float(np.mean(ts))
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(dts)),
+        "steps": args.steps, "warmup": warm, "ms_per_step": 1e3 * float(np.mean(dts)),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "grid": f"{rows}x{cols}", "depth": depth, "batch": B, "seed": 0,
                    "parallelism": "replicas1"},
