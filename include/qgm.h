@@ -195,7 +195,7 @@ typedef struct {
                                  or inside the product kernel; the batched
                                  product-sum kernel's term
                                  groups: 1, 2 or 4, and terms in flight per
-                                 thread: 2 or 4; a GEMM-shaped step may run
+                                 thread: 2, 4 or 8; a GEMM-shaped step may run
                                  as a product-sum) on the bound device, on
                                  tensors from one pass over an all-zero batch,
                                  and keeps the fastest; 0: fixed rules */
@@ -295,7 +295,7 @@ int qgm_plan_get_step_inputs(const qgm_plan *p, int32_t step, int32_t *rec, int6
  * not a tensor-core step), product-sum term groups (0: not tuned), 1 when a
  * folded tensor-core step converts its streamed operand inside the product
  * kernel (instead of a separate split pass), product-sum terms in flight
- * per thread (4, or 0/2 for two), 1 when a GEMM-shaped step runs with the
+ * per thread (4 or 8, or 0/2 for two), 1 when a GEMM-shaped step runs with the
  * product-sum kernels instead of a GEMM kernel, and
  * ms[2c], ms[2c+1] = milliseconds with the fixed rules and with the choice.
  * *n = the number of tuned steps; rec/ms may be NULL to query it. */
@@ -303,7 +303,7 @@ int qgm_plan_get_tuning(const qgm_plan *p, int32_t *rec, float *ms, int64_t cap,
 
 /* Sets launch parameters of steps by hand, in the records qgm_plan_get_tuning
  * returns (6 ints per step: step index, N tile cap 0/64/128/256, term groups
- * 0/1/2/4, in-kernel conversion 0/1, terms in flight 0/2/4, product-sum
+ * 0/1/2/4, in-kernel conversion 0/1, terms in flight 0/2/4/8, product-sum
  * form of a GEMM-shaped step 0/1 (only where no tensor of the step keeps its
  * batch entry outermost); a parameter that does not apply to the step is
  * ignored), e.g. to reuse a tuning saved

@@ -267,49 +267,60 @@ __global__ void __launch_bounds__(512)
         }
         a0 = p0;
         a1 = p1;
-      } else if (U == 4 && tcount >= 4) {
-        // four terms per iteration (their loads in flight together): terms
-        // jt .. jt + 3 differ in the two lowest term bits, at eb + 0, e0,
-        // e0 + e1 and 2 e0 + e1 (e_t: the carry-table steps)
-        for (int jt = 0; jt < tcount; jt += 4) {
-          float2 p[4][2];
+      } else if (U >= 4 && tcount >= U) {
+        // U = 4 or 8 terms per iteration (their loads in flight together):
+        // terms jt .. jt + U - 1 differ in the log2(U) lowest term bits; bit
+        // b moves the address by r_b, with r_0 = e_0, r_1 = e_0 + e_1,
+        // r_2 = 2 e_0 + e_1 + e_2 (e_t: the carry-table steps)
+        for (int jt = 0; jt < tcount; jt += U) {
+          float2 p[U][2];
 #pragma unroll
-          for (int u = 0; u < 4; ++u) p[u][0] = p[u][1] = make_float2(1.f, 0.f);
+          for (int u = 0; u < U; ++u) p[u][0] = p[u][1] = make_float2(1.f, 0.f);
 #pragma unroll
           for (int i = 0; i < M; ++i) {
-            const int64_t e0 = etab[i][0], e1 = etab[i][1];
+            const int64_t r0 = etab[i][0], r1 = etab[i][0] + etab[i][1];
+            const int64_t r2 = U == 8 ? 2 * etab[i][0] + etab[i][1] + etab[i][2] : 0;
             const char *a = ws + rowb[i] + eb[i];
-            const int64_t off[4] = {0, e0, e0 + e1, 2 * e0 + e1};
             if (d.in[i].batched) {
-              float4 v[4];
+              float4 v[U];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4 *>(a + off[u]));
+              for (int u = 0; u < U; ++u)
+                v[u] = __ldg(reinterpret_cast<const float4 *>(a + ((u & 1) ? r0 : 0) + ((u & 2) ? r1 : 0) +
+                                                              ((u & 4) ? r2 : 0)));
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
+              for (int u = 0; u < U; ++u) {
                 p[u][0] = cmul(p[u][0], make_float2(v[u].x * scale[i], v[u].y * scale[i]));
                 p[u][1] = cmul(p[u][1], make_float2(v[u].z * scale[i], v[u].w * scale[i]));
               }
             } else {
-              float2 v[4];
+              float2 v[U];
 #pragma unroll
-              for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float2 *>(a + off[u]));
+              for (int u = 0; u < U; ++u)
+                v[u] = __ldg(reinterpret_cast<const float2 *>(a + ((u & 1) ? r0 : 0) + ((u & 2) ? r1 : 0) +
+                                                              ((u & 4) ? r2 : 0)));
 #pragma unroll
-              for (int u = 0; u < 4; ++u) {
+              for (int u = 0; u < U; ++u) {
                 const float2 sv = make_float2(v[u].x * scale[i], v[u].y * scale[i]);
                 p[u][0] = cmul(p[u][0], sv);
                 p[u][1] = cmul(p[u][1], sv);
               }
             }
           }
-          a0.x += (p[0][0].x + p[1][0].x) + (p[2][0].x + p[3][0].x);
-          a0.y += (p[0][0].y + p[1][0].y) + (p[2][0].y + p[3][0].y);
-          a1.x += (p[0][1].x + p[1][1].x) + (p[2][1].x + p[3][1].x);
-          a1.y += (p[0][1].y + p[1][1].y) + (p[2][1].y + p[3][1].y);
-          if (jt + 4 < tcount) {
-            const int t = __ffs(jt + 4) - 1;
 #pragma unroll
-            for (int i = 0; i < M; ++i)
-              eb[i] += 2 * etab[i][0] + etab[i][1] + etab[i][t];
+          for (int u = 0; u < U; ++u) {
+            a0.x += p[u][0].x;
+            a0.y += p[u][0].y;
+            a1.x += p[u][1].x;
+            a1.y += p[u][1].y;
+          }
+          if (jt + U < tcount) {
+            const int t = __ffs(jt + U) - 1;
+#pragma unroll
+            for (int i = 0; i < M; ++i) {
+              const int64_t r0 = etab[i][0], r1 = etab[i][0] + etab[i][1];
+              const int64_t r2 = U == 8 ? 2 * etab[i][0] + etab[i][1] + etab[i][2] : 0;
+              eb[i] += r0 + r1 + r2 + etab[i][t];
+            }
           }
         }
       } else {
@@ -2257,10 +2268,13 @@ static void launch_step_ws(char *ws, int sms, int Bp, const StepDesc &d, const G
     }
     const uint64_t gy = pow2_floor(std::min<uint64_t>(row_blocks, std::min<uint64_t>(cap, 32768)));
     const dim3 g2(bx, (unsigned)gy), b2(STEP_THREADS, T);
-    // four terms in flight per thread where the tuner measured that faster
-    const bool u4 = tn && tn->U == 4 && d.k >= 2 && (d.k - (31 - __builtin_clz((unsigned)T))) >= 2;
+    // four or eight terms in flight per thread where the tuner measured that
+    // faster (each thread's term count 2^(k - log2 T) must hold them)
+    const int tbits = d.k - (31 - __builtin_clz((unsigned)T));
+    const int uu = tn && tn->U == 8 && tbits >= 3 ? 8 : (tn && tn->U >= 4 && tbits >= 2 ? 4 : 2);
 #define QGM_SB(M_)                                                                      \
-  if (u4) k_step_batched<M_, 4><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP);         \
+  if (uu == 8) k_step_batched<M_, 8><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP);    \
+  else if (uu == 4) k_step_batched<M_, 4><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP); \
   else k_step_batched<M_, 2><<<g2, b2, 0, st>>>(ws, d, meta, hdr, Bp, logP);
     switch (d.m) {
       case 1: QGM_SB(1) break;
@@ -2357,9 +2371,9 @@ static int autotune(qgm_plan *p, cudaStream_t st) {
           cand.push_back(t);
         }
     } else if (d.gemm < 0 && d.batched_out && d.tile_t == 0) {
-      for (int U : {2, 4})
+      for (int U : {2, 4, 8})
         for (int T : {1, 2, 4})
-          if (T <= (1 << std::min(d.k, 4)) && (U == 2 || (1 << d.k) >= 4 * T)) {
+          if (T <= (1 << std::min(d.k, 4)) && (U == 2 || (1 << d.k) >= U * T)) {
             StepTune t;
             t.T = T;
             t.U = U;
@@ -3076,7 +3090,7 @@ int qgm_plan_set_tuning(qgm_plan *p, const int32_t *rec, int64_t n) {
     bool ok = r[0] >= 0 && r[0] < (int32_t)p->steps.size() &&
               (r[1] == 0 || r[1] == 64 || r[1] == 128 || r[1] == 256) &&
               (r[2] == 0 || r[2] == 1 || r[2] == 2 || r[2] == 4) && (r[3] == 0 || r[3] == 1) &&
-              (r[4] == 0 || r[4] == 2 || r[4] == 4) && (r[5] == 0 || r[5] == 1);
+              (r[4] == 0 || r[4] == 2 || r[4] == 4 || r[4] == 8) && (r[5] == 0 || r[5] == 1);
     if (ok && r[5]) {
       // a product-sum needs the batch axis innermost on every tensor of the step
       const StepDesc &d = p->steps[r[0]];

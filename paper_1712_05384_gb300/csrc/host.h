@@ -169,7 +169,7 @@ struct StepTune {
   int32_t nt_cap = 0;     // tensor-core GEMM: N tile at most 256, 128 or 64 (0: 256)
   int32_t T = 0;          // batched product-sum: term groups per row (0: rule)
   int32_t conv = 0;       // folded tensor-core step: 1 converts the M side in the product kernel
-  int32_t U = 0;          // batched product-sum: terms in flight per thread (4, else 2)
+  int32_t U = 0;          // batched product-sum: terms in flight per thread (4 or 8, else 2)
   int32_t ps = 0;         // GEMM-shaped step: 1 runs it with the product-sum kernels
   float ms_rule = 0.f;    // measured time with the fixed rules (ms)
   float ms_best = 0.f;    // measured time of the chosen candidate (ms)

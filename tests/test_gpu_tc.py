@@ -162,7 +162,7 @@ def test_every_tuning_candidate_gives_the_same_amplitudes(rows, cols, depth, B, 
     for nt in (64, 128, 256):
         for conv in (0, 1):
             for T in (1, 2, 4):
-                for U in (2, 4):
+                for U in (2, 4, 8):
                     p.set_tuning([{"step": s, "nt_cap": nt, "conv": conv, "T": T, "U": U} for s in range(n_steps)])
                     a = p.amplitudes_host(bits)
                     assert p.status() == 0
@@ -171,7 +171,7 @@ def test_every_tuning_candidate_gives_the_same_amplitudes(rows, cols, depth, B, 
                     rel, ab = errmeasure.measures(a[:4], ref, c.n)["rel"], errmeasure.measures(a[:4], ref, c.n)["abs"]
                     assert rel < SPLIT_TOL and ab < SPLIT_TOL, (nt, conv, T, U, rel, ab)
     got = p.tuning()
-    assert len(got) == n_steps and all(t["U"] == 4 and t["T"] == 4 for t in got)
+    assert len(got) == n_steps and all(t["U"] == 8 and t["T"] == 4 for t in got)
     # GEMM-shaped steps as product-sums (where no tensor keeps its batch
     # entry outermost; the others refuse)
     shapes = p.gemm_shapes()
