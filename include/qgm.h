@@ -260,7 +260,7 @@ typedef struct {
   int32_t n_nested_steps;     /* steps whose compiled form sums some variables
                                  in an inner loop over part of the inputs */
   int32_t n_gemm_tc_steps;    /* of the GEMM steps, those run on the tensor
-                                 cores (qgm_plan_opts.gemm_split_bf16) */
+                                 cores (qgm_plan_opts.gemm_precision) */
 } qgm_plan_info;
 
 /* Elimination order, slicing, step list and memory layout (Sec. IV, App. A).
