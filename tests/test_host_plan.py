@@ -372,3 +372,18 @@ def test_small_batch_free_steps_run_in_groups():
     assert np.all(small[kinds == 4])
     for s in np.nonzero(small & (kinds != 4))[0]:
         assert not (s > 0 and small[s - 1]) and not (s + 1 < len(kinds) and small[s + 1])
+
+
+@pytest.mark.parametrize("rows,cols,depth,batch", [(5, 9, 40, 4), (4, 8, 40, 16), (4, 6, 34, 6)])
+def test_folded_steps_are_the_convertible_ones(rows, cols, depth, batch):
+    # a tensor-core step can convert its streamed operand in the product
+    # kernel exactly when its batch entries fold into M: the output and one
+    # operand carry the batch axis, the other does not (and the batch has
+    # more than one entry)
+    p = Q.Plan(Q.Model(Q.Circuit.grid(rows, cols, depth, 0)), batch=batch, order_kind=Q.ORDER_MINFILL,
+               executor=Q.EXEC_STEPWISE)
+    gs = p.gemm_shapes()
+    assert any(g["conv_ok"] for g in gs)
+    for g in gs:
+        fold = g["tc"] and g["o_bat"] and (g["a_bat"] != g["b_bat"]) and batch > 1
+        assert g["conv_ok"] == int(bool(fold)), g
